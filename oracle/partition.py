@@ -1,0 +1,138 @@
+"""Slice partition, validation and shift migration (Sections 2.3, 3.1, 3.2).
+
+Test infrastructure only.  Readings where the paper is silent or garbled:
+* CDOS roots (Eq. 15) are read as Phi(omega) = Phi(a) + K j, j = 0..n_s,
+  K = (Phi(b) - Phi(a)) / n_s, found by bisection to 1e-12 relative width.
+* The interval midpoint is (l + u)/2.
+* End slices are [lambda_min, sigma_1) and (sigma_ns, lambda_max].
+* A candidate exactly at tau goes to the lower probe; residual ties are broken by
+  (residual, probe index, Ritz index).
+* k-means++ draws its uniforms from an input array (one per centroid) so that both
+  sides see the same random numbers.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .dos import cdos_Phi
+
+
+def bisect_root(f, lo, hi, target, rel=1e-12, maxit=200):
+    """Smallest-bracket root of f(x) = target for nondecreasing f on [lo, hi]."""
+    flo = f(lo) - target
+    for _ in range(maxit):
+        mid = 0.5 * (lo + hi)
+        if hi - lo <= rel * max(1.0, abs(mid)):
+            break
+        if f(mid) - target < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    del flo
+    return 0.5 * (lo + hi)
+
+
+def cdos_root_intervals(a, b, n_s, n, runs):
+    """Intervals (l_j, u_j) with about equal CDOS mass (Eq. 15)."""
+    Pa = float(cdos_Phi(a, n, runs)[0])
+    Pb = float(cdos_Phi(b, n, runs)[0])
+    K = (Pb - Pa) / n_s
+    f = lambda w: float(cdos_Phi(w, n, runs)[0])
+    roots = [a]
+    for j in range(1, n_s):
+        roots.append(bisect_root(f, a, b, Pa + K * j))
+    roots.append(b)
+    return [(roots[j], roots[j + 1]) for j in range(n_s)]
+
+
+def candidates(shifts, lam_min, lam_max, probes):
+    """Validation candidates per slice (Section 2.3).
+
+    probes[j] = (theta[k], resid[k]) of the probe at shifts[j].  Returns a list over the
+    n_s + 1 slices of lists of (probe j, ritz index i)."""
+    ns = len(shifts)
+    out = []
+    for s in range(ns + 1):
+        cand = []
+        lo = lam_min if s == 0 else shifts[s - 1]
+        hi = lam_max if s == ns else shifts[s]
+        if s == 0:
+            th = probes[0][0]
+            cand += [(0, i) for i in range(len(th)) if lam_min <= th[i] < shifts[0]]
+        elif s == ns:
+            th = probes[ns - 1][0]
+            cand += [(ns - 1, i) for i in range(len(th)) if shifts[-1] < th[i] <= lam_max]
+        else:
+            tau = 0.5 * (lo + hi)
+            th = probes[s - 1][0]
+            cand += [(s - 1, i) for i in range(len(th)) if lo < th[i] <= tau]
+            th = probes[s][0]
+            cand += [(s, i) for i in range(len(th)) if tau < th[i] < hi]
+        out.append(cand)
+    return out
+
+
+def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max):
+    """Apply the three validation cases per slice (Section 2.3).
+
+    nneg_shift[j] = #negative pivots of LDL^T(A - shifts[j] B); nneg_min / nneg_max
+    are the counts at the region bounds.  Returns (validated list of (probe, ritz),
+    per-slice (n_exact, n_cand, status)) with status 'ok' / 'missing' / 'excess'."""
+    ns = len(shifts)
+    cands = candidates(shifts, lam_min, lam_max, probes)
+    bounds = [nneg_min] + list(nneg_shift) + [nneg_max]
+    validated, info = [], []
+    for s in range(ns + 1):
+        n_exact = bounds[s + 1] - bounds[s]
+        c = cands[s]
+        if n_exact == len(c):
+            validated += c
+            info.append((n_exact, len(c), "ok"))
+        elif n_exact > len(c):
+            validated += c
+            info.append((n_exact, len(c), "missing"))
+        else:
+            key = sorted(c, key=lambda pi: (probes[pi[0]][1][pi[1]], pi[0], pi[1]))
+            validated += key[:n_exact]
+            info.append((n_exact, len(c), "excess"))
+    return validated, info
+
+
+def kmeans_pp_init(x, n_c, uniforms):
+    """k-means++ seeding on 1-D data (Section 3.2): the first centroid uniformly, the
+    rest with probability proportional to D(x)^2, D = distance to nearest centroid."""
+    x = np.asarray(x, dtype=np.float64)
+    n = x.size
+    cent = [x[min(n - 1, int(uniforms[0] * n))]]
+    for c in range(1, n_c):
+        d2 = np.min((x[:, None] - np.asarray(cent)[None, :]) ** 2, axis=1)
+        tot = d2.sum()
+        if tot <= 0.0:
+            cent.append(x[min(n - 1, int(uniforms[c] * n))])
+            continue
+        cdf = np.cumsum(d2) / tot
+        idx = int(np.searchsorted(cdf, uniforms[c], side="right"))
+        cent.append(x[min(n - 1, idx)])
+    return np.asarray(cent)
+
+
+def lloyd(x, cent, maxit=1000):
+    """Lloyd iterations until the assignment stops changing; returns sorted centroids."""
+    x = np.asarray(x, dtype=np.float64)
+    cent = np.asarray(cent, dtype=np.float64).copy()
+    assign = None
+    for _ in range(maxit):
+        a = np.argmin(np.abs(x[:, None] - cent[None, :]), axis=1)
+        if assign is not None and np.array_equal(a, assign):
+            break
+        assign = a
+        for c in range(cent.size):
+            m = a == c
+            if m.any():
+                cent[c] = x[m].mean()
+    return np.sort(cent)
+
+
+def kmeans_shifts(ritz_values, n_s, uniforms):
+    """New shifts = k-means centroids of the validated Ritz values (Section 3.2)."""
+    return lloyd(ritz_values, kmeans_pp_init(ritz_values, n_s, uniforms))
