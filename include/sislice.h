@@ -1,0 +1,241 @@
+/*
+ * sislice.h -- C ABI of the GB300 slice-solve library (shift-invert spectrum slicing
+ * of a sparse symmetric-definite pencil, A x = lambda B x, A symmetric, B SPD;
+ * problem statement Eq. 1 of arXiv 1908.06043).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns an ss_status.  SS_OK is 0; on failure ss_last_error(ctx)
+ *   returns a one-line message (owned by the context, valid until the next call).
+ * - "device" pointers are CUDA global-memory pointers on the context's device;
+ *   "host" pointers are ordinary CPU memory.  The caller owns every buffer it passes
+ *   and the CUDA stream; the library owns the opaque handles and frees their memory
+ *   in the matching *_destroy call.  No call allocates memory that the caller sees.
+ * - All device work is ordered on the context's stream.  Calls that return host
+ *   values (ss_inertia, ss_slice_solve, ss_dos_estimate) synchronise that stream.
+ * - Dense blocks of vectors (V, X, right-hand sides) are N x k ROW-MAJOR: element
+ *   (i, j) -- component i of vector j -- sits at offset i*k + j.
+ * - The sparse pattern is the FULL symmetric CSR pattern of A union B (both triangles
+ *   stored, diagonal included, column indices sorted within each row); value arrays
+ *   a_vals / b_vals are aligned with it (an entry absent from one matrix is an
+ *   explicit 0).  Indices are 0-based.
+ */
+#ifndef SISLICE_H
+#define SISLICE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ss_status;
+enum {
+    SS_OK = 0,
+    SS_ERR_ARG = 1,       /* bad argument (null pointer, size, index out of range)   */
+    SS_ERR_CUDA = 2,      /* a CUDA runtime call failed                               */
+    SS_ERR_OOM = 3,       /* device or host allocation failed                        */
+    SS_ERR_SINGULAR = 4,  /* a pivot fell below the threshold: sigma is (near) an
+                             eigenvalue; move sigma and refactor                      */
+    SS_ERR_NOT_SPD = 5,   /* B is not positive definite (DOS needs its Cholesky)      */
+    SS_ERR_NOCONV = 6,    /* the in-slice iteration hit its iteration cap             */
+    SS_ERR_TIMEOUT = 7,   /* a bounded device wait expired                            */
+    SS_ERR_INTERNAL = 8
+};
+
+enum { SS_FP64 = 0, SS_MIXED = 1 };      /* factor precision                     */
+enum { SS_SUBSPACE = 0, SS_BLOCK_LANCZOS = 1 };  /* in-slice driver             */
+
+typedef struct ss_ctx ss_ctx;
+typedef struct ss_symbolic ss_symbolic;
+typedef struct ss_numeric ss_numeric;
+
+/* Options of the symbolic analysis.  Zero fields take the defaults in brackets. */
+typedef struct ss_options {
+    int32_t nd_leaf;        /* nested dissection stops at this many vertices [64]    */
+    int32_t panel;          /* panel width of the blocked front factorisation [64]   */
+    int32_t reserved[6];
+} ss_options;
+
+/* Summary of a symbolic analysis (all counts are exact, from the analysis). */
+typedef struct ss_symbolic_info {
+    int64_t n, nnz;
+    int64_t n_supernodes, n_levels, n_panels, n_panel_levels;
+    int64_t max_front;          /* largest front dimension m                        */
+    int64_t factor_entries;     /* sum over supernodes of m * ncol (stored L panels) */
+    int64_t front_entries;      /* sum over supernodes of m * m (front arena)        */
+    double factor_flops;        /* algorithmic sparse LDL^T flops: sum over
+                                   supernodes of s^3/3 + s^2 b + s b^2, s = ncol,
+                                   b = off-diagonal rows                             */
+    double schur_flops;         /* Schur-update flops per factorisation: sum over panel
+                                   steps of 2 w r(r+1)/2 (lower triangle, r trailing
+                                   rows, w panel width)                              */
+    double panel_flops;         /* panel-transform flops: sum of 2 r w^2             */
+    int64_t l_offdiag_entries;  /* sum over panels of r w: L entries below the panel
+                                   diagonal blocks (read once per triangular sweep)  */
+    int64_t l_diag_entries;     /* sum over panels of w^2                            */
+    double analyze_seconds;
+} ss_symbolic_info;
+
+/* Per-probe statistics of one slice solve. */
+typedef struct ss_probe_stats {
+    int32_t iterations;         /* operator applications of the in-slice driver      */
+    int32_t refine_steps;       /* total FP64 refinement corrections applied         */
+    int32_t converged;          /* 1 when every Ritz value in (lo, hi] met tol       */
+    int32_t reserved;
+    double max_resid_in_slice;  /* max normalised residual over Ritz values in slice */
+    double seconds;
+} ss_probe_stats;
+
+/* Options of one slice solve.  Zero fields take the defaults in brackets. */
+typedef struct ss_solve_opts {
+    int32_t driver;             /* SS_SUBSPACE | SS_BLOCK_LANCZOS [SS_SUBSPACE]      */
+    int32_t max_iter;           /* iteration cap [200]                               */
+    int32_t check_every;        /* Rayleigh-Ritz + residual check period [1]         */
+    int32_t refine;             /* FP64 refinement corrections per solve, mixed
+                                   factor only [2]                                   */
+    double tol;                 /* normalised residual target [1e-10]                */
+    int32_t n_expect;           /* keep iterating until at least this many Ritz values
+                                   lie in (lo, hi] (e.g. an inertia count) [0]        */
+    int32_t reserved[3];
+} ss_solve_opts;
+
+/* ---- context ---------------------------------------------------------------------
+ * ss_create: bind a context to CUDA device `device` and stream `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  The stream is borrowed.
+ * device = -1 makes a host-only context: ss_analyze, ss_symbolic_info_get,
+ * ss_symbolic_perm and ss_symbolic_validate work without a GPU; every device call
+ * returns SS_ERR_ARG.  Errors: SS_ERR_ARG (null ctx), SS_ERR_CUDA (bad device). */
+ss_status ss_create(ss_ctx **ctx, int32_t device, void *cuda_stream);
+ss_status ss_destroy(ss_ctx *ctx);
+const char *ss_last_error(const ss_ctx *ctx);
+
+/* ---- ss_analyze (Section 2.2: the sparse LDL^T of A - sigma B is the major cost;
+ * Section 5: the paper's solver orders with nested dissection) --------------------
+ * Host CSR pattern in, symbolic analysis out: nested-dissection ordering, supernodes
+ * (the dissection blocks), the assembly tree and its level schedule, front index
+ * maps, panel solve schedule and flop counts.  Done once per pattern and reused for
+ * every shift and every pencil on that pattern.  rowptr[n+1] (int64) and colind[nnz]
+ * (int32) are HOST arrays; they are copied.
+ * Errors: SS_ERR_ARG (n <= 0, unsorted / out-of-range / asymmetric pattern),
+ * SS_ERR_OOM. */
+ss_status ss_analyze(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int32_t *colind,
+                     const ss_options *opt, ss_symbolic **out);
+ss_status ss_symbolic_info_get(const ss_symbolic *sym, ss_symbolic_info *info);
+/* Fill-reducing permutation, host int32[n]: perm[new] = old. */
+ss_status ss_symbolic_perm(const ss_symbolic *sym, int32_t *perm);
+ss_status ss_symbolic_destroy(ss_symbolic *sym);
+/* Consistency check of a symbolic analysis (no paper counterpart; a diagnostic): every
+ * index the device kernels derive from it -- arena offsets, assembly destinations,
+ * extend-add maps, panel / step / solve-level descriptors and scratch extents -- is
+ * checked against the buffer it addresses, the ordering is checked to be a permutation
+ * and every stored entry to lie inside its supernode's front.  Host only.
+ * Errors: SS_ERR_INTERNAL with the first violation in ss_last_error. */
+ss_status ss_symbolic_validate(const ss_symbolic *sym);
+
+/* ---- ss_factor (Alg. 2 step 2: (L, D) <- LDL^T of A - sigma B) ------------------
+ * Numeric supernodal multifrontal LDL^T of A - sigma_j B for each of the n_shift
+ * shifts sigma[] (HOST array), one factor per shift, all sharing `sym`.  a_vals /
+ * b_vals are DEVICE float64[nnz] aligned with the analysed pattern; they must stay
+ * alive and unchanged while the factor is used (solves read them for residuals).
+ * Pivoting is Bunch-Kaufman (1x1 / 2x2) restricted to each panel's diagonal block,
+ * computed in FP64.  precision = SS_FP64 keeps fronts in FP64; SS_MIXED keeps fronts
+ * and Schur updates in FP32 with FP64 diagonal blocks, and solves with FP64 iterative
+ * refinement.
+ * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_SINGULAR (a pivot fell below
+ * 64 u ||A - sigma B||_1 for some shift; the factor is still returned and
+ * ss_inertia reports which shift). */
+ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                    const double *sigma, int32_t n_shift, int32_t precision,
+                    ss_numeric **out);
+ss_status ss_factor_destroy(ss_numeric *f);
+
+/* ---- ss_inertia (Section 2.3: Sylvester's law of inertia) ------------------------
+ * Inertia of A - sigma_j B from the block-diagonal D: n_neg = #negative 1x1 pivots
+ * + one per 2x2 block with det < 0 (+ two per 2x2 block with det > 0 and negative
+ * trace).  n_neg equals the number of eigenvalues of (A, B) below sigma_j.  Host
+ * int64 outputs.  *tiny_pivot (may be NULL) is set to 1 if any pivot of this shift
+ * fell below the singularity threshold.  Errors: SS_ERR_ARG. */
+ss_status ss_inertia(const ss_numeric *f, int32_t shift_idx, int64_t *n_neg, int64_t *n_zero,
+                     int64_t *n_pos, int32_t *tiny_pivot);
+
+/* ---- ss_solve (Alg. 2 step 3 without B: X = (A - sigma_j B)^-1 R) ------------------
+ * R and X are DEVICE float64 N x k row-major (may alias).  For a mixed factor, `refine`
+ * FP64 refinement corrections are applied (residual by FP64 SpMM with A and B).
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM. */
+ss_status ss_solve(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k, double *X,
+                   int32_t refine);
+
+/* ---- ss_slice_solve (Alg. 2: shift-invert subspace iteration with Cholesky-QR in
+ * the B inner product, Rayleigh-Ritz, residual norms; Section 2.2) ----------------
+ * Builds the spectral probe of shift sigma_j: k Ritz pairs nearest sigma_j.  V0 is
+ * the DEVICE N x k start block (seeded N(0,1) or a previous probe's X; required).
+ * A Ritz pair is converged when its normalised residual
+ * ||A x - theta B x||_2 / (||A||_1 ||x||_2) <= opts->tol.  Iterates until at least
+ * opts->n_expect Ritz values in (lo, hi] are converged (n_expect > 0, e.g. an exact
+ * count from inertia), or every Ritz value in (lo, hi] is (n_expect = 0), or max_iter.
+ * Unconverged Ritz values inside the window can be spurious mixtures of eigenvectors
+ * at equal distance on both sides of sigma; validation (Section 2.3) discards them.
+ * Outputs: lambda (HOST float64[k], ascending Ritz values), X (DEVICE N x k, B-
+ * orthonormal Ritz vectors in the same order), resid (HOST float64[k]), n_found
+ * (HOST: #converged Ritz values in (lo, hi]), stats (HOST, may be NULL).
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_NOCONV (outputs still valid). */
+ss_status ss_slice_solve(ss_numeric *f, int32_t shift_idx, double lo, double hi,
+                         const ss_solve_opts *opts, const double *V0, int32_t k,
+                         double *lambda, double *X, double *resid, int32_t *n_found,
+                         ss_probe_stats *stats);
+
+/* ---- ss_dos_estimate (Section 3.1, Eqs. 13-14: Lanczos DOS of L^-1 A L^-T) --------
+ * Factors B (Cholesky via LDL^T at sigma = 0 of the pencil (B, 0)), then runs
+ * `steps` Lanczos steps on L^-1 A L^-T with full re-orthogonalisation for each of the
+ * n_vec DEVICE start vectors in start (N x n_vec row-major, e.g. seeded N(0,1)).
+ * Outputs (HOST): theta[n_vec*steps], zeta2[n_vec*steps] (squared first components
+ * of the tridiagonal's eigenvectors, per run, ascending theta), m_run[n_vec] (steps
+ * actually taken per run; entries past m_run are 0).
+ * Errors: SS_ERR_ARG, SS_ERR_NOT_SPD, SS_ERR_CUDA, SS_ERR_OOM. */
+ss_status ss_dos_estimate(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                          int32_t steps, int32_t n_vec, const double *start,
+                          double *theta, double *zeta2, int32_t *m_run);
+
+/* ---- ss_band_energy_grad (Hellmann-Feynman; not in the paper) ----------------------
+ * For E = sum_{i < n_e} lambda_i with B-orthonormal eigenvectors X (DEVICE N x n_e
+ * row-major) and lambda (DEVICE float64[n_e]):
+ *   grad_a[e] = sum_i X[r,i] X[c,i],  grad_b[e] = -sum_i lambda_i X[r,i] X[c,i]
+ * for every stored entry e = (r, c) of the pattern (DEVICE float64[nnz] each; either
+ * may be NULL).  This is the per-stored-entry derivative; a symmetric parameter tying
+ * (r, c) and (c, r) gets the sum of both entries.  Errors: SS_ERR_ARG, SS_ERR_CUDA. */
+ss_status ss_band_energy_grad(ss_symbolic *sym, const double *X, const double *lambda,
+                              int32_t n_e, double *grad_a, double *grad_b);
+
+/* ---- SpMM helper (the CSR sweep of Section 3.1 and the residual of Alg. 2) -------
+ * Y[i, j] = sum_e (alpha[j] a_vals[e] + beta[j] b_vals[e]) X[col(e), j] over row i,
+ * X, Y DEVICE float64 N x k row-major; alpha, beta DEVICE float64[k].
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA. */
+ss_status ss_spmm(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                  const double *alpha, const double *beta, const double *X, int32_t k,
+                  double *Y);
+
+/* Device synchronisation of the context's stream (convenience for bindings). */
+ss_status ss_sync(ss_ctx *ctx);
+
+/* ---- measurement hooks (no paper counterpart) -------------------------------------
+ * Kernel classes, for per-class timing.  ss_launch_count returns the number of
+ * kernels this library has launched since it was loaded (all contexts).
+ * ss_profile(ctx, mask) starts timing every launch of the classes whose bit is set
+ * in mask (bit c = class c) with CUDA events recorded on the launching stream, and
+ * clears the previous totals; mask = 0 stops.  ss_profile_query synchronises the
+ * stream and returns the launch count and summed device time of class cls since the
+ * last ss_profile call.  Errors: SS_ERR_ARG, SS_ERR_CUDA. */
+enum {
+    SS_K_ASSEMBLE = 0, SS_K_EXTEND_ADD, SS_K_DIAG_BK, SS_K_PANEL, SS_K_SCHUR, SS_K_FWD_DIAG,
+    SS_K_FWD_UPDATE, SS_K_BWD_GATHER, SS_K_BWD_DIAG, SS_K_PERMUTE, SS_K_SPMM, SS_K_GRAM,
+    SS_K_GEMM, SS_K_SMALL_DENSE, SS_K_JACOBI, SS_K_LANCZOS, SS_K_SDDMM, SS_K_MISC, SS_K_COUNT
+};
+int64_t ss_launch_count(void);
+ss_status ss_profile(ss_ctx *ctx, uint32_t mask);
+ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SISLICE_H */

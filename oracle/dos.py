@@ -2,9 +2,9 @@
 
 Test infrastructure only.  Follows the paper's steps in order:
 
-1. Lanczos on C = L^-1 A L^-T with B = L L^T (Section 3.1), start vector drawn from
-   N(0,1) (passed in), k steps, full re-orthogonalisation (the paper does not say; we
-   take full re-orthogonalisation).
+1. B-orthonormal Lanczos on B^-1 A (the second form of Section 3.1, the one whose
+   N(0,1) start vector the paper describes), start vector passed in, k steps, full
+   re-orthogonalisation (the paper does not say; we take full re-orthogonalisation).
 2. Ritz pairs (theta_j, g_j) of the Lanczos tridiagonal, zeta_j = e_1^T g_j (Eq. 13).
 3. Gaussian widths nu_j: d_j = max of the neighbour gaps (one gap at the ends), floored
    at 1e-3 (theta_max - theta_min)/k, nu_j = d_j / 3 (our reading of "nearly vanishes").
@@ -28,33 +28,38 @@ from . import dense
 
 
 def lanczos_ritz(A: np.ndarray, B: np.ndarray, x0: np.ndarray, k: int):
-    """k-step Lanczos on L^-1 A L^-T from start vector x0; returns (theta, zeta2, alpha, beta)."""
+    """k-step B-orthonormal Lanczos on B^-1 A from start vector x0 (Section 3.1).
+
+    x_1 = x0 / ||x0||_B; w = B^-1 A x_j - alpha_j x_j - beta_{j-1} x_{j-1} with
+    alpha_j = x_j^T A x_j; full re-orthogonalisation in the B inner product; beta_j =
+    ||w||_B.  Returns (theta, zeta2, alpha, beta); zeta_j = e_1^T g_j for the Ritz
+    vectors g_j of the tridiagonal (Eq. 13).  This is Lanczos on L^-1 A L^-T started
+    from L^T x0 for any B = L L^T."""
     n = A.shape[0]
-    L = np.linalg.cholesky(B)
-    def op(v):
-        y = sla.solve_triangular(L, v, lower=True, trans="T")
-        y = A @ y
-        return sla.solve_triangular(L, y, lower=True)
+    Lb = np.linalg.cholesky(B)
+    def binv(v):
+        return sla.solve_triangular(Lb, sla.solve_triangular(Lb, v, lower=True), lower=True, trans="T")
     k = min(k, n)
-    Q = np.zeros((n, k))
+    X = np.zeros((n, k))
     alpha = np.zeros(k)
     beta = np.zeros(k)
-    q = np.asarray(x0, dtype=np.float64) / np.linalg.norm(x0)
-    q_prev = np.zeros(n)
+    x = np.asarray(x0, dtype=np.float64)
+    x = x / math.sqrt(x @ (B @ x))
+    x_prev = np.zeros(n)
     b_prev = 0.0
     m = k
     for j in range(k):
-        Q[:, j] = q
-        w = op(q) - b_prev * q_prev
-        alpha[j] = q @ w
-        w = w - alpha[j] * q
-        for _ in range(2):                       # full re-orthogonalisation
-            w = w - Q[:, : j + 1] @ (Q[:, : j + 1].T @ w)
-        beta[j] = np.linalg.norm(w)
+        X[:, j] = x
+        u = A @ x
+        alpha[j] = x @ u
+        w = binv(u) - alpha[j] * x - b_prev * x_prev
+        for _ in range(2):                       # full re-orthogonalisation (B inner product)
+            w = w - X[:, : j + 1] @ (X[:, : j + 1].T @ (B @ w))
+        beta[j] = math.sqrt(max(w @ (B @ w), 0.0))
         if j + 1 < k and beta[j] <= 1e-13 * max(1.0, abs(alpha[j])):
             m = j + 1
             break
-        q_prev, q, b_prev = q, w / beta[j], beta[j]
+        x_prev, x, b_prev = x, w / beta[j], beta[j]
     theta, Z = dense.tridiag_eig(alpha[:m], beta[: m - 1], vectors=True)
     zeta2 = Z[0, :] ** 2
     return theta, zeta2, alpha[:m], beta[: m - 1]

@@ -1,0 +1,305 @@
+"""Python binding of the slice-solve library: argument marshalling over the C ABI.
+
+PyTorch provides device memory and the stream; every step of the path runs in the
+library's CUDA kernels.  Names follow the C ABI: ``analyze``, ``factor``, ``inertia``,
+``solve``, ``slice_solve``, ``dos_estimate``, ``band_energy_grad``, ``spmm``.
+
+Blocks of vectors are torch float64 CUDA tensors of shape (N, k), row-major.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class SisliceError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{L.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(t.data_ptr())
+
+
+def _dev(t: torch.Tensor, name: str, dtype=torch.float64) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+class Context:
+    """Binds the library to one CUDA device and a torch stream (default: current)."""
+
+    def __init__(self, device: int = 0, stream: torch.cuda.Stream | None = None):
+        """device = -1 gives a host-only context (symbolic analysis without a GPU)."""
+        self.lib = L.load()
+        self.device = device
+        if device >= 0:
+            self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+            handle = self.stream.cuda_stream
+        else:
+            self.stream, handle = None, 0
+        h = C.c_void_p()
+        rc = self.lib.ss_create(C.byref(h), device, C.c_void_p(handle))
+        if rc != L.SS_OK:
+            raise SisliceError(rc, "ss_create failed")
+        self.h = h
+
+    def check(self, rc: int, what: str, allow=()):
+        if rc != L.SS_OK and rc not in allow:
+            msg = self.lib.ss_last_error(self.h).decode(errors="replace")
+            raise SisliceError(rc, f"{what}: {msg}")
+        return rc
+
+    def sync(self):
+        self.check(self.lib.ss_sync(self.h), "ss_sync")
+
+    def analyze(self, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0) -> "Symbolic":
+        return analyze(self, rowptr, colind, nd_leaf)
+
+    def launch_count(self) -> int:
+        """Kernels launched by the library since it was loaded."""
+        return int(self.lib.ss_launch_count())
+
+    def profile(self, classes=()):
+        """Start per-class event timing of the named kernel classes (empty: stop)."""
+        mask = 0
+        for c in classes:
+            mask |= 1 << L.KERNEL_CLASSES.index(c)
+        self.check(self.lib.ss_profile(self.h, mask), "ss_profile")
+
+    def profile_query(self, cls: str):
+        """(launches, seconds) of a kernel class since profile() (synchronises)."""
+        n, t = C.c_int64(), C.c_double()
+        self.check(self.lib.ss_profile_query(self.h, L.KERNEL_CLASSES.index(cls), C.byref(n), C.byref(t)),
+                   "ss_profile_query")
+        return n.value, t.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ss_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def analyze(ctx: Context, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0) -> "Symbolic":
+    """Symbolic analysis of the full symmetric CSR pattern (host arrays)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    n = rowptr.size - 1
+    opt = L.ss_options()
+    opt.nd_leaf = nd_leaf
+    h = C.c_void_p()
+    ctx.check(ctx.lib.ss_analyze(ctx.h, n, _ptr(rowptr), _ptr(colind), C.byref(opt), C.byref(h)), "ss_analyze")
+    return Symbolic(ctx, h, n, int(rowptr[-1]))
+
+
+class Symbolic:
+    def __init__(self, ctx: Context, h, n: int, nnz: int):
+        self.ctx, self.h, self.n, self.nnz = ctx, h, n, nnz
+        inf = L.ss_symbolic_info()
+        ctx.check(ctx.lib.ss_symbolic_info_get(h, C.byref(inf)), "ss_symbolic_info_get")
+        self.info = {f: getattr(inf, f) for f, _ in L.ss_symbolic_info._fields_}
+
+    def validate(self):
+        """Check every device-side index of the analysis against its buffer (host only)."""
+        self.ctx.check(self.ctx.lib.ss_symbolic_validate(self.h), "ss_symbolic_validate")
+
+    def perm(self) -> np.ndarray:
+        p = np.empty(self.n, dtype=np.int32)
+        self.ctx.check(self.ctx.lib.ss_symbolic_perm(self.h, _ptr(p)), "ss_symbolic_perm")
+        return p
+
+    def factor(self, a_vals, b_vals, sigma, precision: str = "fp64", allow_singular: bool = False) -> "Factor":
+        return factor(self, a_vals, b_vals, sigma, precision, allow_singular)
+
+    def spmm(self, a_vals, b_vals, X, alpha=None, beta=None) -> torch.Tensor:
+        return spmm(self, a_vals, b_vals, X, alpha, beta)
+
+    def dos_estimate(self, a_vals, b_vals, steps: int, start: torch.Tensor):
+        return dos_estimate(self, a_vals, b_vals, steps, start)
+
+    def band_energy_grad(self, X, lam):
+        return band_energy_grad(self, X, lam)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.ss_symbolic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def factor(sym: Symbolic, a_vals, b_vals, sigma, precision: str = "fp64",
+           allow_singular: bool = False) -> "Factor":
+    """LDL^T of A - sigma_j B for every shift (one factor per shift)."""
+    ctx = sym.ctx
+    _dev(a_vals, "a_vals")
+    _dev(b_vals, "b_vals")
+    if a_vals.numel() != sym.nnz or b_vals.numel() != sym.nnz:
+        raise ValueError("value arrays must match the analysed pattern")
+    sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
+    prec = {"fp64": L.SS_FP64, "mixed": L.SS_MIXED}[precision]
+    h = C.c_void_p()
+    rc = ctx.lib.ss_factor(sym.h, _ptr(a_vals), _ptr(b_vals), _ptr(sig), sig.size, prec, C.byref(h))
+    ctx.check(rc, "ss_factor", allow=(L.SS_ERR_SINGULAR,) if allow_singular else ())
+    return Factor(sym, h, a_vals, b_vals, sig, precision, rc == L.SS_ERR_SINGULAR)
+
+
+@dataclass
+class ProbeResult:
+    """One spectral probe SP(sigma) = (sigma, Lambda, X, R) plus solver statistics."""
+    sigma: float
+    theta: np.ndarray           # k Ritz values, ascending
+    X: torch.Tensor             # N x k B-orthonormal Ritz vectors
+    resid: np.ndarray           # normalised residual norms
+    n_found: int                # Ritz values in (lo, hi]
+    iterations: int
+    refine_steps: int
+    converged: bool
+    max_resid_in_slice: float
+    seconds: float
+
+
+class Factor:
+    def __init__(self, sym, h, a_vals, b_vals, sigma, precision, singular):
+        self.sym, self.ctx, self.h = sym, sym.ctx, h
+        self.a_vals, self.b_vals = a_vals, b_vals        # kept alive: the library reads them
+        self.sigma, self.precision, self.singular = sigma, precision, singular
+
+    def inertia(self, j: int = 0):
+        """(n_neg, n_zero, n_pos, tiny_pivot) of A - sigma_j B."""
+        return inertia(self, j)
+
+    def solve(self, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
+        return solve(self, j, R, refine)
+
+    def slice_solve(self, j: int, lo: float, hi: float, V0: torch.Tensor, **kw) -> ProbeResult:
+        return slice_solve(self, j, lo, hi, V0, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.lib.ss_factor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def inertia(f: Factor, j: int = 0):
+    neg, zero, pos, tiny = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32()
+    f.ctx.check(f.ctx.lib.ss_inertia(f.h, j, C.byref(neg), C.byref(zero), C.byref(pos), C.byref(tiny)),
+                "ss_inertia")
+    return neg.value, zero.value, pos.value, bool(tiny.value)
+
+
+def solve(f: Factor, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
+    _dev(R, "R")
+    R2 = R if R.dim() == 2 else R[:, None]
+    X = torch.empty_like(R2)
+    f.ctx.check(f.ctx.lib.ss_solve(f.h, j, _ptr(R2), R2.shape[1], _ptr(X), refine), "ss_solve")
+    return X.view_as(R)
+
+
+def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: float = 1e-10,
+                max_iter: int = 200, check_every: int = 1, refine: int = 2, n_expect: int = 0,
+                allow_noconv: bool = False) -> ProbeResult:
+    """Shift-invert subspace iteration for shift j, converged on Ritz values in (lo, hi]."""
+    _dev(V0, "V0")
+    n, k = V0.shape
+    opts = L.ss_solve_opts()
+    opts.driver = L.SS_SUBSPACE
+    opts.max_iter, opts.check_every, opts.refine, opts.tol, opts.n_expect = max_iter, check_every, refine, tol, n_expect
+    lam = np.empty(k)
+    res = np.empty(k)
+    X = torch.empty_like(V0)
+    nf = C.c_int32()
+    st = L.ss_probe_stats()
+    rc = f.ctx.lib.ss_slice_solve(f.h, j, lo, hi, C.byref(opts), _ptr(V0), k, _ptr(lam), _ptr(X), _ptr(res),
+                                  C.byref(nf), C.byref(st))
+    f.ctx.check(rc, "ss_slice_solve", allow=(L.SS_ERR_NOCONV,) if allow_noconv else ())
+    return ProbeResult(float(f.sigma[j]), lam, X, res, nf.value, st.iterations, st.refine_steps,
+                       bool(st.converged), st.max_resid_in_slice, st.seconds)
+
+
+def dos_estimate(sym: Symbolic, a_vals, b_vals, steps: int, start: torch.Tensor):
+    """Lanczos DOS runs: list of (theta, zeta2) per start vector (columns of start)."""
+    _dev(start, "start")
+    nv = start.shape[1]
+    th = np.zeros(steps * nv)
+    z2 = np.zeros(steps * nv)
+    m = np.zeros(nv, dtype=np.int32)
+    sym.ctx.check(sym.ctx.lib.ss_dos_estimate(sym.h, _ptr(a_vals), _ptr(b_vals), steps, nv, _ptr(start),
+                                              _ptr(th), _ptr(z2), _ptr(m)), "ss_dos_estimate")
+    return [(th[c * steps:c * steps + m[c]].copy(), z2[c * steps:c * steps + m[c]].copy()) for c in range(nv)]
+
+
+def spmm(sym: Symbolic, a_vals, b_vals, X, alpha=None, beta=None) -> torch.Tensor:
+    """Y = (alpha_j A + beta_j B) X (alpha defaults to 1, beta to 0)."""
+    _dev(X, "X")
+    k = X.shape[1]
+    dev = X.device
+    al = None if alpha is None else torch.as_tensor(np.broadcast_to(alpha, (k,)), dtype=torch.float64, device=dev).contiguous()
+    be = None if beta is None else torch.as_tensor(np.broadcast_to(beta, (k,)), dtype=torch.float64, device=dev).contiguous()
+    Y = torch.empty_like(X)
+    sym.ctx.check(sym.ctx.lib.ss_spmm(sym.h, _ptr(a_vals), _ptr(b_vals), _ptr(al), _ptr(be), _ptr(X), k, _ptr(Y)),
+                  "ss_spmm")
+    return Y
+
+
+def band_energy_grad(sym: Symbolic, X: torch.Tensor, lam: torch.Tensor):
+    """Per-stored-entry dE/dA and dE/dB for E = sum(lam), X B-orthonormal (N x n_e)."""
+    _dev(X, "X")
+    lam = _dev(lam.contiguous(), "lambda")
+    ga = torch.empty(sym.nnz, dtype=torch.float64, device=X.device)
+    gb = torch.empty_like(ga)
+    sym.ctx.check(sym.ctx.lib.ss_band_energy_grad(sym.h, _ptr(X), _ptr(lam), X.shape[1], _ptr(ga), _ptr(gb)),
+                  "ss_band_energy_grad")
+    return ga, gb
+
+
+class BandEnergy(torch.autograd.Function):
+    """E = sum of the n_e eigenvalues returned by ``solver(a_vals, b_vals)``.
+
+    ``solver`` returns (lam [n_e] CUDA float64, X [N, n_e] B-orthonormal).  The backward
+    pass is the SDDMM kernel of ``band_energy_grad`` (Hellmann-Feynman): dE/dA sampled
+    on the pattern is X X^T, dE/dB is -X Lambda X^T."""
+
+    @staticmethod
+    def forward(ctx, a_vals, b_vals, sym, solver):
+        lam, X = solver(a_vals, b_vals)
+        ctx.sym = sym
+        ctx.save_for_backward(X, lam)
+        return lam.sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        X, lam = ctx.saved_tensors
+        ga, gb = band_energy_grad(ctx.sym, X.contiguous(), lam)
+        return g * ga, g * gb, None, None

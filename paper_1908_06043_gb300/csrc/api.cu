@@ -1,0 +1,531 @@
+// C ABI: context, symbolic upload, numeric factorisation, inertia, solves, SpMM, gradient.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "factor_kernels.cuh"
+#include "internal.h"
+#include "solve_kernels.cuh"
+#include "sparse_kernels.cuh"
+
+using namespace ssk;
+
+// ------------------------------------------------------------------ launch accounting
+std::atomic<int64_t> g_ss_launches{0};
+
+size_t ss_prof_begin(ss_ctx *ctx, int cls) {
+    size_t slot = 2 * ctx->ev_used.size();
+    while (ctx->ev_pool.size() < slot + 2) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ctx->ev_pool.push_back(e);
+    }
+    ctx->ev_used.push_back({cls, slot});
+    cudaEventRecord(ctx->ev_pool[slot], ctx->stream);
+    return slot;
+}
+
+void ss_prof_end(ss_ctx *ctx, int cls, size_t slot) {
+    (void)cls;
+    cudaEventRecord(ctx->ev_pool[slot + 1], ctx->stream);
+}
+
+extern "C" int64_t ss_launch_count(void) { return g_ss_launches.load(); }
+
+static void prof_collect(ss_ctx *ctx) {
+    for (auto &u : ctx->ev_used) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ctx->ev_pool[u.second], ctx->ev_pool[u.second + 1]) == cudaSuccess) {
+            ctx->prof_launches[u.first] += 1;
+            ctx->prof_seconds[u.first] += ms * 1e-3;
+        }
+    }
+    ctx->ev_used.clear();
+}
+
+extern "C" ss_status ss_profile(ss_ctx *ctx, uint32_t mask) {
+    if (!ctx) return SS_ERR_ARG;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->ev_used.clear();
+    for (int c = 0; c < SS_K_COUNT; ++c) { ctx->prof_launches[c] = 0; ctx->prof_seconds[c] = 0.0; }
+    ctx->prof_mask = mask;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds) {
+    if (!ctx || cls < 0 || cls >= SS_K_COUNT) return SS_ERR_ARG;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_collect(ctx);
+    if (launches) *launches = ctx->prof_launches[cls];
+    if (seconds) *seconds = ctx->prof_seconds[cls];
+    return SS_OK;
+}
+
+// ------------------------------------------------------------------ context
+extern "C" ss_status ss_create(ss_ctx **ctx, int32_t device, void *cuda_stream) {
+    if (!ctx) return SS_ERR_ARG;
+    *ctx = nullptr;
+    ss_ctx *c = new (std::nothrow) ss_ctx();
+    if (!c) return SS_ERR_OOM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (device == -1) {            // host-only context: symbolic analysis without a GPU
+        *ctx = c;
+        return SS_OK;
+    }
+    if (device < 0 || cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return SS_ERR_CUDA;
+    }
+    *ctx = c;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_destroy(ss_ctx *ctx) {
+    delete ctx;
+    return SS_OK;
+}
+
+extern "C" const char *ss_last_error(const ss_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" ss_status ss_sync(ss_ctx *ctx) {
+    if (!ctx) return SS_ERR_ARG;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return SS_OK;
+}
+
+// ------------------------------------------------------------------ symbolic upload
+template <typename V>
+static int upload_vec(ss_ctx *ctx, const std::vector<V> &h, V **d) {
+    *d = nullptr;
+    if (h.empty()) return SS_OK;
+    SS_CUDA_TRY(ctx, cudaMalloc((void **)d, sizeof(V) * h.size()));
+    SS_CUDA_TRY(ctx, cudaMemcpy(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice));
+    return SS_OK;
+}
+
+int ss_symbolic_upload(ss_symbolic *s) {
+    ss_ctx *ctx = s->ctx;
+    if (ctx->device < 0) return SS_OK;     // host-only context
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    int rc;
+#define UP(h, d) if ((rc = upload_vec(ctx, h, &d)) != SS_OK) return rc
+    UP(s->rowptr, s->d_rowptr);
+    UP(s->colind, s->d_colind);
+    UP(s->iperm, s->d_iperm);
+    UP(s->perm, s->d_perm);
+    UP(s->idx, s->d_idx);
+    UP(s->asm_e, s->d_asm_e);
+    UP(s->asm_dest, s->d_asm_dest);
+    UP(s->relmap, s->d_relmap);
+    UP(s->ext_tasks, s->d_ext_tasks);
+    UP(s->panels, s->d_panels);
+    UP(s->tasks, s->d_tasks);
+    UP(s->solve_panels, s->d_solve_panels);
+    UP(s->solve_tile_pre, s->d_solve_tile_pre);
+    std::vector<int32_t> col_panel(s->n);
+    for (size_t p = 0; p < s->panels.size(); ++p)
+        for (int i = 0; i < s->panels[p].w; ++i) col_panel[s->panels[p].g0 + i] = (int32_t)p;
+    UP(col_panel, s->d_col_panel);
+#undef UP
+    return SS_OK;
+}
+
+void ss_symbolic_free_device(ss_symbolic *s) {
+    void *ptrs[] = {s->d_rowptr, s->d_colind, s->d_iperm, s->d_perm, s->d_idx, s->d_asm_e,
+                    s->d_asm_dest, s->d_relmap, s->d_ext_tasks, s->d_panels, s->d_tasks,
+                    s->d_solve_panels, s->d_solve_tile_pre, s->d_col_panel};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    s->d_rowptr = nullptr; s->d_colind = nullptr; s->d_iperm = nullptr; s->d_perm = nullptr;
+    s->d_idx = nullptr; s->d_asm_e = nullptr; s->d_asm_dest = nullptr; s->d_relmap = nullptr;
+    s->d_ext_tasks = nullptr; s->d_panels = nullptr; s->d_tasks = nullptr;
+    s->d_solve_panels = nullptr; s->d_solve_tile_pre = nullptr; s->d_col_panel = nullptr;
+}
+
+// ------------------------------------------------------------------ norms
+__global__ void k_row_abs_max(int64_t n, const int64_t *__restrict__ rowptr, const double *__restrict__ v,
+                              unsigned long long *out) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (r < n)
+        for (int64_t p = rowptr[r]; p < rowptr[r + 1]; ++p) s += fabs(v[p]);
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+int ss_norm1(ss_symbolic *s, const double *vals, double *out) {
+    ss_ctx *ctx = s->ctx;
+    unsigned long long *d = nullptr, h = 0;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&d, sizeof(unsigned long long), ctx->stream));
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(d, 0, sizeof(unsigned long long), ctx->stream));
+    ss_launch(ctx, SS_K_MISC, k_row_abs_max, (unsigned)((s->n + 255) / 256), 256, 0, ctx->stream, s->n, s->d_rowptr, vals, d);
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    SS_CUDA_TRY(ctx, cudaFreeAsync(d, ctx->stream));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double v;
+    std::memcpy(&v, &h, sizeof(v));
+    *out = v;
+    return SS_OK;
+}
+
+// ------------------------------------------------------------------ numeric factorisation
+template <typename T>
+static void set_smem_attrs() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(k_diag_bk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagSmem);
+    cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem<T>());
+    cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_smem<T>());
+    cudaFuncSetAttribute(k_fwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_solve_smem<T>());
+    cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_solve_smem<T>());
+    cudaFuncSetAttribute(k_fwd_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_solve_smem<T>());
+    cudaFuncSetAttribute(k_bwd_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_solve_smem<T>());
+}
+
+template <typename T>
+static int factor_run(ss_numeric *f) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    set_smem_attrs<T>();
+    const int ns = f->n_shift;
+    const int64_t npan = (int64_t)s->panels.size();
+    std::vector<ShiftPtrs<T>> hp(ns);
+    T *mt = nullptr, *wb = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mt, sizeof(T) * std::max<int64_t>(1, (int64_t)s->mt_max * NB * NB) * ns, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wb, sizeof(T) * std::max<int64_t>(1, s->wbuf_max) * ns, st));
+    for (int j = 0; j < ns; ++j) {
+        ShiftPtrs<T> &p = hp[j];
+        p.arena = (T *)f->arena[j];
+        p.linv = f->linv[j];
+        p.dblk = f->dblk[j];
+        p.piv = f->piv[j];
+        p.mt = mt + (int64_t)j * s->mt_max * NB * NB;
+        p.wbuf = wb + (int64_t)j * std::max<int64_t>(1, s->wbuf_max);
+        p.counts = f->d_counts + 5 * j;
+        p.sigma = f->sigma[j];
+        p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
+        p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
+    }
+    ShiftPtrs<T> *dp = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dp, sizeof(ShiftPtrs<T>) * ns, st));
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
+    std::vector<unsigned long long> init(5 * ns, 0);
+    for (int j = 0; j < ns; ++j) init[5 * j + 4] = 0x7ff0000000000000ull;   // +inf bits
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->d_counts, init.data(), sizeof(unsigned long long) * 5 * ns,
+                                     cudaMemcpyHostToDevice, st));
+    for (int32_t l = 0; l < s->nlev; ++l) {
+        const int64_t b0 = s->lev_arena_begin[l], b1 = s->lev_arena_end[l];
+        for (int j = 0; j < ns; ++j)
+            SS_CUDA_TRY(ctx, cudaMemsetAsync((T *)f->arena[j] + b0, 0, sizeof(T) * (b1 - b0), st));
+        const int64_t a0 = s->asm_lev_off[l], acount = s->asm_lev_off[l + 1] - a0;
+        if (acount > 0) {
+            unsigned gx = (unsigned)std::min<int64_t>((acount + 255) / 256, 8192);
+            ss_launch(ctx, SS_K_ASSEMBLE, k_assemble<T>, dim3(gx, ns), 256, 0, st, acount, s->d_asm_e + a0, s->d_asm_dest + a0,
+                                                         f->a_vals, f->b_vals, dp);
+        }
+        for (int32_t q = s->lev_ext_pass_off[l]; q < s->lev_ext_pass_off[l + 1]; ++q) {
+            const ExtendPass &ps = s->ext_pass[q];
+            ss_launch(ctx, SS_K_EXTEND_ADD, k_extend_add<T>, dim3(ps.cols, ns), 128, 0, st, s->d_ext_tasks + ps.task_off, ps.count,
+                                                               s->d_relmap, dp);
+        }
+        for (int32_t q = s->lev_step_off[l]; q < s->lev_step_off[l + 1]; ++q) {
+            const StepDesc &sd = s->steps[q];
+            const StepTask *tk = s->d_tasks + sd.task_off;
+            ss_launch(ctx, SS_K_DIAG_BK, k_diag_bk<T>, dim3(sd.count, ns), 256, kDiagSmem, st, tk, dp, 0);
+            if (sd.tiles4 > 0)
+                ss_launch(ctx, SS_K_PANEL, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count, dp);
+            if (sd.tiles3 > 0)
+                ss_launch(ctx, SS_K_SCHUR, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count, dp);
+        }
+    }
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    SS_CUDA_TRY(ctx, cudaFreeAsync(dp, st));
+    SS_CUDA_TRY(ctx, cudaFreeAsync(mt, st));
+    SS_CUDA_TRY(ctx, cudaFreeAsync(wb, st));
+    (void)npan;
+    return SS_OK;
+}
+
+static void factor_free(ss_numeric *f) {
+    for (void *p : f->arena) if (p) cudaFree(p);
+    for (double *p : f->linv) if (p) cudaFree(p);
+    for (double *p : f->dblk) if (p) cudaFree(p);
+    for (int32_t *p : f->piv) if (p) cudaFree(p);
+    if (f->d_counts) cudaFree(f->d_counts);
+    f->arena.clear(); f->linv.clear(); f->dblk.clear(); f->piv.clear();
+    f->d_counts = nullptr;
+}
+
+int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
+                     int32_t n_shift, int32_t precision, ss_numeric **out) {
+    ss_ctx *ctx = sym->ctx;
+    *out = nullptr;
+    ss_numeric *f = new (std::nothrow) ss_numeric();
+    if (!f) return ctx->set_error(SS_ERR_OOM, "ss_factor: host allocation failed");
+    f->sym = sym;
+    f->precision = precision;
+    f->n_shift = n_shift;
+    f->sigma.assign(sigma, sigma + n_shift);
+    f->a_vals = a_vals;
+    f->b_vals = b_vals;
+    int rc = SS_OK;
+    const size_t esz = precision == SS_MIXED ? sizeof(float) : sizeof(double);
+    const int64_t npan = (int64_t)sym->panels.size();
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if ((rc = ss_norm1(sym, a_vals, &f->norm_a1)) != SS_OK) { delete f; return rc; }
+    if ((rc = ss_norm1(sym, b_vals, &f->norm_b1)) != SS_OK) { delete f; return rc; }
+    f->arena.assign(n_shift, nullptr);
+    f->linv.assign(n_shift, nullptr);
+    f->dblk.assign(n_shift, nullptr);
+    f->piv.assign(n_shift, nullptr);
+    cudaError_t e = cudaMalloc((void **)&f->d_counts, sizeof(unsigned long long) * 5 * n_shift);
+    for (int j = 0; j < n_shift && e == cudaSuccess; ++j) {
+        e = cudaMalloc(&f->arena[j], esz * std::max<int64_t>(1, sym->arena));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&f->linv[j], sizeof(double) * NB * NB * npan);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&f->dblk[j], sizeof(double) * 2 * NB * npan);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&f->piv[j], sizeof(int32_t) * NB * npan);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        factor_free(f);
+        delete f;
+        return ctx->set_error(e == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA,
+                              std::string("ss_factor: device allocation failed: ") + cudaGetErrorString(e));
+    }
+    rc = precision == SS_MIXED ? factor_run<float>(f) : factor_run<double>(f);
+    if (rc == SS_OK) rc = ss_factor_fetch_counts(f);
+    if (rc != SS_OK && rc != SS_ERR_SINGULAR) {
+        factor_free(f);
+        delete f;
+        return rc;
+    }
+    *out = f;
+    return rc;
+}
+
+int ss_factor_fetch_counts(ss_numeric *f) {
+    ss_ctx *ctx = f->sym->ctx;
+    f->h_counts.assign(5 * f->n_shift, 0);
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->h_counts.data(), f->d_counts,
+                                     sizeof(unsigned long long) * 5 * f->n_shift, cudaMemcpyDeviceToHost,
+                                     ctx->stream));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    f->counts_valid = true;
+    for (int j = 0; j < f->n_shift; ++j)
+        if (f->h_counts[5 * j + 3]) {
+            return ctx->set_error(SS_ERR_SINGULAR, "ss_factor: a pivot fell below the singularity "
+                                                   "threshold for shift " + std::to_string(j));
+        }
+    return SS_OK;
+}
+
+extern "C" ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                               const double *sigma, int32_t n_shift, int32_t precision, ss_numeric **out) {
+    if (!sym) return SS_ERR_ARG;
+    ss_ctx *ctx = sym->ctx;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "ss_factor: host-only context");
+    if (!out || !a_vals || !b_vals || !sigma || n_shift <= 0 || n_shift > 65535 ||
+        (precision != SS_FP64 && precision != SS_MIXED))
+        return ctx->set_error(SS_ERR_ARG, "ss_factor: bad argument");
+    for (int j = 0; j < n_shift; ++j)
+        if (!std::isfinite(sigma[j])) return ctx->set_error(SS_ERR_ARG, "ss_factor: non-finite shift");
+    try {
+        return ss_factor_create(sym, a_vals, b_vals, sigma, n_shift, precision, out);
+    } catch (const std::bad_alloc &) {
+        return ctx->set_error(SS_ERR_OOM, "ss_factor: host allocation failed");
+    }
+}
+
+extern "C" ss_status ss_factor_destroy(ss_numeric *f) {
+    if (!f) return SS_OK;
+    factor_free(f);
+    delete f;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_inertia(const ss_numeric *f, int32_t j, int64_t *n_neg, int64_t *n_zero,
+                                int64_t *n_pos, int32_t *tiny) {
+    if (!f || j < 0 || j >= f->n_shift || !f->counts_valid) return SS_ERR_ARG;
+    if (n_neg) *n_neg = (int64_t)f->h_counts[5 * j + 0];
+    if (n_zero) *n_zero = (int64_t)f->h_counts[5 * j + 1];
+    if (n_pos) *n_pos = (int64_t)f->h_counts[5 * j + 2];
+    if (tiny) *tiny = f->h_counts[5 * j + 3] ? 1 : 0;
+    return SS_OK;
+}
+
+double ss_factor_min_pivot_ratio(const ss_numeric *f, int32_t j) {
+    double v;
+    std::memcpy(&v, &f->h_counts[5 * j + 4], sizeof(v));
+    return v;
+}
+
+// ------------------------------------------------------------------ solves
+template <typename T>
+int solve_permuted(ss_numeric *f, int j, T *b, int k) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    set_smem_attrs<T>();
+    const T *arena = (const T *)f->arena[j];
+    const int nchunk = (k + KC - 1) / KC;
+    const int nlev = (int)s->solve_levels.size();
+    for (int L = 0; L < nlev; ++L) {
+        const SolveLevel &sl = s->solve_levels[L];
+        const int32_t *lp = s->d_solve_panels + sl.panel_off;
+        ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, lp, s->d_panels, f->linv[j],
+                                                                               f->piv[j], b, k);
+        if (sl.row_tiles > 0)
+            ss_launch(ctx, SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
+                lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k);
+    }
+    int32_t maxc = 0;
+    for (const SolveLevel &sl : s->solve_levels) maxc = std::max(maxc, sl.count);
+    T *z = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&z, sizeof(T) * (int64_t)maxc * NB * k, st));
+    for (int L = nlev - 1; L >= 0; --L) {
+        const SolveLevel &sl = s->solve_levels[L];
+        const int32_t *lp = s->d_solve_panels + sl.panel_off;
+        if (sl.row_tiles > 0) {
+            SS_CUDA_TRY(ctx, cudaMemsetAsync(z, 0, sizeof(T) * (int64_t)sl.count * NB * k, st));
+            ss_launch(ctx, SS_K_BWD_GATHER, k_bwd_gather<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
+                lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k, z);
+        }
+        ss_launch(ctx, SS_K_BWD_DIAG, k_bwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, 
+            lp, s->d_panels, f->linv[j], f->dblk[j], f->piv[j], z, sl.row_tiles > 0 ? 1 : 0, b, k);
+    }
+    SS_CUDA_TRY(ctx, cudaFreeAsync(z, st));
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+template int solve_permuted<double>(ss_numeric *, int, double *, int);
+template int solve_permuted<float>(ss_numeric *, int, float *, int);
+
+__global__ void k_axpy_sub(int64_t tot, const double *__restrict__ R, const double *__restrict__ Y,
+                           double *__restrict__ out) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < tot) out[q] = R[q] - Y[q];
+}
+
+__global__ void k_fill_const(int k, double v, double *x) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < k) x[c] = v;
+}
+
+int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
+                const double *X, int k, double *Y) {
+    ss_ctx *ctx = s->ctx;
+    const int64_t threads = s->n * 32;
+    const unsigned grid = (unsigned)((threads + 255) / 256);
+    if (k >= 16)
+        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_cols, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, alpha, beta, X, k, Y);
+    else if (k <= 4)
+        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<4>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, alpha, beta, X, k, Y);
+    else
+        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<16>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, alpha, beta, X, k, Y);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+// X = (A - sigma B)^-1 R in the original order; FP64 R, X (may alias).
+int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    const int64_t tot = s->n * k;
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    int rc;
+    if (steps_done) *steps_done = 0;
+    if (f->precision == SS_FP64) {
+        double *w = nullptr;
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&w, sizeof(double) * tot, st));
+        ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm, R, w, 0);
+        if ((rc = solve_permuted<double>(f, j, w, k)) != SS_OK) return rc;
+        ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm, w, X, 1);
+        SS_CUDA_TRY(ctx, cudaFreeAsync(w, st));
+        SS_CUDA_TRY(ctx, cudaGetLastError());
+        return SS_OK;
+    }
+    // mixed: FP32 solves inside FP64 iterative refinement, X_0 = 0
+    float *wf = nullptr;
+    double *r = nullptr, *y = nullptr, *al = nullptr, *be = nullptr, *x = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wf, sizeof(float) * tot, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&r, sizeof(double) * tot, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&y, sizeof(double) * tot, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&x, sizeof(double) * tot, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&al, sizeof(double) * 2 * k, st));
+    be = al + k;
+    ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, 1.0, al);
+    ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, -f->sigma[j], be);
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, sizeof(double) * tot, st));
+    for (int it = 0; it <= refine; ++it) {
+        const double *rhs = R;
+        if (it > 0) {
+            if ((rc = spmm_launch(s, f->a_vals, f->b_vals, al, be, x, k, y)) != SS_OK) return rc;
+            ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, y, r);
+            rhs = r;
+        }
+        ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<float, double>, g, 256, 0, st, s->n, k, s->d_perm, rhs, wf, 0);
+        if ((rc = solve_permuted<float>(f, j, wf, k)) != SS_OK) return rc;
+        ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, float>, g, 256, 0, st, s->n, k, s->d_perm, wf, x, 2);
+        if (steps_done && it > 0) (*steps_done)++;
+    }
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(X, x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+    cudaFreeAsync(wf, st);
+    cudaFreeAsync(r, st);
+    cudaFreeAsync(y, st);
+    cudaFreeAsync(x, st);
+    cudaFreeAsync(al, st);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+extern "C" ss_status ss_solve(ss_numeric *f, int32_t j, const double *R, int32_t k, double *X, int32_t refine) {
+    if (!f) return SS_ERR_ARG;
+    ss_ctx *ctx = f->sym->ctx;
+    if (j < 0 || j >= f->n_shift || !R || !X || k <= 0 || refine < 0)
+        return ctx->set_error(SS_ERR_ARG, "ss_solve: bad argument");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return solve_apply(f, j, R, k, X, refine, nullptr);
+}
+
+extern "C" ss_status ss_spmm(ss_symbolic *s, const double *a, const double *b, const double *alpha,
+                             const double *beta, const double *X, int32_t k, double *Y) {
+    if (!s) return SS_ERR_ARG;
+    ss_ctx *ctx = s->ctx;
+    if (ctx->device < 0 || !a || !X || !Y || k <= 0 || (beta && !b))
+        return ctx->set_error(SS_ERR_ARG, "ss_spmm: bad argument or host-only context");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return spmm_launch(s, a, b ? b : a, alpha, beta, X, k, Y);
+}
+
+extern "C" ss_status ss_band_energy_grad(ss_symbolic *s, const double *X, const double *lambda, int32_t n_e,
+                                         double *grad_a, double *grad_b) {
+    if (!s) return SS_ERR_ARG;
+    ss_ctx *ctx = s->ctx;
+    if (ctx->device < 0 || !X || !lambda || n_e <= 0 || (!grad_a && !grad_b))
+        return ctx->set_error(SS_ERR_ARG, "ss_band_energy_grad: bad argument or host-only context");
+    const size_t smem = sizeof(double) * 2 * (size_t)n_e;
+    if (smem > 220 * 1024) return ctx->set_error(SS_ERR_ARG, "ss_band_energy_grad: n_e too large (max 14080)");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(sss::k_sddmm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr = true;
+    }
+    ss_launch(ctx, SS_K_SDDMM, sss::k_sddmm, (unsigned)s->n, 256, smem, ctx->stream, s->n, s->d_rowptr, s->d_colind, X, lambda, n_e,
+                                                             grad_a, grad_b);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}

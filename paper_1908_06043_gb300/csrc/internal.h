@@ -1,0 +1,203 @@
+// Internal structures of the slice-solve library (host side).  Not part of the ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sislice.h"
+
+struct ss_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    std::string err;
+    // per-class launch timing (ss_profile): event pairs recorded around launches
+    uint32_t prof_mask = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_used;     // (class, index of the start event)
+    int64_t prof_launches[SS_K_COUNT] = {};
+    double prof_seconds[SS_K_COUNT] = {};
+    int set_error(int code, const std::string &msg) {
+        err = msg;
+        return code;
+    }
+    ~ss_ctx() {
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    }
+};
+
+extern std::atomic<int64_t> g_ss_launches;
+size_t ss_prof_begin(ss_ctx *ctx, int cls);
+void ss_prof_end(ss_ctx *ctx, int cls, size_t slot);
+
+#ifdef __CUDACC__
+// Every kernel of the library is launched through here: it counts the launch and, when
+// the class is being profiled, brackets it with events on the launching stream.
+template <typename... KArgs, typename... Args>
+inline void ss_launch(ss_ctx *ctx, int cls, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                      cudaStream_t st, Args &&...args) {
+    g_ss_launches.fetch_add(1, std::memory_order_relaxed);
+    if (ctx->prof_mask & (1u << cls)) {
+        size_t slot = ss_prof_begin(ctx, cls);
+        kern<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+        ss_prof_end(ctx, cls, slot);
+    } else {
+        kern<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    }
+}
+#endif
+
+// One panel of the blocked front factorisation: columns [k0, k0+w) of front `sn`.
+// The panel's L rows below its diagonal block are front rows [k0+w, m), whose global
+// (permuted) indices are idx[idx_off + k0 + w ...].
+struct PanelDesc {
+    int64_t front_off;   // arena offset (entries) of the front, column-major m x m
+    int64_t idx_off;     // offset of the front's global index list in idx
+    int32_t m;           // front dimension
+    int32_t k0;          // first front column of the panel
+    int32_t w;           // panel width (<= nb)
+    int32_t g0;          // global (permuted) index of the panel's first column
+    int32_t sn;          // owning supernode
+    int32_t pad;
+};
+
+// One front taking part in factor step (level, t): panel `panel` is eliminated and
+// the trailing front [k0+w, m) x [k0+w, m) is updated.
+struct StepTask {
+    int64_t front_off;
+    int64_t wbuf_off;    // offset of this task's W = L21 D block (r x w, col-major) in W scratch
+    int32_t m, k0, w, r; // r = m - k0 - w
+    int32_t panel;
+    int32_t mt_slot;     // slot of the w x w transform in the Mt scratch
+    int32_t tiles4_pre;  // exclusive prefix of panel-transform row tiles
+    int32_t tiles3_pre;  // exclusive prefix of Schur-update tiles
+};
+
+struct StepDesc {
+    int64_t task_off;    // into tasks
+    int32_t count;       // fronts in this step
+    int32_t tiles4, tiles3;
+    int32_t level;
+};
+
+// Child -> parent extend-add unit: child front contribution block (rows [ncol, m))
+// added into the parent front through relmap.
+struct ExtendTask {
+    int64_t child_off, parent_off;
+    int64_t rel_off;     // into relmap (length nr)
+    int32_t child_m, child_ncol, parent_m, col_pre;  // col_pre: exclusive prefix of columns
+};
+
+struct ExtendPass {     // one non-conflicting pass (the q-th child of each parent)
+    int64_t task_off;
+    int32_t count, cols;
+};
+
+struct SolveLevel {      // panels whose forward step can run together
+    int64_t panel_off;   // into solve_panels
+    int32_t count;
+    int32_t row_tiles;   // total row tiles (64 rows) of the panels' below-diagonal rows
+};
+
+struct ss_symbolic {
+    ss_ctx *ctx = nullptr;
+    int64_t n = 0, nnz = 0;
+    int nb = 64;
+    std::vector<int32_t> perm, iperm;        // perm[new] = old, iperm[old] = new
+    std::vector<int64_t> rowptr;             // host copy of the pattern
+    std::vector<int32_t> colind;
+
+    int32_t nsn = 0;
+    std::vector<int32_t> sn_first;           // nsn + 1
+    std::vector<int32_t> sn_parent, sn_nrow, sn_level;
+    std::vector<int64_t> sn_idx_off;         // nsn + 1
+    std::vector<int32_t> idx;                // per supernode: [its columns, its rows]
+    std::vector<int64_t> front_off;          // arena offsets (level-ordered)
+    int64_t arena = 0;
+    int32_t nlev = 0;
+    std::vector<int64_t> lev_arena_begin, lev_arena_end;   // arena range per level
+
+    // assembly of the original entries, grouped by level
+    std::vector<int64_t> asm_lev_off;        // nlev + 1
+    std::vector<int32_t> asm_e;              // CSR entry index
+    std::vector<int64_t> asm_dest;           // arena offset
+
+    std::vector<int32_t> relmap;             // child rows -> parent front positions
+    std::vector<ExtendTask> ext_tasks;
+    std::vector<ExtendPass> ext_pass;
+    std::vector<int32_t> lev_ext_pass_off;   // nlev + 1, into ext_pass
+
+    std::vector<PanelDesc> panels;
+    std::vector<StepTask> tasks;
+    std::vector<StepDesc> steps;
+    std::vector<int32_t> lev_step_off;       // nlev + 1, into steps
+    int64_t wbuf_max = 0;                    // max W scratch entries over steps
+    int32_t mt_max = 0;                      // max fronts in one step
+
+    std::vector<int32_t> solve_panels;       // panel ids grouped by solve level
+    std::vector<SolveLevel> solve_levels;
+    std::vector<int32_t> solve_tile_pre;     // per solve_panels entry: exclusive row-tile prefix
+
+    ss_symbolic_info info{};
+
+    // device mirrors
+    int64_t *d_rowptr = nullptr;
+    int32_t *d_colind = nullptr;
+    int32_t *d_iperm = nullptr;              // old -> new
+    int32_t *d_perm = nullptr;               // new -> old
+    int32_t *d_idx = nullptr;
+    int32_t *d_asm_e = nullptr;
+    int64_t *d_asm_dest = nullptr;
+    int32_t *d_relmap = nullptr;
+    ExtendTask *d_ext_tasks = nullptr;
+    PanelDesc *d_panels = nullptr;
+    StepTask *d_tasks = nullptr;
+    int32_t *d_solve_panels = nullptr;
+    int32_t *d_solve_tile_pre = nullptr;
+    int32_t *d_col_panel = nullptr;          // permuted column -> panel
+};
+
+struct ss_numeric {
+    ss_symbolic *sym = nullptr;
+    int precision = SS_FP64;
+    int32_t n_shift = 0;
+    std::vector<double> sigma;
+    const double *a_vals = nullptr, *b_vals = nullptr;   // caller-owned device arrays
+    double norm_a1 = 0, norm_b1 = 0;
+    // per shift
+    std::vector<void *> arena;            // front arena (double or float)
+    std::vector<double *> linv;           // npanels * nb * nb, L11^-1 of each panel
+    std::vector<double *> dblk;           // npanels * nb * 2: D diagonal, D sub-diagonal
+    std::vector<int32_t *> piv;           // npanels * nb: local pivot order
+    unsigned long long *d_counts = nullptr;   // per shift: neg, zero, pos, tiny
+    std::vector<unsigned long long> h_counts;
+    bool counts_valid = false;
+};
+
+// helpers implemented in the .cu files
+int ss_symbolic_upload(ss_symbolic *s);
+void ss_symbolic_free_device(ss_symbolic *s);
+int ss_factor_fetch_counts(ss_numeric *f);
+int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
+                     int32_t n_shift, int32_t precision, ss_numeric **out);
+double ss_factor_min_pivot_ratio(const ss_numeric *f, int32_t j);
+int ss_norm1(ss_symbolic *s, const double *vals, double *out);
+// in-place solve (A - sigma_j B) x = b of a permuted-order N x k block
+template <typename T> int solve_permuted(ss_numeric *f, int j, T *b, int k);
+// X = (A - sigma_j B)^-1 R in the original order (FP64 in/out, refinement for mixed)
+int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done);
+int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
+                const double *X, int k, double *Y);
+
+#define SS_CUDA_TRY(ctx, call)                                                           \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return (ctx)->set_error(e_ == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA, \
+                                    std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)

@@ -1,0 +1,235 @@
+// Level-scheduled panel triangular solves with the multifrontal factor (Alg. 2 step 3:
+// V <- L^-T D^-1 L^-1 (B V)).  Right-hand sides are N x k row-major in the permuted
+// (analysis) order.  For a panel with pivot order P, unit lower L11 (its inverse stored),
+// block-diagonal D and below-diagonal rows L21 (front rows [k0+w, m)):
+//   forward:  y = L11^-1 P b1 (stored in place of b1),  b2 -= L21 y       (push, atomics)
+//   backward: z = L21^T x2 (gathered, atomics into a per-panel buffer),
+//             x1 = P^T L11^-T (D^-1 y - z)                                 (scatter)
+// Panels in one solve level are independent; levels run in order (forward) or reverse
+// order (backward).  T is the factor / right-hand-side type.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace ssk {
+
+constexpr int KC = 32;     // right-hand-side columns per block
+// dynamic shared memory of the solve kernels
+template <typename T> constexpr size_t diag_solve_smem() { return sizeof(T) * NB * ((KC + 1) + (NB + 1)); }
+template <typename T> constexpr size_t tile_solve_smem() { return sizeof(T) * (NB * (TR + 1) + TR * (KC + 1)); }
+
+__device__ __forceinline__ void atomic_add_t(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_t(float *p, float v) { atomicAdd(p, v); }
+
+// forward diagonal step: block (panel in level, rhs chunk)
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_diag(const int32_t *__restrict__ lvl_panels,
+                                                   const PanelDesc *__restrict__ panels,
+                                                   const double *__restrict__ linv,
+                                                   const int32_t *__restrict__ piv, T *b, int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*Y)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw);
+    T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KC + 1));
+    const int p = lvl_panels[blockIdx.x];
+    const PanelDesc pd = panels[p];
+    const int w = pd.w, c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const int tid = threadIdx.x;
+    for (int q = tid; q < w * KC; q += 256) {
+        int i = q / KC, c = q % KC;
+        int src = piv[(int64_t)p * NB + i];
+        Y[i][c] = c < kc ? b[(int64_t)(pd.g0 + src) * k + c0 + c] : (T)0;
+    }
+    for (int q = tid; q < w * w; q += 256) {
+        int i = q / w, j = q % w;
+        Lm[i][j] = (T)linv[(int64_t)p * NB * NB + i * NB + j];
+    }
+    __syncthreads();
+    for (int q = tid; q < w * KC; q += 256) {
+        int i = q / KC, c = q % KC;
+        if (c >= kc) continue;
+        T acc = 0;
+        for (int t = 0; t <= i; ++t) acc += Lm[i][t] * Y[t][c];
+        b[(int64_t)(pd.g0 + i) * k + c0 + c] = acc;
+    }
+}
+
+// forward update: block (row tile of a panel in level, rhs chunk): b2 -= L21 y
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_update(const int32_t *__restrict__ lvl_panels,
+                                                     const int32_t *__restrict__ tile_pre,
+                                                     int32_t count, const PanelDesc *__restrict__ panels,
+                                                     const int32_t *__restrict__ idx,
+                                                     const T *__restrict__ arena, T *b, int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*Ls)[TR + 1] = reinterpret_cast<T (*)[TR + 1]>(smem_raw);                 // Ls[t][row]
+    T (*Y)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw + sizeof(T) * NB * (TR + 1));
+    const int tile = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_pre[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const PanelDesc pd = panels[lvl_panels[lo]];
+    const int w = pd.w, m = pd.m;
+    const int r0 = (tile - tile_pre[lo]) * TR;
+    const int rbelow = m - pd.k0 - w;
+    const int nr = min(TR, rbelow - r0);
+    const int c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const T *F = arena + pd.front_off;
+    const int64_t rowbase = pd.k0 + w + r0;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < w * TR; q += 256) {
+        int t = q / TR, i = q % TR;
+        Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
+    }
+    for (int q = tid; q < w * KC; q += 256) {
+        int t = q / KC, c = q % KC;
+        Y[t][c] = c < kc ? b[(int64_t)(pd.g0 + t) * k + c0 + c] : (T)0;
+    }
+    __syncthreads();
+    const int *gi = idx + pd.idx_off + rowbase;
+    // thread: column c = tid % 32, rows (tid / 32) + 8 a
+    const int c = tid & 31, rr = tid >> 5;
+    if (c < kc) {
+        for (int a = 0; a < TR / 8; ++a) {
+            int i = rr + 8 * a;
+            if (i >= nr) break;
+            T acc = 0;
+            for (int t = 0; t < w; ++t) acc += Ls[t][i] * Y[t][c];
+            atomic_add_t(&b[(int64_t)gi[i] * k + c0 + c], -acc);
+        }
+    }
+}
+
+// backward gather: z[slot][t][c] += sum_rows L21[row][t] x[idx[row]][c]
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_gather(const int32_t *__restrict__ lvl_panels,
+                                                     const int32_t *__restrict__ tile_pre,
+                                                     int32_t count, const PanelDesc *__restrict__ panels,
+                                                     const int32_t *__restrict__ idx,
+                                                     const T *__restrict__ arena, const T *__restrict__ x,
+                                                     int k, T *zbuf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*Ls)[TR + 1] = reinterpret_cast<T (*)[TR + 1]>(smem_raw);
+    T (*Xs)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw + sizeof(T) * NB * (TR + 1));
+    const int tile = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_pre[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    const PanelDesc pd = panels[lvl_panels[lo]];
+    const int w = pd.w, m = pd.m;
+    const int r0 = (tile - tile_pre[lo]) * TR;
+    const int rbelow = m - pd.k0 - w;
+    const int nr = min(TR, rbelow - r0);
+    const int c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const T *F = arena + pd.front_off;
+    const int64_t rowbase = pd.k0 + w + r0;
+    const int *gi = idx + pd.idx_off + rowbase;
+    const int tid = threadIdx.x;
+    for (int q = tid; q < w * TR; q += 256) {
+        int t = q / TR, i = q % TR;
+        Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
+    }
+    for (int q = tid; q < TR * KC; q += 256) {
+        int i = q / KC, c = q % KC;
+        Xs[i][c] = (i < nr && c < kc) ? x[(int64_t)gi[i] * k + c0 + c] : (T)0;
+    }
+    __syncthreads();
+    T *z = zbuf + (int64_t)lo * NB * k;
+    for (int q = tid; q < w * KC; q += 256) {
+        int t = q / KC, c = q % KC;
+        if (c >= kc) continue;
+        T acc = 0;
+        for (int i = 0; i < nr; ++i) acc += Ls[t][i] * Xs[i][c];
+        atomic_add_t(&z[(int64_t)t * k + c0 + c], acc);
+    }
+}
+
+// backward diagonal step: x1 = P^T L11^-T (D^-1 y - z)
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lvl_panels,
+                                                   const PanelDesc *__restrict__ panels,
+                                                   const double *__restrict__ linv,
+                                                   const double *__restrict__ dblk,
+                                                   const int32_t *__restrict__ piv,
+                                                   const T *__restrict__ zbuf, int use_z, T *x,
+                                                   int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T (*U)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw);
+    T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KC + 1));
+    __shared__ double sd[NB], se[NB];
+    const int slot = blockIdx.x;
+    const int p = lvl_panels[slot];
+    const PanelDesc pd = panels[p];
+    const int w = pd.w, c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const int tid = threadIdx.x;
+    if (tid < NB) {
+        sd[tid] = dblk[(int64_t)p * 2 * NB + tid];
+        se[tid] = dblk[(int64_t)p * 2 * NB + NB + tid];
+    }
+    for (int q = tid; q < w * w; q += 256) {
+        int i = q / w, j = q % w;
+        Lm[i][j] = (T)linv[(int64_t)p * NB * NB + i * NB + j];
+    }
+    for (int q = tid; q < w * KC; q += 256) {
+        int i = q / KC, c = q % KC;
+        U[i][c] = c < kc ? x[(int64_t)(pd.g0 + i) * k + c0 + c] : (T)0;
+    }
+    __syncthreads();
+    T val[NB / 8];
+    // u = Dinv y - z, each thread handles entries (i, c) with i = tid/32 + 8a
+    const int c = tid & 31, rr = tid >> 5;
+    for (int a = 0; a < NB / 8; ++a) {
+        int i = rr + 8 * a;
+        double u = 0.0;
+        if (i < w && c < kc) {
+            if (se[i] != 0.0) {                     // first row of a 2x2 block
+                double A = sd[i], B = se[i], C = sd[i + 1], det = A * C - B * B;
+                u = (C * (double)U[i][c] - B * (double)U[i + 1][c]) / det;
+            } else if (i > 0 && se[i - 1] != 0.0) { // second row of a 2x2 block
+                double A = sd[i - 1], B = se[i - 1], C = sd[i], det = A * C - B * B;
+                u = (-B * (double)U[i - 1][c] + A * (double)U[i][c]) / det;
+            } else {
+                u = sd[i] != 0.0 ? (double)U[i][c] / sd[i] : 0.0;
+            }
+            if (use_z) u -= (double)zbuf[(int64_t)slot * NB * k + (int64_t)i * k + c0 + c];
+        }
+        val[a] = (T)u;
+    }
+    __syncthreads();
+    for (int a = 0; a < NB / 8; ++a) {
+        int i = rr + 8 * a;
+        if (i < w) U[i][c] = val[a];
+    }
+    __syncthreads();
+    // x'[i] = sum_{t >= i} Linv[t][i] u[t];  x[g0 + piv[i]] = x'[i]
+    for (int q = tid; q < w * KC; q += 256) {
+        int i = q / KC, cc = q % KC;
+        if (cc >= kc) continue;
+        T acc = 0;
+        for (int t = i; t < w; ++t) acc += Lm[t][i] * U[t][cc];
+        x[(int64_t)(pd.g0 + piv[(int64_t)p * NB + i]) * k + c0 + cc] = acc;
+    }
+}
+
+// row permutation: mode 0 gather dst[i] = src[perm[i]]; 1 scatter dst[perm[i]] = src[i];
+// 2 scatter-add dst[perm[i]] += src[i]
+template <typename TD, typename TS>
+__global__ void k_permute_rows(int64_t n, int k, const int32_t *__restrict__ perm,
+                               const TS *__restrict__ src, TD *dst, int mode) {
+    int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * k) return;
+    int64_t i = q / k;
+    int c = (int)(q - i * k);
+    int64_t j = perm[i];
+    if (mode == 1) dst[j * k + c] = (TD)src[q];
+    else if (mode == 2) dst[j * k + c] += (TD)src[q];
+    else dst[q] = (TD)src[j * k + c];
+}
+
+}  // namespace ssk

@@ -1,0 +1,310 @@
+"""Host-side SISLICE logic over the CUDA library (Alg. 1 with a fixed pencil, Sec. 2-3).
+
+The device work -- factorisations, inertia, in-slice iterations, DOS sweeps -- runs in
+the library; this module sequences it and holds the O(n_s k) scalar logic:
+
+* ``DosModel``: the Lanczos DOS / CDOS closed forms (Eqs. 13-14) with Gaussian widths
+  nu_j = d_j / 3, d_j the larger neighbour gap of the Ritz values (floored), averaged
+  over start vectors; the interval expectation shift (Eqs. 16-17).
+* ``cdos_partition``: n_s intervals of equal CDOS mass (Eq. 15, read as
+  Phi(omega) = Phi(a) + K j), one shift per interval at its DOS expectation.
+* ``region_for_lowest``: [lambda_min, lambda_max] holding exactly the n_e lowest
+  eigenvalues, from the DOS estimate and exact inertia counts.
+* ``validate``: candidates split at the slice midpoints, exact counts from inertia,
+  the three cases of Section 2.3.
+* ``kmeans_shifts``: k-means++ seeding and Lloyd iterations on validated Ritz values
+  (Section 3.2); the uniforms are passed in.
+* ``SliceSolver.run``: factor every shift (one batched call), inertia, probes, rounds of
+  subspace iterations until every slice validates.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+from scipy.special import erf
+
+from . import api
+
+
+# ----------------------------------------------------------------- DOS model
+class DosModel:
+    """phi / Phi of Eqs. 13-14 averaged over Lanczos runs [(theta, zeta2), ...]."""
+
+    def __init__(self, n: int, runs):
+        self.n = n
+        self.runs = []
+        for th, z2 in runs:
+            th = np.asarray(th, dtype=np.float64)
+            self.runs.append((th, np.asarray(z2, dtype=np.float64), self.widths(th)))
+
+    @staticmethod
+    def widths(theta: np.ndarray) -> np.ndarray:
+        m = theta.size
+        if m == 1:
+            return np.ones(1)
+        gap = np.diff(theta)
+        d = np.empty(m)
+        d[0], d[-1] = gap[0], gap[-1]
+        if m > 2:
+            d[1:-1] = np.maximum(gap[:-1], gap[1:])
+        d = np.maximum(d, 1e-3 * (theta[-1] - theta[0]) / m)
+        return d / 3.0
+
+    def _kappa(self, w, th, nu):
+        return (np.atleast_1d(w)[:, None] - th[None, :]) / (nu[None, :] * math.sqrt(2.0))
+
+    def phi(self, w):
+        out = 0.0
+        for th, z2, nu in self.runs:
+            k = self._kappa(w, th, nu)
+            out = out + self.n / math.sqrt(2 * math.pi) * (z2 / nu * np.exp(-k * k)).sum(axis=1)
+        return out / len(self.runs)
+
+    def Phi(self, w):
+        out = 0.0
+        for th, z2, nu in self.runs:
+            k = self._kappa(w, th, nu)
+            out = out + 0.5 * self.n * (z2 * (erf(k) + 1.0)).sum(axis=1)
+        return out / len(self.runs)
+
+    def expectation(self, l, u):
+        num = 0.0
+        for th, z2, nu in self.runs:
+            k = self._kappa(np.array([l, u]), th, nu)
+            ps = th / 2 * erf(k) - nu / math.sqrt(2 * math.pi) * np.exp(-k * k)
+            num += self.n * float((z2 * (ps[1] - ps[0])).sum())
+        num /= len(self.runs)
+        den = float(self.Phi(u)[0] - self.Phi(l)[0])
+        return num / den if den > 0 else 0.5 * (l + u)
+
+    def root(self, target, lo, hi, rel=1e-12):
+        """omega in [lo, hi] with Phi(omega) = target (bisection; Phi is nondecreasing)."""
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if hi - lo <= rel * max(1.0, abs(mid)):
+                break
+            if self.Phi(mid)[0] < target:
+                lo = mid
+            else:
+                hi = mid
+        return 0.5 * (lo + hi)
+
+    def theta_range(self):
+        lo = min(float((th - 3 * nu).min()) for th, _, nu in self.runs)
+        hi = max(float((th + 3 * nu).max()) for th, _, nu in self.runs)
+        return lo, hi
+
+
+def cdos_partition(model: DosModel, a: float, b: float, n_s: int):
+    """n_s intervals of equal CDOS mass on [a, b] and the expectation shift of each."""
+    Pa, Pb = float(model.Phi(a)[0]), float(model.Phi(b)[0])
+    K = (Pb - Pa) / n_s
+    roots = [a] + [model.root(Pa + K * j, a, b) for j in range(1, n_s)] + [b]
+    iv = [(roots[j], roots[j + 1]) for j in range(n_s)]
+    shifts = [model.expectation(l, u) for l, u in iv]
+    return iv, shifts
+
+
+# ----------------------------------------------------------------- validation
+def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max, tol):
+    """Section 2.3.  probes[j] = (theta, resid).  Returns (selected [(probe, ritz)],
+    per-slice records (n_exact, n_cand, n_conv, status))."""
+    ns = len(shifts)
+    bounds = [nneg_min] + list(nneg_shift) + [nneg_max]
+    selected, info = [], []
+    for s in range(ns + 1):
+        lo = lam_min if s == 0 else shifts[s - 1]
+        hi = lam_max if s == ns else shifts[s]
+        cand = []
+        if s == 0:
+            th = probes[0][0]
+            cand += [(0, i) for i in np.nonzero((th >= lam_min) & (th < hi))[0]]
+        elif s == ns:
+            th = probes[ns - 1][0]
+            cand += [(ns - 1, i) for i in np.nonzero((th > lo) & (th <= lam_max))[0]]
+        else:
+            tau = 0.5 * (lo + hi)
+            th = probes[s - 1][0]
+            cand += [(s - 1, i) for i in np.nonzero((th > lo) & (th <= tau))[0]]
+            th = probes[s][0]
+            cand += [(s, i) for i in np.nonzero((th > tau) & (th < hi))[0]]
+        n_exact = bounds[s + 1] - bounds[s]
+        cand.sort(key=lambda pi: (probes[pi[0]][1][pi[1]], pi[0], pi[1]))
+        n_conv = sum(1 for pj, i in cand if probes[pj][1][i] <= tol)
+        if n_exact == len(cand):
+            status = "ok"
+        elif n_exact > len(cand):
+            status = "missing"
+        else:
+            status = "excess"
+        selected += cand[:n_exact]
+        info.append((n_exact, len(cand), n_conv, status))
+    return selected, info
+
+
+# ----------------------------------------------------------------- k-means migration
+def kmeans_shifts(values, n_s, uniforms, max_iter=1000):
+    """k-means++ seeding (first centroid uniform, then D^2-weighted) and Lloyd steps."""
+    x = np.sort(np.asarray(values, dtype=np.float64))
+    n = x.size
+    cent = [x[min(n - 1, int(uniforms[0] * n))]]
+    for c in range(1, n_s):
+        d2 = np.min((x[:, None] - np.asarray(cent)[None, :]) ** 2, axis=1)
+        tot = d2.sum()
+        if tot <= 0:
+            cent.append(x[min(n - 1, int(uniforms[c] * n))])
+            continue
+        idx = int(np.searchsorted(np.cumsum(d2) / tot, uniforms[c], side="right"))
+        cent.append(x[min(n - 1, idx)])
+    cent = np.asarray(cent)
+    assign = None
+    for _ in range(max_iter):
+        a = np.argmin(np.abs(x[:, None] - cent[None, :]), axis=1)
+        if assign is not None and np.array_equal(a, assign):
+            break
+        assign = a
+        for c in range(n_s):
+            m = a == c
+            if m.any():
+                cent[c] = x[m].mean()
+    return np.sort(cent)
+
+
+# ----------------------------------------------------------------- solver
+@dataclass
+class SliceResult:
+    shifts: list
+    lam_min: float
+    lam_max: float
+    eigenvalues: np.ndarray
+    eigenvectors: torch.Tensor
+    residuals: np.ndarray
+    slices: list
+    probes: list
+    rounds: int
+    timings: dict = field(default_factory=dict)
+
+
+class SliceSolver:
+    """Lowest-n_e eigenpairs of (A, B) by spectrum slicing on one GPU."""
+
+    def __init__(self, sym: api.Symbolic, a_vals, b_vals, precision="mixed", tol=1e-10, refine=2):
+        self.sym, self.a, self.b = sym, a_vals, b_vals
+        self.precision, self.tol, self.refine = precision, tol, refine
+
+    def count_below(self, sigmas):
+        """Exact eigenvalue counts below each sigma (inertia of one batched factor)."""
+        f = self.sym.factor(self.a, self.b, sigmas, self.precision)
+        out = [f.inertia(j)[0] for j in range(len(sigmas))]
+        f.close()
+        return out
+
+    def region_for_lowest(self, model: DosModel, n_e: int):
+        """[lambda_min, lambda_max] with nu(lambda_min) = 0 and nu(lambda_max) = n_e."""
+        lo_t, hi_t = model.theta_range()
+        lam_min = lo_t
+        span = hi_t - lo_t
+        while self.count_below([lam_min])[0] > 0:
+            lam_min -= 0.1 * span
+        guess = model.root(n_e + 0.5, lo_t, hi_t)
+        c = self.count_below([guess])[0]
+        lo, hi = (lam_min, guess) if c > n_e else (guess, guess)
+        step = 0.01 * span
+        while c <= n_e and hi < hi_t + span:         # bracket from above
+            lo, hi = hi, hi + step
+            step *= 2
+            c = self.count_below([hi])[0]
+        # nu(lo) <= n_e < nu(hi): bisect until a point with nu == n_e that sits
+        # mid-gap is found
+        clo = self.count_below([lo])[0]
+        for _ in range(80):
+            if clo == n_e and c > n_e and (hi - lo) < 1e-3 * span:
+                break
+            mid = 0.5 * (lo + hi)
+            cm = self.count_below([mid])[0]
+            if cm <= n_e:
+                lo, clo = mid, cm
+            else:
+                hi, c = mid, cm
+        return lam_min, lo
+
+    def run(self, shifts, lam_min, lam_max, k, V0=None, max_rounds=60, iters_per_round=4, seed=0):
+        """Factor the shifts and the two region bounds in one batched call, then run
+        rounds of subspace iterations on the probes next to any slice that does not yet
+        validate (fewer converged candidates than its exact count)."""
+        t0 = time.perf_counter()
+        ns = len(shifts)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        f = self.sym.factor(self.a, self.b, list(shifts) + [lam_min, lam_max], self.precision)
+        ev1.record()
+        counts = [f.inertia(j)[0] for j in range(ns + 2)]
+        nneg, nneg_min, nneg_max = counts[:ns], counts[ns], counts[ns + 1]
+        torch.cuda.synchronize()
+        t_factor = ev0.elapsed_time(ev1) / 1e3
+        n = self.sym.n
+        if V0 is None:
+            g = torch.Generator(device="cuda").manual_seed(seed)
+            V0 = [torch.randn(n, k, generator=g, device="cuda", dtype=torch.float64) for _ in range(ns)]
+        Vs = list(V0)
+        probes = [None] * ns
+        windows = []
+        for j in range(ns):
+            lo = lam_min if j == 0 else 0.5 * (shifts[j - 1] + shifts[j])
+            hi = lam_max if j == ns - 1 else 0.5 * (shifts[j] + shifts[j + 1])
+            windows.append((lo, hi))
+        active = list(range(ns))
+        rounds = 0
+        t_solve = 0.0
+        iters = [0] * ns
+        info = []
+        sel = []
+        while active and rounds < max_rounds:
+            rounds += 1
+            ts = time.perf_counter()
+            for j in active:
+                lo, hi = windows[j]
+                pr = f.slice_solve(j, lo, hi, Vs[j], tol=self.tol, max_iter=iters_per_round,
+                                   refine=self.refine, n_expect=k + 1, allow_noconv=True)
+                probes[j] = pr
+                Vs[j] = pr.X
+                iters[j] += pr.iterations
+            t_solve += time.perf_counter() - ts
+            sel, info = validate(shifts, lam_min, lam_max, [(p.theta, p.resid) for p in probes], nneg,
+                                 nneg_min, nneg_max, self.tol)
+            bad = set()
+            for s, (n_exact, n_cand, n_conv, status) in enumerate(info):
+                if n_conv < n_exact:
+                    if s > 0:
+                        bad.add(s - 1)
+                    if s < ns:
+                        bad.add(s)
+            active = sorted(bad)
+        lam = np.array([probes[pj].theta[i] for pj, i in sel])
+        res = np.array([probes[pj].resid[i] for pj, i in sel])
+        order = np.argsort(lam, kind="stable")
+        X = torch.stack([probes[sel[q][0]].X[:, sel[q][1]] for q in order], dim=1) if sel else None
+        f.close()
+        return SliceResult(list(shifts), lam_min, lam_max, lam[order], X, res[order], info, probes, rounds,
+                           dict(factor_s=t_factor, solve_s=t_solve, total_s=time.perf_counter() - t0,
+                                iterations=iters, n_below_max=nneg_max, n_below_min=nneg_min,
+                                converged=not active))
+
+    def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01):
+        """Region and shifts from the DOS alone: lambda_min below every Ritz value,
+        lambda_max at Phi = (1 + margin) n_e + 1, n_s CDOS intervals between them."""
+        lo_t, hi_t = model.theta_range()
+        lam_min = lo_t
+        lam_max = model.root((1.0 + margin) * n_e + 1.0, lo_t, hi_t)
+        _, shifts = cdos_partition(model, lam_min, lam_max, n_s)
+        return lam_min, lam_max, shifts
+
+
+def default_basis_width(n_e: int, n_s: int) -> int:
+    """k = 2 ceil(n_e / n_s) + 16 rounded up to a multiple of 16."""
+    k = 2 * (-(-n_e // n_s)) + 16
+    return -(-k // 16) * 16

@@ -1,0 +1,52 @@
+"""GPU parity of the SpMM sweep, the Lanczos DOS estimate (Section 3.1) and the
+band-energy gradient SDDMM against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dense, dos, grad
+from tests.gpu_util import setup
+from workloads.pencils import config_pencil, gaussian_pencil, normal_block
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("k", [1, 3, 4, 7, 16, 40])
+def test_spmm_matches_oracle(gpu_lib, k):
+    p = gaussian_pencil((4, 3, 5), seed=8)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    X = np.random.default_rng(k).standard_normal((p.n, k))
+    al = np.linspace(1.0, 2.0, k)
+    be = np.linspace(-0.5, 0.5, k)
+    Y = sym.spmm(a, b, torch.tensor(X, device="cuda"), al, be).cpu().numpy()
+    ref = dense.csr_mm(p.rowptr, p.colind, p.a, X) * al + dense.csr_mm(p.rowptr, p.colind, p.b, X) * be
+    assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_dos_matches_oracle_lanczos(gpu_lib):
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    steps, nv = 60, 4
+    X0 = normal_block(p.n, nv, 21)
+    runs = sym.dos_estimate(a, b, steps, torch.tensor(X0, device="cuda"))
+    A, B = p.dense("a"), p.dense("b")
+    for c in range(nv):
+        th_o, z_o, _, _ = dos.lanczos_ritz(A, B, X0[:, c], steps)
+        th, z = runs[c]
+        assert th.size == th_o.size
+        assert np.abs(th - th_o).max() <= 1e-8 * np.abs(th_o).max()
+        assert np.abs(z - z_o).max() <= 1e-8
+        assert abs(z.sum() - 1.0) <= 1e-10
+
+
+def test_band_energy_grad_matches_oracle(gpu_lib):
+    p = gaussian_pencil((4, 4, 3), seed=6)
+    lam, X = dense.gen_eig(p.dense("a"), p.dense("b"))
+    ne = 19
+    ctx, sym, a, b = setup(gpu_lib, p)
+    Xd = torch.tensor(np.ascontiguousarray(X[:, :ne]), device="cuda")
+    ld = torch.tensor(lam[:ne], device="cuda")
+    ga, gb = sym.band_energy_grad(Xd, ld)
+    ga_o, gb_o = grad.band_energy_grad(p, lam[:ne], X[:, :ne])
+    assert np.abs(ga.cpu().numpy() - ga_o).max() <= 1e-12 * np.abs(ga_o).max()
+    assert np.abs(gb.cpu().numpy() - gb_o).max() <= 1e-12 * np.abs(gb_o).max()

@@ -35,10 +35,10 @@ def test_full_lanczos_reproduces_spectrum_and_weights():
     th, z2, _, _ = dos.lanczos_ritz(A, B, x0, p.n)
     lam, X = dense.gen_eig(A, B)
     assert np.allclose(th, lam, atol=1e-9 * np.abs(lam).max())
-    # zeta_j^2 = (y_j^T q_1)^2 with y_j = L^T x_j the eigenvectors of L^-1 A L^-T
-    L = np.linalg.cholesky(B)
-    q1 = x0 / np.linalg.norm(x0)
-    w = (X.T @ L @ q1) ** 2
+    # zeta_j^2 = (x_j^T B x_1)^2 for the B-orthonormal eigenvectors x_j and the
+    # B-normalised start vector x_1
+    x1 = x0 / np.sqrt(x0 @ B @ x0)
+    w = (X.T @ B @ x1) ** 2
     assert np.allclose(z2, w, atol=1e-9)
 
 
