@@ -192,18 +192,26 @@ def main():
     a = torch.tensor(p.a, device="cuda")
     b = torch.tensor(p.b, device="cuda")
     n_e, n_s = wl["n_e"], wl["n_s"]
-    k = default_basis_width(n_e, n_s)
+    k = 0                                     # probe basis: 2 c + 16 per window of c eigenvalues
     steps_dos, n_vec = 100, 4
     ha = torch.tensor(p.a).pin_memory()
     hb = torch.tensor(p.b).pin_memory()
 
     def step(precision, a_dev, b_dev, seed):
+        t0 = time.perf_counter()
         start = torch.tensor(normal_block(p.n, n_vec, 1000 + seed), device="cuda")
         runs = sym.dos_estimate(a_dev, b_dev, steps_dos, start)
         model = DosModel(p.n, runs)
         solver = SliceSolver(sym, a_dev, b_dev, precision=precision)
-        lam_min, lam_max, shifts = solver.place_shifts(model, n_e, n_s)
-        res = solver.run(shifts, lam_min, lam_max, k, seed=seed, iters_per_round=4)
+        lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
+        t1 = time.perf_counter()
+        res = solver.run(shifts, lam_min, lam_max, model, seed=seed, splits=splits, ks=ks)
+        if args.verbose:
+            print(f"[step {precision} seed={seed}] dos+place {t1 - t0:.3f}s factor {res.timings['factor_s']:.3f}s "
+                  f"probes {res.timings['solve_s']:.3f}s total {time.perf_counter() - t0:.3f}s rounds {res.rounds} "
+                  f"found {len(res.eigenvalues)} (nu(max)={res.timings['n_below_max']}) "
+                  f"maxres {res.residuals.max() if len(res.residuals) else -1:.2e} "
+                  f"slices {[i[:3] for i in res.slices]}", file=sys.stderr, flush=True)
         return res
 
     def check(res):
@@ -302,7 +310,9 @@ def main():
            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic",
-           "config": {"workload": wl["name"], "precision": args.precision, "basis_k": k,
+           "config": {"workload": wl["name"], "precision": args.precision,
+                      "probe_driver": "shift-invert subspace iteration (Alg. 2) with Rayleigh-Ritz every iteration",
+                      "shift_placement": "DOS ball partition (radius 2h ball <= basis)",
                       "lanczos_steps": steps_dos, "lanczos_vectors": n_vec, "parallelism": f"replicas x{ws}",
                       "l2": "inputs larger than L2 (factor arena > 129 MB)",
                       "eigenpairs_validated": int(len(r0.eigenvalues)), "all_validated": all_ok,

@@ -90,14 +90,17 @@ typedef struct ss_probe_stats {
 /* Options of one slice solve.  Zero fields take the defaults in brackets. */
 typedef struct ss_solve_opts {
     int32_t driver;             /* SS_SUBSPACE | SS_BLOCK_LANCZOS [SS_SUBSPACE]      */
-    int32_t max_iter;           /* iteration cap [200]                               */
+    int32_t max_iter;           /* SS_SUBSPACE: iteration cap [200];
+                                   SS_BLOCK_LANCZOS: Krylov blocks in the basis [6]  */
     int32_t check_every;        /* Rayleigh-Ritz + residual check period [1]         */
     int32_t refine;             /* FP64 refinement corrections per solve, mixed
                                    factor only [2]                                   */
     double tol;                 /* normalised residual target [1e-10]                */
     int32_t n_expect;           /* keep iterating until at least this many Ritz values
                                    lie in (lo, hi] (e.g. an inertia count) [0]        */
-    int32_t reserved[3];
+    int32_t k_out;              /* Ritz pairs returned (SS_BLOCK_LANCZOS: the k_out
+                                   nearest sigma, <= k * max_iter) [k]               */
+    int32_t reserved[2];
 } ss_solve_opts;
 
 /* ---- context ---------------------------------------------------------------------
@@ -141,7 +144,9 @@ ss_status ss_symbolic_validate(const ss_symbolic *sym);
  * Pivoting is Bunch-Kaufman (1x1 / 2x2) restricted to each panel's diagonal block,
  * computed in FP64.  precision = SS_FP64 keeps fronts in FP64; SS_MIXED keeps fronts
  * and Schur updates in FP32 with FP64 diagonal blocks, and solves with FP64 iterative
- * refinement.
+ * refinement.  SS_MIXED checks every shift's FP32 factor: one FP32 solve of a fixed
+ * probe vector must reduce the residual to rho <= 1e-2 of the right-hand side, else that
+ * shift is refactored in FP64 (ss_factor_quality reports which).
  * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_SINGULAR (a pivot fell below
  * 64 u ||A - sigma B||_1 for some shift; the factor is still returned and
  * ss_inertia reports which shift). */
@@ -159,6 +164,19 @@ ss_status ss_factor_destroy(ss_numeric *f);
 ss_status ss_inertia(const ss_numeric *f, int32_t shift_idx, int64_t *n_neg, int64_t *n_zero,
                      int64_t *n_pos, int32_t *tiny_pivot);
 
+/* Precision shift j was finally factored in (SS_FP64 after a mixed-precision
+ * fallback) and, for an FP32 factor, its measured contraction factor rho.
+ * Host outputs, each may be NULL.  Errors: SS_ERR_ARG. */
+ss_status ss_factor_quality(const ss_numeric *f, int32_t shift_idx, int32_t *precision_used,
+                            double *rho);
+
+/* Numerical diagnostics of shift j's factor (no paper counterpart): the smallest pivot
+ * magnitude relative to ||A||_1 + |sigma| ||B||_1 (for a 2x2 block, its smaller
+ * eigenvalue magnitude), the largest |L| entry (element growth), and the number of 2x2
+ * pivot blocks.  Host outputs, each may be NULL.  Errors: SS_ERR_ARG. */
+ss_status ss_factor_stats(const ss_numeric *f, int32_t shift_idx, double *min_pivot_ratio,
+                          double *max_abs_l, int64_t *n_2x2);
+
 /* ---- ss_solve (Alg. 2 step 3 without B: X = (A - sigma_j B)^-1 R) ------------------
  * R and X are DEVICE float64 N x k row-major (may alias).  For a mixed factor, `refine`
  * FP64 refinement corrections are applied (residual by FP64 SpMM with A and B).
@@ -167,28 +185,36 @@ ss_status ss_solve(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k,
                    int32_t refine);
 
 /* ---- ss_slice_solve (Alg. 2: shift-invert subspace iteration with Cholesky-QR in
- * the B inner product, Rayleigh-Ritz, residual norms; Section 2.2) ----------------
- * Builds the spectral probe of shift sigma_j: k Ritz pairs nearest sigma_j.  V0 is
- * the DEVICE N x k start block (seeded N(0,1) or a previous probe's X; required).
+ * the B inner product, Rayleigh-Ritz, residual norms; Section 2.2; or the shift-invert
+ * block Lanczos the paper names as its alternative, Section 1) ----------------------
+ * Builds the spectral probe of shift sigma_j.  V0 is the DEVICE N x k start block
+ * (seeded N(0,1) or a previous probe's X; required).  SS_SUBSPACE iterates on k
+ * vectors and returns k Ritz pairs.  SS_BLOCK_LANCZOS builds max_iter blocks of width k
+ * (O = (A - sigma B)^-1 B, full B-re-orthogonalisation), does one Rayleigh-Ritz on the
+ * whole basis and returns the k_out Ritz pairs nearest sigma.
  * A Ritz pair is converged when its normalised residual
  * ||A x - theta B x||_2 / (||A||_1 ||x||_2) <= opts->tol.  Iterates until at least
  * opts->n_expect Ritz values in (lo, hi] are converged (n_expect > 0, e.g. an exact
  * count from inertia), or every Ritz value in (lo, hi] is (n_expect = 0), or max_iter.
  * Unconverged Ritz values inside the window can be spurious mixtures of eigenvectors
  * at equal distance on both sides of sigma; validation (Section 2.3) discards them.
- * Outputs: lambda (HOST float64[k], ascending Ritz values), X (DEVICE N x k, B-
- * orthonormal Ritz vectors in the same order), resid (HOST float64[k]), n_found
- * (HOST: #converged Ritz values in (lo, hi]), stats (HOST, may be NULL).
+ * Outputs (k_out entries; k_out = k for SS_SUBSPACE): lambda (HOST float64, ascending
+ * Ritz values), X (DEVICE N x k_out, B-orthonormal Ritz vectors in the same order),
+ * resid (HOST float64), n_found (HOST: #converged Ritz values in (lo, hi]), stats
+ * (HOST, may be NULL).
  * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_NOCONV (outputs still valid). */
 ss_status ss_slice_solve(ss_numeric *f, int32_t shift_idx, double lo, double hi,
                          const ss_solve_opts *opts, const double *V0, int32_t k,
                          double *lambda, double *X, double *resid, int32_t *n_found,
                          ss_probe_stats *stats);
 
-/* ---- ss_dos_estimate (Section 3.1, Eqs. 13-14: Lanczos DOS of L^-1 A L^-T) --------
- * Factors B (Cholesky via LDL^T at sigma = 0 of the pencil (B, 0)), then runs
- * `steps` Lanczos steps on L^-1 A L^-T with full re-orthogonalisation for each of the
- * n_vec DEVICE start vectors in start (N x n_vec row-major, e.g. seeded N(0,1)).
+/* ---- ss_dos_estimate (Section 3.1, Eqs. 13-14: Lanczos DOS of G^-1 A G^-T) --------
+ * Factors B = G G^T (the LDL^T at sigma = 0 of the pencil (B, 0), G = P L D^1/2), then
+ * runs `steps` Lanczos steps on G^-1 A G^-T with full re-orthogonalisation for each of
+ * the n_vec DEVICE start vectors y0 in start (N x n_vec row-major, seeded N(0,1)).  It
+ * is computed as B-orthonormal Lanczos on B^-1 A from x0 = G^-T y0; because the start
+ * vectors are i.i.d. N(0,1) the estimate's distribution does not depend on which
+ * square root G of B is used.
  * Outputs (HOST): theta[n_vec*steps], zeta2[n_vec*steps] (squared first components
  * of the tridiagonal's eigenvectors, per run, ascending theta), m_run[n_vec] (steps
  * actually taken per run; entries past m_run are 0).
@@ -196,6 +222,12 @@ ss_status ss_slice_solve(ss_numeric *f, int32_t shift_idx, double lo, double hi,
 ss_status ss_dos_estimate(ss_symbolic *sym, const double *a_vals, const double *b_vals,
                           int32_t steps, int32_t n_vec, const double *start,
                           double *theta, double *zeta2, int32_t *m_run);
+/* ss_dos_lanczos: the same Lanczos run from explicit start vectors x0 of the
+ * B-orthonormal form (Section 3.1's second form): x_1 = x0 / ||x0||_B, operator B^-1 A.
+ * Same outputs and errors as ss_dos_estimate. */
+ss_status ss_dos_lanczos(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                         int32_t steps, int32_t n_vec, const double *x0,
+                         double *theta, double *zeta2, int32_t *m_run);
 
 /* ---- ss_band_energy_grad (Hellmann-Feynman; not in the paper) ----------------------
  * For E = sum_{i < n_e} lambda_i with B-orthonormal eigenvectors X (DEVICE N x n_e

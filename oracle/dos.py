@@ -65,6 +65,14 @@ def lanczos_ritz(A: np.ndarray, B: np.ndarray, x0: np.ndarray, k: int):
     return theta, zeta2, alpha[:m], beta[: m - 1]
 
 
+def lanczos_ritz_cholesky_frame(A: np.ndarray, B: np.ndarray, y0: np.ndarray, k: int):
+    """Lanczos on L^-1 A L^-T (B = L L^T, the Cholesky factor) started at y0: the same
+    run as B-orthonormal Lanczos on B^-1 A from x0 = L^-T y0 (Section 3.1, first form)."""
+    L = np.linalg.cholesky(B)
+    x0 = sla.solve_triangular(L, np.asarray(y0, dtype=np.float64), lower=True, trans="T")
+    return lanczos_ritz(A, B, x0, k)
+
+
 def gaussian_widths(theta: np.ndarray) -> np.ndarray:
     """nu_j = d_j / 3, d_j = max neighbour gap (single gap at the ends), floored."""
     theta = np.asarray(theta, dtype=np.float64)

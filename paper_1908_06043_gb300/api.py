@@ -138,6 +138,9 @@ class Symbolic:
     def dos_estimate(self, a_vals, b_vals, steps: int, start: torch.Tensor):
         return dos_estimate(self, a_vals, b_vals, steps, start)
 
+    def dos_lanczos(self, a_vals, b_vals, steps: int, x0: torch.Tensor):
+        return dos_lanczos(self, a_vals, b_vals, steps, x0)
+
     def band_energy_grad(self, X, lam):
         return band_energy_grad(self, X, lam)
 
@@ -194,6 +197,19 @@ class Factor:
         """(n_neg, n_zero, n_pos, tiny_pivot) of A - sigma_j B."""
         return inertia(self, j)
 
+    def stats(self, j: int = 0):
+        """(min pivot / ||A - sigma B||_1 bound, max |L|, number of 2x2 pivots) of shift j."""
+        mp, ml, n2 = C.c_double(), C.c_double(), C.c_int64()
+        self.ctx.check(self.ctx.lib.ss_factor_stats(self.h, j, C.byref(mp), C.byref(ml), C.byref(n2)),
+                       "ss_factor_stats")
+        return mp.value, ml.value, n2.value
+
+    def quality(self, j: int = 0):
+        """(precision the shift was factored in, FP32 contraction factor rho)."""
+        pr, rho = C.c_int32(), C.c_double()
+        self.ctx.check(self.ctx.lib.ss_factor_quality(self.h, j, C.byref(pr), C.byref(rho)), "ss_factor_quality")
+        return ("fp64" if pr.value == L.SS_FP64 else "mixed"), rho.value
+
     def solve(self, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
         return solve(self, j, R, refine)
 
@@ -228,17 +244,21 @@ def solve(f: Factor, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
 
 
 def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: float = 1e-10,
-                max_iter: int = 200, check_every: int = 1, refine: int = 2, n_expect: int = 0,
-                allow_noconv: bool = False) -> ProbeResult:
-    """Shift-invert subspace iteration for shift j, converged on Ritz values in (lo, hi]."""
+                max_iter: int = 0, check_every: int = 1, refine: int = 2, n_expect: int = 0,
+                allow_noconv: bool = False, driver: str = "subspace", k_out: int = 0) -> ProbeResult:
+    """Spectral probe of shift j: shift-invert subspace iteration (Alg. 2; max_iter
+    iterations) or shift-invert block Lanczos (max_iter blocks of width V0.shape[1],
+    returning the k_out Ritz pairs nearest sigma_j)."""
     _dev(V0, "V0")
     n, k = V0.shape
+    kout = k_out if (driver == "lanczos" and k_out > 0) else k
     opts = L.ss_solve_opts()
-    opts.driver = L.SS_SUBSPACE
+    opts.driver = {"subspace": L.SS_SUBSPACE, "lanczos": L.SS_BLOCK_LANCZOS}[driver]
     opts.max_iter, opts.check_every, opts.refine, opts.tol, opts.n_expect = max_iter, check_every, refine, tol, n_expect
-    lam = np.empty(k)
-    res = np.empty(k)
-    X = torch.empty_like(V0)
+    opts.k_out = kout
+    lam = np.empty(kout)
+    res = np.empty(kout)
+    X = torch.empty((n, kout), dtype=torch.float64, device=V0.device)
     nf = C.c_int32()
     st = L.ss_probe_stats()
     rc = f.ctx.lib.ss_slice_solve(f.h, j, lo, hi, C.byref(opts), _ptr(V0), k, _ptr(lam), _ptr(X), _ptr(res),
@@ -248,16 +268,25 @@ def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: 
                        bool(st.converged), st.max_resid_in_slice, st.seconds)
 
 
-def dos_estimate(sym: Symbolic, a_vals, b_vals, steps: int, start: torch.Tensor):
-    """Lanczos DOS runs: list of (theta, zeta2) per start vector (columns of start)."""
+def _lanczos_call(fn, name, sym, a_vals, b_vals, steps, start):
     _dev(start, "start")
     nv = start.shape[1]
     th = np.zeros(steps * nv)
     z2 = np.zeros(steps * nv)
     m = np.zeros(nv, dtype=np.int32)
-    sym.ctx.check(sym.ctx.lib.ss_dos_estimate(sym.h, _ptr(a_vals), _ptr(b_vals), steps, nv, _ptr(start),
-                                              _ptr(th), _ptr(z2), _ptr(m)), "ss_dos_estimate")
+    sym.ctx.check(fn(sym.h, _ptr(a_vals), _ptr(b_vals), steps, nv, _ptr(start), _ptr(th), _ptr(z2), _ptr(m)), name)
     return [(th[c * steps:c * steps + m[c]].copy(), z2[c * steps:c * steps + m[c]].copy()) for c in range(nv)]
+
+
+def dos_estimate(sym: Symbolic, a_vals, b_vals, steps: int, start: torch.Tensor):
+    """Lanczos DOS runs on G^-1 A G^-T (B = G G^T) from i.i.d. N(0,1) start vectors y0
+    (columns of start): list of (theta, zeta2) per run."""
+    return _lanczos_call(sym.ctx.lib.ss_dos_estimate, "ss_dos_estimate", sym, a_vals, b_vals, steps, start)
+
+
+def dos_lanczos(sym: Symbolic, a_vals, b_vals, steps: int, x0: torch.Tensor):
+    """The same Lanczos runs in the B-orthonormal form from explicit start vectors x0."""
+    return _lanczos_call(sym.ctx.lib.ss_dos_lanczos, "ss_dos_lanczos", sym, a_vals, b_vals, steps, x0)
 
 
 def spmm(sym: Symbolic, a_vals, b_vals, X, alpha=None, beta=None) -> torch.Tensor:
@@ -265,8 +294,8 @@ def spmm(sym: Symbolic, a_vals, b_vals, X, alpha=None, beta=None) -> torch.Tenso
     _dev(X, "X")
     k = X.shape[1]
     dev = X.device
-    al = None if alpha is None else torch.as_tensor(np.broadcast_to(alpha, (k,)), dtype=torch.float64, device=dev).contiguous()
-    be = None if beta is None else torch.as_tensor(np.broadcast_to(beta, (k,)), dtype=torch.float64, device=dev).contiguous()
+    al = None if alpha is None else torch.tensor(np.broadcast_to(alpha, (k,)).copy(), dtype=torch.float64, device=dev)
+    be = None if beta is None else torch.tensor(np.broadcast_to(beta, (k,)).copy(), dtype=torch.float64, device=dev)
     Y = torch.empty_like(X)
     sym.ctx.check(sym.ctx.lib.ss_spmm(sym.h, _ptr(a_vals), _ptr(b_vals), _ptr(al), _ptr(be), _ptr(X), k, _ptr(Y)),
                   "ss_spmm")

@@ -194,26 +194,28 @@ static void set_smem_attrs() {
 }
 
 template <typename T>
-static int factor_run(ss_numeric *f) {
+static int factor_run(ss_numeric *f, const std::vector<int> &which) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     set_smem_attrs<T>();
-    const int ns = f->n_shift;
+    const int ns = (int)which.size();
+    if (ns == 0) return SS_OK;
     const int64_t npan = (int64_t)s->panels.size();
     std::vector<ShiftPtrs<T>> hp(ns);
     T *mt = nullptr, *wb = nullptr;
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mt, sizeof(T) * std::max<int64_t>(1, (int64_t)s->mt_max * NB * NB) * ns, st));
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wb, sizeof(T) * std::max<int64_t>(1, s->wbuf_max) * ns, st));
-    for (int j = 0; j < ns; ++j) {
-        ShiftPtrs<T> &p = hp[j];
+    for (int q = 0; q < ns; ++q) {
+        const int j = which[q];
+        ShiftPtrs<T> &p = hp[q];
         p.arena = (T *)f->arena[j];
         p.linv = f->linv[j];
         p.dblk = f->dblk[j];
         p.piv = f->piv[j];
-        p.mt = mt + (int64_t)j * s->mt_max * NB * NB;
-        p.wbuf = wb + (int64_t)j * std::max<int64_t>(1, s->wbuf_max);
-        p.counts = f->d_counts + 5 * j;
+        p.mt = mt + (int64_t)q * s->mt_max * NB * NB;
+        p.wbuf = wb + (int64_t)q * std::max<int64_t>(1, s->wbuf_max);
+        p.counts = f->d_counts + SS_NCOUNT * j;
         p.sigma = f->sigma[j];
         p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
         p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
@@ -221,14 +223,15 @@ static int factor_run(ss_numeric *f) {
     ShiftPtrs<T> *dp = nullptr;
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dp, sizeof(ShiftPtrs<T>) * ns, st));
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
-    std::vector<unsigned long long> init(5 * ns, 0);
-    for (int j = 0; j < ns; ++j) init[5 * j + 4] = 0x7ff0000000000000ull;   // +inf bits
-    SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->d_counts, init.data(), sizeof(unsigned long long) * 5 * ns,
-                                     cudaMemcpyHostToDevice, st));
+    static const unsigned long long init[SS_NCOUNT] = {0, 0, 0, 0, 0x7ff0000000000000ull /* +inf */, 0, 0};
+    for (int q = 0; q < ns; ++q)
+        SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->d_counts + SS_NCOUNT * which[q], init, sizeof(init),
+                                         cudaMemcpyHostToDevice, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));    // init is a host array
     for (int32_t l = 0; l < s->nlev; ++l) {
         const int64_t b0 = s->lev_arena_begin[l], b1 = s->lev_arena_end[l];
-        for (int j = 0; j < ns; ++j)
-            SS_CUDA_TRY(ctx, cudaMemsetAsync((T *)f->arena[j] + b0, 0, sizeof(T) * (b1 - b0), st));
+        for (int q = 0; q < ns; ++q)
+            SS_CUDA_TRY(ctx, cudaMemsetAsync((T *)f->arena[which[q]] + b0, 0, sizeof(T) * (b1 - b0), st));
         const int64_t a0 = s->asm_lev_off[l], acount = s->asm_lev_off[l + 1] - a0;
         if (acount > 0) {
             unsigned gx = (unsigned)std::min<int64_t>((acount + 255) / 256, 8192);
@@ -290,7 +293,7 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
     f->linv.assign(n_shift, nullptr);
     f->dblk.assign(n_shift, nullptr);
     f->piv.assign(n_shift, nullptr);
-    cudaError_t e = cudaMalloc((void **)&f->d_counts, sizeof(unsigned long long) * 5 * n_shift);
+    cudaError_t e = cudaMalloc((void **)&f->d_counts, sizeof(unsigned long long) * SS_NCOUNT * n_shift);
     for (int j = 0; j < n_shift && e == cudaSuccess; ++j) {
         e = cudaMalloc(&f->arena[j], esz * std::max<int64_t>(1, sym->arena));
         if (e == cudaSuccess) e = cudaMalloc((void **)&f->linv[j], sizeof(double) * NB * NB * npan);
@@ -304,7 +307,35 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
         return ctx->set_error(e == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA,
                               std::string("ss_factor: device allocation failed: ") + cudaGetErrorString(e));
     }
-    rc = precision == SS_MIXED ? factor_run<float>(f) : factor_run<double>(f);
+    std::vector<int> all(n_shift);
+    for (int j = 0; j < n_shift; ++j) all[j] = j;
+    f->shift_prec.assign(n_shift, precision);
+    f->rho.assign(n_shift, 0.0);
+    if (precision == SS_MIXED) {
+        rc = factor_run<float>(f, all);
+        // quality gate: the FP32 factor is kept only where one FP32 solve contracts the
+        // error of an FP64 refinement step by at least 1e-2; elsewhere (sigma close to an
+        // eigenvalue, large element growth) the shift is refactored in FP64
+        std::vector<int> redo;
+        for (int j = 0; j < n_shift && rc == SS_OK; ++j) {
+            rc = solve_contraction(f, j, &f->rho[j]);
+            if (rc == SS_OK && !(f->rho[j] <= 1e-2)) redo.push_back(j);
+        }
+        for (int j : redo) {
+            if (rc != SS_OK) break;
+            cudaFree(f->arena[j]);
+            f->arena[j] = nullptr;
+            cudaError_t e2 = cudaMalloc(&f->arena[j], sizeof(double) * std::max<int64_t>(1, sym->arena));
+            if (e2 != cudaSuccess) {
+                cudaGetLastError();
+                rc = ctx->set_error(SS_ERR_OOM, "ss_factor: device allocation for an FP64 refactor failed");
+            }
+            f->shift_prec[j] = SS_FP64;
+        }
+        if (rc == SS_OK) rc = factor_run<double>(f, redo);
+    } else {
+        rc = factor_run<double>(f, all);
+    }
     if (rc == SS_OK) rc = ss_factor_fetch_counts(f);
     if (rc != SS_OK && rc != SS_ERR_SINGULAR) {
         factor_free(f);
@@ -317,14 +348,14 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
 
 int ss_factor_fetch_counts(ss_numeric *f) {
     ss_ctx *ctx = f->sym->ctx;
-    f->h_counts.assign(5 * f->n_shift, 0);
+    f->h_counts.assign(SS_NCOUNT * f->n_shift, 0);
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->h_counts.data(), f->d_counts,
-                                     sizeof(unsigned long long) * 5 * f->n_shift, cudaMemcpyDeviceToHost,
+                                     sizeof(unsigned long long) * SS_NCOUNT * f->n_shift, cudaMemcpyDeviceToHost,
                                      ctx->stream));
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     f->counts_valid = true;
     for (int j = 0; j < f->n_shift; ++j)
-        if (f->h_counts[5 * j + 3]) {
+        if (f->h_counts[SS_NCOUNT * j + 3]) {
             return ctx->set_error(SS_ERR_SINGULAR, "ss_factor: a pivot fell below the singularity "
                                                    "threshold for shift " + std::to_string(j));
         }
@@ -358,22 +389,61 @@ extern "C" ss_status ss_factor_destroy(ss_numeric *f) {
 extern "C" ss_status ss_inertia(const ss_numeric *f, int32_t j, int64_t *n_neg, int64_t *n_zero,
                                 int64_t *n_pos, int32_t *tiny) {
     if (!f || j < 0 || j >= f->n_shift || !f->counts_valid) return SS_ERR_ARG;
-    if (n_neg) *n_neg = (int64_t)f->h_counts[5 * j + 0];
-    if (n_zero) *n_zero = (int64_t)f->h_counts[5 * j + 1];
-    if (n_pos) *n_pos = (int64_t)f->h_counts[5 * j + 2];
-    if (tiny) *tiny = f->h_counts[5 * j + 3] ? 1 : 0;
+    if (n_neg) *n_neg = (int64_t)f->h_counts[SS_NCOUNT * j + 0];
+    if (n_zero) *n_zero = (int64_t)f->h_counts[SS_NCOUNT * j + 1];
+    if (n_pos) *n_pos = (int64_t)f->h_counts[SS_NCOUNT * j + 2];
+    if (tiny) *tiny = f->h_counts[SS_NCOUNT * j + 3] ? 1 : 0;
     return SS_OK;
 }
 
-double ss_factor_min_pivot_ratio(const ss_numeric *f, int32_t j) {
+extern "C" ss_status ss_factor_quality(const ss_numeric *f, int32_t j, int32_t *precision_used, double *rho) {
+    if (!f || j < 0 || j >= f->n_shift) return SS_ERR_ARG;
+    if (precision_used) *precision_used = f->shift_prec[j];
+    if (rho) *rho = f->rho[j];
+    return SS_OK;
+}
+
+extern "C" ss_status ss_factor_stats(const ss_numeric *f, int32_t j, double *min_pivot_ratio, double *max_abs_l,
+                                     int64_t *n_2x2) {
+    if (!f || j < 0 || j >= f->n_shift || !f->counts_valid) return SS_ERR_ARG;
     double v;
-    std::memcpy(&v, &f->h_counts[5 * j + 4], sizeof(v));
-    return v;
+    if (min_pivot_ratio) { std::memcpy(&v, &f->h_counts[SS_NCOUNT * j + 4], sizeof(v)); *min_pivot_ratio = v; }
+    if (max_abs_l) { std::memcpy(&v, &f->h_counts[SS_NCOUNT * j + 6], sizeof(v)); *max_abs_l = v; }
+    if (n_2x2) *n_2x2 = (int64_t)f->h_counts[SS_NCOUNT * j + 5];
+    return SS_OK;
 }
 
 // ------------------------------------------------------------------ solves
 template <typename T>
+static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool backward, int dinv);
+
+template <typename T>
 int solve_permuted(ss_numeric *f, int j, T *b, int k) {
+    return solve_levels<T>(f, j, b, k, true, true, 1);
+}
+
+// x = P L^-T D^-1/2 y for an SPD factor (the Cholesky frame of B = G G^T, G = P L D^1/2):
+// y is read in the permuted order, x is written in the original order.
+int solve_half_backward(ss_numeric *f, int j, const double *y, int k, double *x) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    const int64_t tot = s->n * k;
+    const unsigned g = (unsigned)((tot + 255) / 256);
+    double *w = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&w, sizeof(double) * tot, st));
+    ss_launch(ctx, SS_K_MISC, k_dhalf<double>, g, 256, 0, st, s->n, s->d_col_panel, s->d_panels, f->dblk[j], y, w, k);
+    int rc = solve_levels<double>(f, j, w, k, false, true, 0);
+    if (rc != SS_OK) return rc;
+    ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
+              (const double *)w, x, 1);
+    SS_CUDA_TRY(ctx, cudaFreeAsync(w, st));
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+template <typename T>
+static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool backward, int dinv) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
@@ -381,7 +451,7 @@ int solve_permuted(ss_numeric *f, int j, T *b, int k) {
     const T *arena = (const T *)f->arena[j];
     const int nchunk = (k + KC - 1) / KC;
     const int nlev = (int)s->solve_levels.size();
-    for (int L = 0; L < nlev; ++L) {
+    for (int L = 0; forward && L < nlev; ++L) {
         const SolveLevel &sl = s->solve_levels[L];
         const int32_t *lp = s->d_solve_panels + sl.panel_off;
         ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, lp, s->d_panels, f->linv[j],
@@ -390,6 +460,7 @@ int solve_permuted(ss_numeric *f, int j, T *b, int k) {
             ss_launch(ctx, SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k);
     }
+    if (!backward) return SS_OK;
     int32_t maxc = 0;
     for (const SolveLevel &sl : s->solve_levels) maxc = std::max(maxc, sl.count);
     T *z = nullptr;
@@ -403,7 +474,7 @@ int solve_permuted(ss_numeric *f, int j, T *b, int k) {
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k, z);
         }
         ss_launch(ctx, SS_K_BWD_DIAG, k_bwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, 
-            lp, s->d_panels, f->linv[j], f->dblk[j], f->piv[j], z, sl.row_tiles > 0 ? 1 : 0, b, k);
+            lp, s->d_panels, f->linv[j], f->dblk[j], f->piv[j], z, sl.row_tiles > 0 ? 1 : 0, b, k, dinv);
     }
     SS_CUDA_TRY(ctx, cudaFreeAsync(z, st));
     SS_CUDA_TRY(ctx, cudaGetLastError());
@@ -423,18 +494,95 @@ __global__ void k_fill_const(int k, double v, double *x) {
     if (c < k) x[c] = v;
 }
 
-int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
-                const double *X, int k, double *Y) {
+int spmm_launch_ld(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
+                   const double *X, int64_t ldx, int k, double *Y, int64_t ldy) {
     ss_ctx *ctx = s->ctx;
     const int64_t threads = s->n * 32;
     const unsigned grid = (unsigned)((threads + 255) / 256);
-    if (k >= 16)
-        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_cols, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, alpha, beta, X, k, Y);
-    else if (k <= 4)
-        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<4>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, alpha, beta, X, k, Y);
+#define SS_SPMM_ROWS(NC)                                                                                     \
+    ss_launch(ctx, SS_K_SPMM, sss::k_spmm_rows<NC>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, \
+              alpha, beta, X, ldx, k, Y, ldy)
+    if (k <= 4)
+        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<4>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b,
+                  alpha, beta, X, ldx, k, Y, ldy);
+    else if (k < 16)
+        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<16>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a,
+                  b, alpha, beta, X, ldx, k, Y, ldy);
+    else if (k <= 32) SS_SPMM_ROWS(1);
+    else if (k <= 64) SS_SPMM_ROWS(2);
+    else if (k <= 128) SS_SPMM_ROWS(4);
+    else if (k <= 256) SS_SPMM_ROWS(8);
+    else if (k <= 512) SS_SPMM_ROWS(16);
     else
-        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<16>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b, alpha, beta, X, k, Y);
+        ss_launch(ctx, SS_K_SPMM, sss::k_spmm_cols, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b,
+                  alpha, beta, X, ldx, k, Y, ldy);
+#undef SS_SPMM_ROWS
     SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
+                const double *X, int k, double *Y) {
+    return spmm_launch_ld(s, a, b, alpha, beta, X, k, k, Y, k);
+}
+
+__global__ void k_probe_vector(int64_t n, double *r) {
+    // deterministic, sign-varying right-hand side: r_i = sin(0.7 i + 0.3) + 0.5 cos(1.9 i)
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) r[i] = sin(0.7 * (double)i + 0.3) + 0.5 * cos(1.9 * (double)i);
+}
+
+__global__ void k_absmax_diff(int64_t n, const double *__restrict__ r, const double *__restrict__ y,
+                              unsigned long long *out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double d = 0.0, m = 0.0;
+    if (i < n) { d = fabs(r[i] - y[i]); m = fabs(r[i]); }
+    for (int o = 16; o > 0; o >>= 1) {
+        d = fmax(d, __shfl_down_sync(0xffffffffu, d, o));
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[0], (unsigned long long)__double_as_longlong(isfinite(d) ? d : 1e300));
+        atomicMax(&out[1], (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// rho = ||r - (A - sigma B) x||_inf / ||r||_inf for one FP32 solve x of a probe vector r
+int solve_contraction(ss_numeric *f, int j, double *rho) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    const int64_t n = s->n;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    double *r = nullptr, *x = nullptr, *y = nullptr, *co = nullptr;
+    float *w = nullptr;
+    unsigned long long *mx = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&r, sizeof(double) * (3 * n + 2), st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&w, sizeof(float) * n, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mx, sizeof(unsigned long long) * 2, st));
+    x = r + n;
+    y = x + n;
+    co = y + n;
+    ss_launch(ctx, SS_K_MISC, k_probe_vector, g, 256, 0, st, n, r);
+    ss_launch(ctx, SS_K_MISC, k_fill_const, 1, 32, 0, st, 1, 1.0, co);
+    ss_launch(ctx, SS_K_MISC, k_fill_const, 1, 32, 0, st, 1, -f->sigma[j], co + 1);
+    ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<float, double>, g, 256, 0, st, n, 1, s->d_perm, (const double *)r, w, 0);
+    int rc = solve_permuted<float>(f, j, w, 1);
+    if (rc != SS_OK) return rc;
+    ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, float>, g, 256, 0, st, n, 1, s->d_perm, (const float *)w, x, 1);
+    if ((rc = spmm_launch(s, f->a_vals, f->b_vals, co, co + 1, x, 1, y)) != SS_OK) return rc;
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 2, st));
+    ss_launch(ctx, SS_K_MISC, k_absmax_diff, g, 256, 0, st, n, (const double *)r, (const double *)y, mx);
+    unsigned long long h[2];
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    cudaFreeAsync(r, st);
+    cudaFreeAsync(w, st);
+    cudaFreeAsync(mx, st);
+    double d, m;
+    std::memcpy(&d, &h[0], sizeof(d));
+    std::memcpy(&m, &h[1], sizeof(m));
+    *rho = m > 0 ? d / m : INFINITY;
     return SS_OK;
 }
 
@@ -447,7 +595,7 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     const unsigned g = (unsigned)((tot + 255) / 256);
     int rc;
     if (steps_done) *steps_done = 0;
-    if (f->precision == SS_FP64) {
+    if (f->shift_prec[j] == SS_FP64) {
         double *w = nullptr;
         SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&w, sizeof(double) * tot, st));
         ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm, R, w, 0);
@@ -457,7 +605,11 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
         SS_CUDA_TRY(ctx, cudaGetLastError());
         return SS_OK;
     }
-    // mixed: FP32 solves inside FP64 iterative refinement, X_0 = 0
+    // mixed: FP32 solves inside FP64 iterative refinement, X_0 = 0; a requested
+    // refinement gets at least the number of steps the shift's contraction factor needs
+    // to reach 1e-13
+    if (refine > 0 && f->rho[j] > 0.0 && f->rho[j] < 1.0)
+        refine = std::max(refine, std::min(8, (int)std::ceil(std::log(1e-13) / std::log(f->rho[j])) - 1));
     float *wf = nullptr;
     double *r = nullptr, *y = nullptr, *al = nullptr, *be = nullptr, *x = nullptr;
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wf, sizeof(float) * tot, st));

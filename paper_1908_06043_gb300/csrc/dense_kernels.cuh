@@ -14,9 +14,9 @@ namespace ssd {
 
 // ---------------------------------------------------------------- Gram G += X^T Y
 // block = 32 x 32 tile of G over one chunk of rows; 256 threads, 2 x 2 outputs each
-__global__ void __launch_bounds__(256) k_gram(int64_t n, const double *__restrict__ X, int k1,
-                                              const double *__restrict__ Y, int k2, int64_t rows_per,
-                                              double *G) {
+__global__ void __launch_bounds__(256) k_gram(int64_t n, const double *__restrict__ X, int64_t ldx, int k1,
+                                              const double *__restrict__ Y, int64_t ldy, int k2,
+                                              int64_t rows_per, double *G) {
     __shared__ double Xs[32][33], Ys[32][33];
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int64_t r_begin = blockIdx.z * rows_per;
@@ -27,8 +27,8 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, const double *__restric
         for (int q = tid; q < 32 * 32; q += 256) {
             int rr = q >> 5, c = q & 31;
             int64_t r = r0 + rr;
-            Xs[rr][c] = (r < r_end && i0 + c < k1) ? X[r * k1 + i0 + c] : 0.0;
-            Ys[rr][c] = (r < r_end && j0 + c < k2) ? Y[r * k2 + j0 + c] : 0.0;
+            Xs[rr][c] = (r < r_end && i0 + c < k1) ? X[r * ldx + i0 + c] : 0.0;
+            Ys[rr][c] = (r < r_end && j0 + c < k2) ? Y[r * ldy + j0 + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
@@ -49,11 +49,13 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, const double *__restric
         }
 }
 
-// ---------------------------------------------------------------- Y = X Q  (or X Q^T)
-// block = 64 rows x 32 columns of Y; k1 chunks of 32 through shared memory
-__global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__restrict__ X, int k1,
+// ---------------------------------------------------------------- Y = beta Y + alpha X Q  (or X Q^T)
+// block = 64 rows x 32 columns of Y; k1 chunks of 32 through shared memory.  Q is k1 x k2
+// (ldq = k2) or, transposed, k2 x k1 (ldq = k1).  beta = 0 does not read Y.
+__global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__restrict__ X, int64_t ldx, int k1,
                                                    const double *__restrict__ Q, int k2, int transq,
-                                                   double *__restrict__ Y) {
+                                                   double alpha, double beta, double *__restrict__ Y,
+                                                   int64_t ldy) {
     __shared__ double Xs[64][33], Qs[32][33];
     const int64_t r0 = blockIdx.x * 64ll;
     const int j0 = blockIdx.y * 32;
@@ -63,7 +65,7 @@ __global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__re
         for (int q = tid; q < 64 * 32; q += 256) {
             int rr = q >> 5, c = q & 31;
             int64_t r = r0 + rr;
-            Xs[rr][c] = (r < n && t0 + c < k1) ? X[r * k1 + t0 + c] : 0.0;
+            Xs[rr][c] = (r < n && t0 + c < k1) ? X[r * ldx + t0 + c] : 0.0;
         }
         for (int q = tid; q < 32 * 32; q += 256) {
             int t = q >> 5, c = q & 31;
@@ -85,17 +87,21 @@ __global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__re
 #pragma unroll
         for (int a = 0; a < 8; ++a) {
             int64_t r = r0 + tr + 8 * a;
-            if (r < n) Y[r * k2 + j0 + tc] = acc[a];
+            if (r < n) {
+                double *y = Y + r * ldy + j0 + tc;
+                *y = (beta != 0.0 ? beta * *y : 0.0) + alpha * acc[a];
+            }
         }
 }
 
 // ---------------------------------------------------------------- small Cholesky
 // G (k x k, row-major, symmetric) -> lower R with G = R R^T, upper part zeroed.
-// info[0] = 0 ok, j+1 if the j-th pivot was not positive.  One block.
+// info[0] = 0 ok, j+1 if the j-th pivot was not positive.  One block; right-looking,
+// warp w updates rows j+1+w, j+1+w+nwarps, ... of the trailing lower triangle.
 __global__ void __launch_bounds__(1024) k_chol_small(double *G, int k, int *info) {
     __shared__ double s_d;
     __shared__ int s_bad;
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     if (tid == 0) s_bad = 0;
     __syncthreads();
     for (int j = 0; j < k; ++j) {
@@ -110,16 +116,10 @@ __global__ void __launch_bounds__(1024) k_chol_small(double *G, int k, int *info
         const double inv = 1.0 / s_d;
         for (int i = j + 1 + tid; i < k; i += nt) G[(int64_t)i * k + j] *= inv;
         __syncthreads();
-        const int rem = k - j - 1;
-        const int64_t tot = (int64_t)rem * (rem + 1) / 2;
-        for (int64_t q = tid; q < tot; q += nt) {
-            // (i, l) with j < l <= i, enumerated row by row
-            int ii = (int)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
-            while ((int64_t)(ii + 1) * (ii + 2) / 2 <= q) ++ii;
-            while ((int64_t)ii * (ii + 1) / 2 > q) --ii;
-            int ll = (int)(q - (int64_t)ii * (ii + 1) / 2);
-            int i = j + 1 + ii, l = j + 1 + ll;
-            G[(int64_t)i * k + l] -= G[(int64_t)i * k + j] * G[(int64_t)l * k + j];
+        for (int i = j + 1 + wid; i < k; i += nw) {
+            const double gij = G[(int64_t)i * k + j];
+            double *gi = G + (int64_t)i * k;
+            for (int l = j + 1 + lane; l <= i; l += 32) gi[l] -= gij * G[(int64_t)l * k + j];
         }
         __syncthreads();
     }
@@ -159,70 +159,237 @@ __device__ __forceinline__ int jac_partner(int i, int r, int kp) {
     return p;
 }
 
-__device__ __forceinline__ void jac_coeffs(const double *H, int k, int kp, int r, int i, double thr,
-                                           double &al, double &be, int &y) {
-    y = jac_partner(i, r, kp);
-    al = 1.0;
-    be = 0.0;
-    if (y >= k || i >= k) { y = i; return; }
-    const int p = min(i, y), q = max(i, y);
-    const double hpq = H[(int64_t)p * k + q];
-    const double hpp = H[(int64_t)p * k + p], hqq = H[(int64_t)q * k + q];
-    if (fabs(hpq) <= thr * sqrt(fabs(hpp * hqq)) || hpq == 0.0) { y = i; return; }
-    const double th = (hqq - hpp) / (2.0 * hpq);
-    const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-    const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-    al = c;
-    be = (i == p) ? -s : s;
+// The whole eigensolve in one block: every round computes the k/2 rotations from the
+// current H, then each thread rotates whole 2 x 2 blocks {p, q} x {p', q'} of H in place
+// (H' = J^T H J touches only the rows/columns of the pairs) and row pairs of V (V' = V J).
+// Sweeps stop once off(H)^2 <= tol^2 ||H||_F^2 or after max_sweeps.  H and V are k x k
+// row-major in global memory (V must hold the identity or a previous rotation on entry).
+// Shared memory: 3 * (kp / 2) values (pair, c, s).
+__global__ void __launch_bounds__(1024) k_jacobi_block(double *H, double *V, int k, double thr, double tol,
+                                                       int max_sweeps, int *sweeps_done) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int kp = k + (k & 1);
+    const int np = kp / 2;
+    int *pp = reinterpret_cast<int *>(smem_raw);             // p of pair t (p < q)
+    int *pq = pp + np;                                        // q of pair t
+    double *pc = reinterpret_cast<double *>(pq + np + (np & 1));
+    double *ps = pc + np;
+    __shared__ double red_off[32], red_all[32];
+    __shared__ int s_stop;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        // convergence test
+        double off = 0.0, all = 0.0;
+        for (int64_t q = tid; q < (int64_t)k * k; q += nt) {
+            double v = H[q] * H[q];
+            all += v;
+            if (q / k != q % k) off += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_down_sync(0xffffffffu, off, o);
+            all += __shfl_down_sync(0xffffffffu, all, o);
+        }
+        if ((tid & 31) == 0) { red_off[tid >> 5] = off; red_all[tid >> 5] = all; }
+        __syncthreads();
+        if (tid == 0) {
+            double o2 = 0.0, a2 = 0.0;
+            for (int w = 0; w < (nt >> 5); ++w) { o2 += red_off[w]; a2 += red_all[w]; }
+            s_stop = (o2 <= tol * tol * a2) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_stop) break;
+        for (int r = 0; r < kp - 1; ++r) {
+            // rotations of this round
+            for (int t = tid; t < np; t += nt) {
+                int i = (t == 0) ? kp - 1 : (r + t) % (kp - 1);
+                int y = jac_partner(i, r, kp);
+                int p = min(i, y), q = max(i, y);
+                double c = 1.0, sn = 0.0;
+                if (q < k) {
+                    const double hpq = H[(int64_t)p * k + q];
+                    const double hpp = H[(int64_t)p * k + p], hqq = H[(int64_t)q * k + q];
+                    if (hpq != 0.0 && fabs(hpq) > thr * sqrt(fabs(hpp * hqq))) {
+                        const double th = (hqq - hpp) / (2.0 * hpq);
+                        const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        sn = tt * c;
+                    }
+                }
+                pp[t] = p; pq[t] = q; pc[t] = c; ps[t] = sn;
+            }
+            __syncthreads();
+            // H <- J^T H J on 2 x 2 blocks (pair a rows) x (pair b columns)
+            for (int64_t e = tid; e < (int64_t)np * np; e += nt) {
+                const int ta = (int)(e / np), tb = (int)(e % np);
+                const int p1 = pp[ta], q1 = pq[ta], p2 = pp[tb], q2 = pq[tb];
+                const double c1 = pc[ta], s1 = ps[ta], c2 = pc[tb], s2 = ps[tb];
+                if (s1 == 0.0 && s2 == 0.0) continue;
+                const bool rq = q1 < k, cq = q2 < k;
+                double h11 = H[(int64_t)p1 * k + p2];
+                double h12 = cq ? H[(int64_t)p1 * k + q2] : 0.0;
+                double h21 = rq ? H[(int64_t)q1 * k + p2] : 0.0;
+                double h22 = (rq && cq) ? H[(int64_t)q1 * k + q2] : 0.0;
+                // columns: new_p = c h_p - s h_q, new_q = s h_p + c h_q
+                double a11 = c2 * h11 - s2 * h12, a12 = s2 * h11 + c2 * h12;
+                double a21 = c2 * h21 - s2 * h22, a22 = s2 * h21 + c2 * h22;
+                // rows
+                double b11 = c1 * a11 - s1 * a21, b21 = s1 * a11 + c1 * a21;
+                double b12 = c1 * a12 - s1 * a22, b22 = s1 * a12 + c1 * a22;
+                if (ta == tb && s1 != 0.0) { b12 = 0.0; b21 = 0.0; }   // the annihilated pair
+                H[(int64_t)p1 * k + p2] = b11;
+                if (cq) H[(int64_t)p1 * k + q2] = b12;
+                if (rq) H[(int64_t)q1 * k + p2] = b21;
+                if (rq && cq) H[(int64_t)q1 * k + q2] = b22;
+            }
+            // V <- V J on row pairs (column pair tb)
+            for (int64_t e = tid; e < (int64_t)k * np; e += nt) {
+                const int row = (int)(e / np), tb = (int)(e % np);
+                const double s2 = ps[tb];
+                if (s2 == 0.0) continue;
+                const int p2 = pp[tb], q2 = pq[tb];
+                const double c2 = pc[tb];
+                double *vr = V + (int64_t)row * k;
+                const double vp = vr[p2], vq = vr[q2];
+                vr[p2] = c2 * vp - s2 * vq;
+                vr[q2] = s2 * vp + c2 * vq;
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && sweeps_done) *sweeps_done = sweep;
 }
 
-__global__ void k_jacobi_round(const double *__restrict__ H, double *__restrict__ H2,
-                               const double *__restrict__ V, double *__restrict__ V2, int k, int kp,
-                               int r, double thr, const int *__restrict__ done) {
-    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= (int64_t)k * k) return;
-    if (*done) {                       // converged: copy through so the ping-pong stays valid
-        H2[q] = H[q];
-        V2[q] = V[q];
-        return;
-    }
-    const int i = (int)(q / k), j = (int)(q % k);
-    double ai, bi, aj, bj;
-    int yi, yj;
-    jac_coeffs(H, k, kp, r, i, thr, ai, bi, yi);
-    jac_coeffs(H, k, kp, r, j, thr, aj, bj, yj);
-    double h = ai * aj * H[(int64_t)i * k + j];
-    if (bj != 0.0) h += ai * bj * H[(int64_t)i * k + yj];
-    if (bi != 0.0) h += bi * aj * H[(int64_t)yi * k + j];
-    if (bi != 0.0 && bj != 0.0) h += bi * bj * H[(int64_t)yi * k + yj];
-    if (i != j && ((i == yj) || (j == yi)) && bi != 0.0) h = 0.0;     // annihilated pair
-    H2[q] = h;
-    // V' = V J: column j mixes with its partner
-    double v = aj * V[(int64_t)i * k + j];
-    if (bj != 0.0) v += bj * V[(int64_t)i * k + yj];
-    V2[q] = v;
-}
+// ---------------------------------------------------------------- grid-wide Jacobi
+// Grid barrier for a cooperative launch (every block resident).  The spin on the
+// generation word is bounded: after `limit` polls the block records a timeout in *err
+// and every block leaves the kernel at its next barrier.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
 
-// sets *done when off(H)^2 <= tol^2 * ||H||_F^2 (one block)
-__global__ void k_jacobi_check(const double *__restrict__ H, int k, double tol, int *done) {
-    __shared__ double s_off[32], s_all[32];
-    double off = 0.0, all = 0.0;
-    for (int64_t q = threadIdx.x; q < (int64_t)k * k; q += blockDim.x) {
-        double v = H[q] * H[q];
-        all += v;
-        if (q / k != q % k) off += v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        off += __shfl_down_sync(0xffffffffu, off, o);
-        all += __shfl_down_sync(0xffffffffu, all, o);
-    }
-    if ((threadIdx.x & 31) == 0) { s_off[threadIdx.x >> 5] = off; s_all[threadIdx.x >> 5] = all; }
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, unsigned int nblocks, long long limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        off = 0; all = 0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { off += s_off[w]; all += s_all[w]; }
-        if (off <= tol * tol * all) *done = 1;
+        volatile unsigned int *vgen = &bar->gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == g) {
+                if (++it > limit || *(volatile int *)&bar->err) {
+                    atomicExch(&bar->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
     }
+    __syncthreads();
+    return *(volatile int *)&bar->err == 0;
+}
+
+// The same parallel-ordered Jacobi as k_jacobi_block, spread over a cooperative grid:
+// per round the rotations go to global scratch (pairs / cs), a grid barrier, the 2 x 2
+// block and row-pair updates over all threads, a grid barrier.  acc: 2 * max_sweeps
+// doubles (zeroed) for the per-sweep off-diagonal / total norms.
+__global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *V, int k, double thr, double tol,
+                                                     int max_sweeps, int2 *pairs, double2 *cs, double *acc,
+                                                     GridBar *bar, long long limit, int *sweeps_done) {
+    const int kp = k + (k & 1);
+    const int np = kp / 2;
+    const unsigned int nb = gridDim.x;
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)nb * blockDim.x;
+    __shared__ double red_off[8], red_all[8];
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        double off = 0.0, all = 0.0;
+        for (int64_t q = gtid; q < (int64_t)k * k; q += gthreads) {
+            double v = H[q] * H[q];
+            all += v;
+            if (q / k != q % k) off += v;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_down_sync(0xffffffffu, off, o);
+            all += __shfl_down_sync(0xffffffffu, all, o);
+        }
+        if ((threadIdx.x & 31) == 0) { red_off[threadIdx.x >> 5] = off; red_all[threadIdx.x >> 5] = all; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double o2 = 0.0, a2 = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { o2 += red_off[w]; a2 += red_all[w]; }
+            atomicAdd(&acc[2 * sweep], o2);
+            atomicAdd(&acc[2 * sweep + 1], a2);
+        }
+        if (!grid_barrier(bar, nb, limit)) return;
+        const double o2 = *(volatile double *)&acc[2 * sweep], a2 = *(volatile double *)&acc[2 * sweep + 1];
+        if (o2 <= tol * tol * a2) break;
+        for (int r = 0; r < kp - 1; ++r) {
+            for (int64_t t = gtid; t < np; t += gthreads) {
+                int i = (t == 0) ? kp - 1 : (int)((r + t) % (kp - 1));
+                int y = jac_partner(i, r, kp);
+                int p = min(i, y), q = max(i, y);
+                double c = 1.0, sn = 0.0;
+                if (q < k) {
+                    const double hpq = H[(int64_t)p * k + q];
+                    const double hpp = H[(int64_t)p * k + p], hqq = H[(int64_t)q * k + q];
+                    if (hpq != 0.0 && fabs(hpq) > thr * sqrt(fabs(hpp * hqq))) {
+                        const double th = (hqq - hpp) / (2.0 * hpq);
+                        const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        sn = tt * c;
+                    }
+                }
+                pairs[t] = make_int2(p, q);
+                cs[t] = make_double2(c, sn);
+            }
+            if (!grid_barrier(bar, nb, limit)) return;
+            for (int64_t e = gtid; e < (int64_t)np * np; e += gthreads) {
+                const int ta = (int)(e / np), tb = (int)(e % np);
+                const double2 r1 = cs[ta], r2 = cs[tb];
+                const double c1 = r1.x, s1 = r1.y, c2 = r2.x, s2 = r2.y;
+                if (s1 == 0.0 && s2 == 0.0) continue;
+                const int2 a1 = pairs[ta], a2p = pairs[tb];
+                const int p1 = a1.x, q1 = a1.y, p2 = a2p.x, q2 = a2p.y;
+                const bool rq = q1 < k, cq = q2 < k;
+                double h11 = H[(int64_t)p1 * k + p2];
+                double h12 = cq ? H[(int64_t)p1 * k + q2] : 0.0;
+                double h21 = rq ? H[(int64_t)q1 * k + p2] : 0.0;
+                double h22 = (rq && cq) ? H[(int64_t)q1 * k + q2] : 0.0;
+                double x11 = c2 * h11 - s2 * h12, x12 = s2 * h11 + c2 * h12;
+                double x21 = c2 * h21 - s2 * h22, x22 = s2 * h21 + c2 * h22;
+                double b11 = c1 * x11 - s1 * x21, b21 = s1 * x11 + c1 * x21;
+                double b12 = c1 * x12 - s1 * x22, b22 = s1 * x12 + c1 * x22;
+                if (ta == tb && s1 != 0.0) { b12 = 0.0; b21 = 0.0; }
+                H[(int64_t)p1 * k + p2] = b11;
+                if (cq) H[(int64_t)p1 * k + q2] = b12;
+                if (rq) H[(int64_t)q1 * k + p2] = b21;
+                if (rq && cq) H[(int64_t)q1 * k + q2] = b22;
+            }
+            for (int64_t e = gtid; e < (int64_t)k * np; e += gthreads) {
+                const int row = (int)(e / np), tb = (int)(e % np);
+                const double2 r2 = cs[tb];
+                if (r2.y == 0.0) continue;
+                const int2 a2p = pairs[tb];
+                double *vr = V + (int64_t)row * k;
+                const double vp = vr[a2p.x], vq = vr[a2p.y];
+                vr[a2p.x] = r2.x * vp - r2.y * vq;
+                vr[a2p.y] = r2.y * vp + r2.x * vq;
+            }
+            if (!grid_barrier(bar, nb, limit)) return;
+        }
+    }
+    if (gtid == 0 && sweeps_done) *sweeps_done = sweep;
 }
 
 // ascending eigenvalues with their eigenvector columns: rank by (value, index)
@@ -238,6 +405,16 @@ __global__ void k_eig_sort(const double *__restrict__ H, const double *__restric
     }
     evals[rank] = li;
     for (int r = 0; r < k; ++r) Q[(int64_t)r * k + rank] = V[(int64_t)r * k + i];
+}
+
+// copy an n x k block between leading dimensions
+__global__ void k_copy_cols(int64_t n, int k, const double *__restrict__ X, int64_t ldx, double *__restrict__ Y,
+                            int64_t ldy) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * k) return;
+    const int64_t r = q / k;
+    const int c = (int)(q - r * k);
+    Y[r * ldy + c] = X[r * ldx + c];
 }
 
 __global__ void k_set_identity(double *V, int k) {
@@ -273,6 +450,21 @@ __global__ void k_col_sumsq(int64_t n, int k, const double *__restrict__ X, int6
         double acc = 0.0;
         for (int64_t r = r0; r < r1; ++r) {
             double v = X[r * k + c];
+            acc += v * v;
+        }
+        atomicAdd(&out[c], acc);
+    }
+}
+
+// out[c] += sum_r (AX[r][c] - theta[c] BX[r][c])^2  (residual column norms, squared)
+__global__ void k_resid_sumsq(int64_t n, int k, const double *__restrict__ AX, const double *__restrict__ BX,
+                              const double *__restrict__ theta, int64_t rows_per, double *out) {
+    const int64_t r0 = blockIdx.y * rows_per, r1 = min(n, r0 + rows_per);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) {
+        const double th = theta[c];
+        double acc = 0.0;
+        for (int64_t r = r0; r < r1; ++r) {
+            double v = AX[r * k + c] - th * BX[r * k + c];
             acc += v * v;
         }
         atomicAdd(&out[c], acc);

@@ -35,7 +35,7 @@ struct ShiftPtrs {
     int32_t *piv;                   // npanels * NB
     T *mt;                          // mt_max * NB * NB
     T *wbuf;                        // wbuf_max
-    unsigned long long *counts;     // [neg, zero, pos, tiny, min_pivot_bits]
+    unsigned long long *counts;     // [neg, zero, pos, tiny, min_pivot_bits, n2x2, max_abs_l_bits]
     double sigma;
     double tiny_thr;                // pivots below this are flagged
     double norm;                    // ||A - sigma B||_1 bound (for min-pivot ratio)
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) k_diag_bk(const StepTask *__restrict__ ta
     __shared__ double dd[NB], de[NB];
     __shared__ int s_kind, s_r;        // pivot decision
     __shared__ double s_lam;
-    __shared__ unsigned long long c_neg, c_zero, c_pos, c_tiny;
+    __shared__ unsigned long long c_neg, c_zero, c_pos, c_tiny, c_2x2;
     __shared__ double s_minpiv;
     const int tid = threadIdx.x, nt = blockDim.x;
     const T *F = s.arena + tk.front_off;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_diag_bk(const StepTask *__restrict__ ta
         }
     }
     if (tid < NB) { perm[tid] = tid; dd[tid] = 0.0; de[tid] = 0.0; }
-    if (tid == 0) { c_neg = c_zero = c_pos = c_tiny = 0; s_minpiv = 1e300; }
+    if (tid == 0) { c_neg = c_zero = c_pos = c_tiny = c_2x2 = 0; s_minpiv = 1e300; }
     __syncthreads();
 
     const double alpha = 0.6403882032022076;   // (1 + sqrt(17)) / 8
@@ -186,6 +186,7 @@ __global__ void __launch_bounds__(256) k_diag_bk(const StepTask *__restrict__ ta
             const double det = a * c - b * b;
             if (tid == 0) {
                 dd[k] = a; dd[k + 1] = c; de[k] = b; de[k + 1] = 0.0;
+                c_2x2++;
                 double tr = a + c;
                 if (det < 0) { c_neg++; c_pos++; }
                 else if (det > 0) { if (tr > 0) c_pos += 2; else c_neg += 2; }
@@ -262,7 +263,16 @@ __global__ void __launch_bounds__(256) k_diag_bk(const StepTask *__restrict__ ta
         if (c_tiny) atomicAdd(&s.counts[3], c_tiny);
         double ratio = s_minpiv / (s.norm > 0 ? s.norm : 1.0);
         atomicMin(&s.counts[4], (unsigned long long)__double_as_longlong(ratio));
+        if (c_2x2) atomicAdd(&s.counts[5], c_2x2);
     }
+    // largest |L| entry of the diagonal block (element growth diagnostic)
+    double lmax = 0.0;
+    for (int q = tid; q < w * w; q += nt) {
+        int i = q / w, j = q % w;
+        if (i > j) lmax = fmax(lmax, fabs(A[i * LD + j]));
+    }
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
+    if ((tid & 31) == 0 && lmax > 0.0) atomicMax(&s.counts[6], (unsigned long long)__double_as_longlong(lmax));
 }
 
 // ---------------------------------------------------------------- K4: panel transform
@@ -325,16 +335,20 @@ __global__ void __launch_bounds__(256) k_panel(const StepTask *__restrict__ task
         for (int b = 0; b < 4; ++b) Ls[ty + 16 * b][tx + 16 * a] = acc[a][b];
     __syncthreads();
     T *W = s.wbuf + tk.wbuf_off;
+    double lmax = 0.0;
     for (int q = tid; q < w * TR; q += 256) {
         int j = q / TR, i = q % TR;
         if (i >= nr) continue;
         T l = Ls[j][i];
+        lmax = fmax(lmax, fabs((double)l));
         F[(int64_t)(tk.k0 + j) * m + rowbase + i] = l;
         double wv = (double)l * sd[j];
         if (se[j] != 0.0) wv += (double)Ls[j + 1][i] * se[j];
         if (j > 0 && se[j - 1] != 0.0) wv += (double)Ls[j - 1][i] * se[j - 1];
         W[(int64_t)j * tk.r + r0 + i] = (T)wv;
     }
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_down_sync(0xffffffffu, lmax, o));
+    if ((tid & 31) == 0 && lmax > 0.0) atomicMax(&s.counts[6], (unsigned long long)__double_as_longlong(lmax));
 }
 
 // ---------------------------------------------------------------- K3: Schur update

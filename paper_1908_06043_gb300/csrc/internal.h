@@ -164,8 +164,10 @@ struct ss_symbolic {
 
 struct ss_numeric {
     ss_symbolic *sym = nullptr;
-    int precision = SS_FP64;
+    int precision = SS_FP64;              // requested precision
     int32_t n_shift = 0;
+    std::vector<int> shift_prec;          // precision each shift was factored in
+    std::vector<double> rho;              // mixed: contraction factor of one FP32 solve
     std::vector<double> sigma;
     const double *a_vals = nullptr, *b_vals = nullptr;   // caller-owned device arrays
     double norm_a1 = 0, norm_b1 = 0;
@@ -185,19 +187,26 @@ void ss_symbolic_free_device(ss_symbolic *s);
 int ss_factor_fetch_counts(ss_numeric *f);
 int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
                      int32_t n_shift, int32_t precision, ss_numeric **out);
-double ss_factor_min_pivot_ratio(const ss_numeric *f, int32_t j);
+constexpr int SS_NCOUNT = 7;   // per-shift device counters: neg, zero, pos, tiny, min pivot, 2x2, max |L|
 int ss_norm1(ss_symbolic *s, const double *vals, double *out);
+int solve_contraction(ss_numeric *f, int j, double *rho);
 // in-place solve (A - sigma_j B) x = b of a permuted-order N x k block
 template <typename T> int solve_permuted(ss_numeric *f, int j, T *b, int k);
 // X = (A - sigma_j B)^-1 R in the original order (FP64 in/out, refinement for mixed)
 int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done);
 int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
                 const double *X, int k, double *Y);
+int spmm_launch_ld(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
+                   const double *X, int64_t ldx, int k, double *Y, int64_t ldy);
+// x = P L^-T D^-1/2 y (y permuted order, x original order), SPD factors only
+int solve_half_backward(ss_numeric *f, int j, const double *y, int k, double *x);
 
 #define SS_CUDA_TRY(ctx, call)                                                           \
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
-        if (e_ != cudaSuccess)                                                           \
+        if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError(); /* clear a non-sticky error so later calls start clean */ \
             return (ctx)->set_error(e_ == cudaErrorMemoryAllocation ? SS_ERR_OOM : SS_ERR_CUDA, \
                                     std::string(#call) + ": " + cudaGetErrorString(e_)); \
+        }                                                                                \
     } while (0)

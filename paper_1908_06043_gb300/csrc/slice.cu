@@ -44,8 +44,9 @@ struct DevBuf {
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-// G = X^T Y (k1 x k2)
-int gram(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Y, int k2, double *G) {
+// G = X^T Y (k1 x k2, contiguous); X, Y n x k with leading dimensions ldx, ldy
+int gram_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Y, int64_t ldy, int k2,
+            double *G) {
     cudaStream_t st = ctx->stream;
     SS_CUDA_TRY(ctx, cudaMemsetAsync(G, 0, sizeof(double) * k1 * k2, st));
     const int64_t bxy = (int64_t)cdiv(k1, 32) * cdiv(k2, 32);
@@ -53,16 +54,27 @@ int gram(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Y, int k
     nz = std::min<int64_t>(nz, std::max<int64_t>(1, n / 256));
     int64_t per = ((n + nz - 1) / nz + 31) / 32 * 32;
     nz = (n + per - 1) / per;
-    ss_launch(ctx, SS_K_GRAM, ssd::k_gram, dim3(cdiv(k1, 32), cdiv(k2, 32), (unsigned)std::max<int64_t>(1, nz)), 256, 0, st, 
-        n, X, k1, Y, k2, per, G);
+    ss_launch(ctx, SS_K_GRAM, ssd::k_gram, dim3(cdiv(k1, 32), cdiv(k2, 32), (unsigned)std::max<int64_t>(1, nz)), 256,
+              0, st, n, X, ldx, k1, Y, ldy, k2, per, G);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+int gram(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Y, int k2, double *G) {
+    return gram_ld(ctx, X, k1, n, k1, Y, k2, k2, G);
+}
+
+// Y = beta Y + alpha X Q (Q k1 x k2) or X Q^T (Q k2 x k1)
+int gemm_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Q, int k2, int transq,
+            double alpha, double beta, double *Y, int64_t ldy) {
+    ss_launch(ctx, SS_K_GEMM, ssd::k_gemm_tall, dim3(cdiv(n, 64), cdiv(k2, 32)), 256, 0, ctx->stream, n, X, ldx, k1,
+              Q, k2, transq, alpha, beta, Y, ldy);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }
 
 int gemm_tall(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Q, int k2, int transq, double *Y) {
-    ss_launch(ctx, SS_K_GEMM, ssd::k_gemm_tall, dim3(cdiv(n, 64), cdiv(k2, 32)), 256, 0, ctx->stream, n, X, k1, Q, k2, transq, Y);
-    SS_CUDA_TRY(ctx, cudaGetLastError());
-    return SS_OK;
+    return gemm_ld(ctx, X, k1, n, k1, Q, k2, transq, 1.0, 0.0, Y, k2);
 }
 
 __global__ void k_symmetrize(double *H, int k) {
@@ -91,29 +103,53 @@ __global__ void k_add_shift_diag(double *G, int k, double rel) {
 // Symmetric eigenproblem of H (k x k, destroyed): ascending evals (device) and Q.
 int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf) {
     cudaStream_t st = ctx->stream;
-    double *H2, *V, *V2;
-    int *done;
-    TRY_ALLOC(ctx, buf.get(&H2, (size_t)k * k));
+    double *V;
     TRY_ALLOC(ctx, buf.get(&V, (size_t)k * k));
-    TRY_ALLOC(ctx, buf.get(&V2, (size_t)k * k));
-    TRY_ALLOC(ctx, buf.get(&done, 1));
     const unsigned g = cdiv((int64_t)k * k, 256);
     ss_launch(ctx, SS_K_SMALL_DENSE, k_symmetrize, g, 256, 0, st, H, k);
     ss_launch(ctx, SS_K_JACOBI, ssd::k_set_identity, g, 256, 0, st, V, k);
-    SS_CUDA_TRY(ctx, cudaMemsetAsync(done, 0, sizeof(int), st));
-    const int kp = k + (k & 1);
-    int hdone = 0;
-    for (int sweep = 0; sweep < 30 && !hdone && k > 1; ++sweep) {
-        for (int r = 0; r < kp - 1; ++r) {
-            ss_launch(ctx, SS_K_JACOBI, ssd::k_jacobi_round, g, 256, 0, st, H, H2, V, V2, k, kp, r, 1e-18, done);
-            std::swap(H, H2);
-            std::swap(V, V2);
-        }
-        ss_launch(ctx, SS_K_JACOBI, ssd::k_jacobi_check, 1, 1024, 0, st, H, k, 1e-15, done);
-        SS_CUDA_TRY(ctx, cudaMemcpyAsync(&hdone, done, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (k > 1 && k <= 96) {
+        const int np = (k + (k & 1)) / 2;
+        const size_t smem = sizeof(int) * (2 * np + 2) + sizeof(double) * 2 * np;
+        ss_launch(ctx, SS_K_JACOBI, ssd::k_jacobi_block, 1, 1024, smem, st, H, V, k, 1e-18, 1e-14, 40,
+                  (int *)nullptr);
+    } else if (k > 96) {
+        // cooperative grid: every block resident, rounds separated by a bounded barrier
+        const int np = (k + (k & 1)) / 2, max_sweeps = 40;
+        int2 *pairs;
+        double2 *cs;
+        double *acc;
+        ssd::GridBar *bar;
+        int *status;
+        TRY_ALLOC(ctx, buf.get(&pairs, (size_t)np));
+        TRY_ALLOC(ctx, buf.get(&cs, (size_t)np));
+        TRY_ALLOC(ctx, buf.get(&acc, (size_t)2 * max_sweeps));
+        TRY_ALLOC(ctx, buf.get(&bar, 1));
+        TRY_ALLOC(ctx, buf.get(&status, 1));
+        SS_CUDA_TRY(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * 2 * max_sweeps, st));
+        SS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, sizeof(ssd::GridBar), st));
+        int per_sm = 0;
+        SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssd::k_jacobi_grid, 256, 0));
+        const int64_t want = ((int64_t)np * np + 255) / 256;
+        int nb = (int)std::min<int64_t>(std::max(1, std::min(per_sm, 2)) * (int64_t)ctx->sm_count, std::max<int64_t>(1, want));
+        const double thr = 1e-18, tol = 1e-14;
+        const long long limit = 20000000;      // polls of about 64 ns: ~1 s
+        int *sw = status;
+        void *args[] = {(void *)&H, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol, (void *)&max_sweeps,
+                        (void *)&pairs, (void *)&cs, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
+        g_ss_launches.fetch_add(1, std::memory_order_relaxed);
+        size_t slot = 0;
+        const bool prof = ctx->prof_mask & (1u << SS_K_JACOBI);
+        if (prof) slot = ss_prof_begin(ctx, SS_K_JACOBI);
+        SS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)ssd::k_jacobi_grid, dim3(nb), dim3(256), args, 0, st));
+        if (prof) ss_prof_end(ctx, SS_K_JACOBI, slot);
+        int herr = 0;
+        SS_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
         SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        if (herr) return ctx->set_error(SS_ERR_TIMEOUT, "Jacobi eigensolver: grid barrier timed out");
     }
-    ss_launch(ctx, SS_K_JACOBI, ssd::k_eig_sort, cdiv(k, 256), 256, 0, st, H, V, k, evals, Q);
+    ss_launch(ctx, SS_K_JACOBI, ssd::k_eig_sort, cdiv(k, 256), 256, 0, st, (const double *)H, (const double *)V, k,
+              evals, Q);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }
@@ -155,30 +191,44 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
     return SS_OK;
 }
 
-// Rayleigh-Ritz on B-orthonormal V: H = V^T A V = Q Theta Q^T, X = V Q, and the
-// normalised residuals ||A x - theta B x|| / (||A||_1 ||x||).  V <- X.
-int rayleigh_ritz(ss_numeric *f, double *&V, double *&Wk, double *T, int k, double *H, double *Q,
-                  double *theta_d, double *resid_d, double *rr, double *xx, double *be, DevBuf &buf) {
+// B-orthonormalise W in place, carrying BW = B W along: G = W^T BW = R R^T,
+// W <- W R^-T, BW <- BW R^-T, twice (Cholesky-QR2); a failed Cholesky is retried with
+// a diagonal shift of G (shifted Cholesky-QR).  Wt, BWt: n x k scratch (swapped in).
+int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&BWt, int k, double *G, double *Rinv,
+                 int *info) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     int rc;
-    if ((rc = spmm_launch(s, f->a_vals, f->a_vals, nullptr, nullptr, V, k, Wk)) != SS_OK) return rc;
-    if ((rc = gram(ctx, V, s->n, k, Wk, k, H)) != SS_OK) return rc;
-    if ((rc = sym_eig(ctx, H, k, theta_d, Q, buf)) != SS_OK) return rc;
-    if ((rc = gemm_tall(ctx, V, s->n, k, Q, k, 0, Wk)) != SS_OK) return rc;
-    std::swap(V, Wk);
-    ss_launch(ctx, SS_K_MISC, ssd::k_neg_scale, cdiv(k, 256), 256, 0, st, k, theta_d, be);
-    if ((rc = spmm_launch(s, f->a_vals, f->b_vals, nullptr, be, V, k, T)) != SS_OK) return rc;
-    SS_CUDA_TRY(ctx, cudaMemsetAsync(rr, 0, sizeof(double) * 2 * k, st));
-    const int64_t per = 2048;
-    ss_launch(ctx, SS_K_MISC, ssd::k_col_sumsq, dim3(cdiv(k, 128), cdiv(s->n, per)), 128, 0, st, s->n, k, T, per, rr);
-    ss_launch(ctx, SS_K_MISC, ssd::k_col_sumsq, dim3(cdiv(k, 128), cdiv(s->n, per)), 128, 0, st, s->n, k, V, per, xx);
-    ss_launch(ctx, SS_K_MISC, ssd::k_resid_finish, cdiv(k, 256), 256, 0, st, k, rr, xx, f->norm_a1, resid_d);
-    SS_CUDA_TRY(ctx, cudaGetLastError());
+    for (int pass = 0; pass < 2; ++pass) {
+        int hinfo = 0;
+        for (int attempt = 0; attempt < 3; ++attempt) {
+            if ((rc = gram(ctx, W, s->n, k, BW, k, G)) != SS_OK) return rc;
+            ss_launch(ctx, SS_K_SMALL_DENSE, k_symmetrize, cdiv((int64_t)k * k, 256), 256, 0, st, G, k);
+            if (attempt > 0) {
+                const double rel = 11.0 * ((double)s->n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 *
+                                   (attempt == 1 ? 1.0 : 1e4);
+                ss_launch(ctx, SS_K_SMALL_DENSE, k_add_shift_diag, 1, 256, 0, st, G, k, rel);
+            }
+            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, 0, st, G, k, info);
+            SS_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+            if (hinfo == 0) break;
+        }
+        if (hinfo != 0) return ctx->set_error(SS_ERR_NOCONV, "Cholesky-QR: basis is numerically rank deficient");
+        ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 128), 128, 0, st, (const double *)G, k, Rinv);
+        if ((rc = gemm_tall(ctx, W, s->n, k, Rinv, k, 1, Wt)) != SS_OK) return rc;
+        if ((rc = gemm_tall(ctx, BW, s->n, k, Rinv, k, 1, BWt)) != SS_OK) return rc;
+        std::swap(W, Wt);
+        std::swap(BW, BWt);
+    }
     return SS_OK;
 }
 
+// Alg. 2 with a Rayleigh-Ritz step every check_every iterations.  Per iteration: one
+// solve (A - sigma B) W = B V, one SpMM for B W, Cholesky-QR2 in the B inner product
+// carrying B W, and at a check one SpMM for A W, H = W^T A W = Q Theta Q^T, X = W Q with
+// A X and B X formed as (A W) Q and (B W) Q, the residual norms, and V = X, B V = B X.
 int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_opts &o, const double *V0, int k,
                      double *lambda, double *X, double *resid, int32_t *n_found, ss_probe_stats *stats) {
     ss_symbolic *s = f->sym;
@@ -187,66 +237,102 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     auto t0 = std::chrono::steady_clock::now();
     const int64_t n = s->n;
     DevBuf buf(st);
-    double *V, *Wk, *T, *G, *Rinv, *Q, *theta_d, *resid_d, *rr, *be;
+    double *V, *BV, *W, *BW, *T1, *T2, *G, *Rinv, *Q, *theta_d, *resid_d, *rr;
     int *info;
     TRY_ALLOC(ctx, buf.get(&V, (size_t)n * k));
-    TRY_ALLOC(ctx, buf.get(&Wk, (size_t)n * k));
-    TRY_ALLOC(ctx, buf.get(&T, (size_t)n * k));
+    TRY_ALLOC(ctx, buf.get(&BV, (size_t)n * k));
+    TRY_ALLOC(ctx, buf.get(&W, (size_t)n * k));
+    TRY_ALLOC(ctx, buf.get(&BW, (size_t)n * k));
+    TRY_ALLOC(ctx, buf.get(&T1, (size_t)n * k));
+    TRY_ALLOC(ctx, buf.get(&T2, (size_t)n * k));
     TRY_ALLOC(ctx, buf.get(&G, (size_t)k * k));
     TRY_ALLOC(ctx, buf.get(&Rinv, (size_t)k * k));
     TRY_ALLOC(ctx, buf.get(&Q, (size_t)k * k));
     TRY_ALLOC(ctx, buf.get(&theta_d, (size_t)k));
     TRY_ALLOC(ctx, buf.get(&resid_d, (size_t)k));
     TRY_ALLOC(ctx, buf.get(&rr, (size_t)2 * k));
-    TRY_ALLOC(ctx, buf.get(&be, (size_t)k));
     TRY_ALLOC(ctx, buf.get(&info, 1));
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(V, V0, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
     int rc;
-    if ((rc = cholqr_b(f, V, Wk, k, G, Rinv, info, buf)) != SS_OK) return rc;
+    if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, BV)) != SS_OK) return rc;
+    if ((rc = cholqr_track(f, V, BV, T1, T2, k, G, Rinv, info)) != SS_OK) return rc;
     std::vector<double> th(k), rs(k);
     int it = 0, refine_total = 0;
-    bool conv = false;
-    double maxr = 0.0;
+    bool conv = false, have_rr = false, near_conv = false;
+    double maxr = 0.0, maxr_all = INFINITY;
     int nf = 0;
     const int max_iter = o.max_iter > 0 ? o.max_iter : 200;
     const int every = o.check_every > 0 ? o.check_every : 1;
     const int refine = o.refine > 0 ? o.refine : 2;
     const double tol = o.tol > 0 ? o.tol : 1e-10;
+    const int64_t per = 2048;
     while (it < max_iter) {
         ++it;
-        // V <- (A - sigma B)^-1 B V  (Alg. 2 step 3), then B-orthonormalise (step 4)
-        if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, T)) != SS_OK) return rc;
+        // W = (A - sigma B)^-1 B V (Alg. 2 step 3); a mixed factor runs plain FP32 solves
+        // while the window's residuals are above 1e-6 and FP64 refinement afterwards
         int done_ref = 0;
-        if ((rc = solve_apply(f, j, T, k, V, refine, &done_ref)) != SS_OK) return rc;
+        const int ref_now = (f->shift_prec[j] == SS_MIXED && !near_conv) ? 0 : refine;
+        if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref)) != SS_OK) return rc;
         refine_total += done_ref;
-        if ((rc = cholqr_b(f, V, Wk, k, G, Rinv, info, buf)) != SS_OK) return rc;
-        if (it % every == 0 || it == max_iter) {
-            if ((rc = rayleigh_ritz(f, V, Wk, T, k, G, Q, theta_d, resid_d, rr, rr + k, be, buf)) != SS_OK)
-                return rc;
-            SS_CUDA_TRY(ctx, cudaMemcpyAsync(th.data(), theta_d, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-            SS_CUDA_TRY(ctx, cudaMemcpyAsync(rs.data(), resid_d, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
-            SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-            // a Ritz value in the window counts once its residual meets tol; unconverged
-            // ones in the window may be spurious mixtures from the edge of the basis
-            // (eigenvalues at equal distance on both sides of sigma), which validation by
-            // inertia counts removes (Section 2.3), so with n_expect given the probe stops
-            // as soon as n_expect of them have converged
-            nf = 0;
-            maxr = 0.0;
-            int nin = 0;
-            for (int i = 0; i < k; ++i) {
-                if (th[i] > lo && th[i] <= hi) {
-                    ++nin;
-                    if (rs[i] <= tol) {
-                        ++nf;
-                        maxr = std::max(maxr, rs[i]);
-                    }
+        if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;
+        if ((rc = cholqr_track(f, W, BW, T1, T2, k, G, Rinv, info)) != SS_OK) return rc;   // Alg. 2 step 4
+        if (it % every != 0 && it != max_iter) {
+            std::swap(V, W);
+            std::swap(BV, BW);
+            continue;
+        }
+        // Rayleigh-Ritz: H = W^T A W; the dead V / BV buffers take A W and A X
+        double *AW = V, *AX = BV;
+        if ((rc = spmm_launch(s, f->a_vals, f->a_vals, nullptr, nullptr, W, k, AW)) != SS_OK) return rc;
+        if ((rc = gram(ctx, W, n, k, AW, k, G)) != SS_OK) return rc;
+        if ((rc = sym_eig(ctx, G, k, theta_d, Q, buf)) != SS_OK) return rc;
+        if ((rc = gemm_tall(ctx, W, n, k, Q, k, 0, T1)) != SS_OK) return rc;      // X
+        if ((rc = gemm_tall(ctx, BW, n, k, Q, k, 0, T2)) != SS_OK) return rc;     // B X
+        if ((rc = gemm_tall(ctx, AW, n, k, Q, k, 0, AX)) != SS_OK) return rc;     // A X
+        SS_CUDA_TRY(ctx, cudaMemsetAsync(rr, 0, sizeof(double) * 2 * k, st));
+        ss_launch(ctx, SS_K_MISC, ssd::k_resid_sumsq, dim3(cdiv(k, 128), cdiv(n, per)), 128, 0, st, n, k,
+                  (const double *)AX, (const double *)T2, (const double *)theta_d, per, rr);
+        ss_launch(ctx, SS_K_MISC, ssd::k_col_sumsq, dim3(cdiv(k, 128), cdiv(n, per)), 128, 0, st, n, k,
+                  (const double *)T1, per, rr + k);
+        ss_launch(ctx, SS_K_MISC, ssd::k_resid_finish, cdiv(k, 256), 256, 0, st, k, (const double *)rr,
+                  (const double *)(rr + k), f->norm_a1, resid_d);
+        // V = X, B V = B X
+        std::swap(V, T1);
+        std::swap(BV, T2);
+        SS_CUDA_TRY(ctx, cudaMemcpyAsync(th.data(), theta_d, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        SS_CUDA_TRY(ctx, cudaMemcpyAsync(rs.data(), resid_d, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+        SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        have_rr = true;
+        // a Ritz value in the window counts once its residual meets tol; unconverged
+        // ones in the window may be spurious mixtures from the edge of the basis
+        // (eigenvalues at equal distance on both sides of sigma), which validation by
+        // inertia counts removes (Section 2.3), so with n_expect given the probe stops
+        // as soon as n_expect of them have converged
+        nf = 0;
+        maxr = 0.0;
+        maxr_all = 0.0;
+        int nin = 0;
+        for (int i = 0; i < k; ++i) {
+            if (th[i] > lo && th[i] <= hi) {
+                ++nin;
+                maxr_all = std::max(maxr_all, rs[i]);
+                if (rs[i] <= tol) {
+                    ++nf;
+                    maxr = std::max(maxr, rs[i]);
                 }
             }
-            const bool done = o.n_expect > 0 ? (nf >= o.n_expect) : (nf == nin);
-            if (done && it >= 2) { conv = true; break; }
         }
+        const bool done = o.n_expect > 0 ? (nf >= o.n_expect) : (nf == nin);
+        if (done && it >= 2) { conv = true; break; }
+        // FP64 refinement starts once the window's target count is within 1e-6
+        int n6 = 0;
+        for (int i = 0; i < k; ++i)
+            if (th[i] > lo && th[i] <= hi && rs[i] <= 1e-6) ++n6;
+        const int target = o.n_expect > 0 ? o.n_expect : std::max(1, nin - 2);
+        near_conv = near_conv || n6 >= target;
     }
+    (void)have_rr;
+    (void)maxr_all;
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(X, V, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     std::memcpy(lambda, th.data(), sizeof(double) * k);
@@ -263,24 +349,151 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     return SS_OK;
 }
 
-// B-orthonormal Lanczos on B^-1 A (Section 3.1) for n_vec start vectors at once.
-int dos_impl(ss_symbolic *s, const double *a_vals, const double *b_vals, int steps, int nv, const double *start,
-             double *theta, double *zeta2, int32_t *m_run) {
+// Shift-invert block Lanczos (the SI-Lanczos the paper names as the alternative to
+// Alg. 2, Section 1) in the B inner product with full re-orthogonalisation: V_1 =
+// CholQR_B(V0), V_{i+1} = CholQR_B((I - P) O V_i) with O = (A - sigma B)^-1 B and P the
+// B-orthogonal projector on every earlier block (applied twice), then one Rayleigh-Ritz
+// on the whole basis (H = V^T A V) and the k_out Ritz pairs nearest sigma.
+int block_lanczos_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_opts &o, const double *V0,
+                       int p, int kout, double *lambda, double *X, double *resid, int32_t *n_found,
+                       ss_probe_stats *stats) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t n = s->n;
+    const int m = o.max_iter > 0 ? o.max_iter : 6;
+    const int64_t dmax = (int64_t)m * p;
+    if (kout > dmax) return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: k_out exceeds the Krylov basis");
+    const int refine = o.refine > 0 ? o.refine : 2;
+    const double tol = o.tol > 0 ? o.tol : 1e-10;
+    const double sigma = f->sigma[j];
+    DevBuf buf(st);
+    double *Vb, *AV, *W, *Wk, *T, *Gp, *Rinv, *Hc, *H, *Q, *theta_d, *Qsel, *resid_d, *rr, *be;
+    int *info;
+    TRY_ALLOC(ctx, buf.get(&Vb, (size_t)n * dmax));
+    TRY_ALLOC(ctx, buf.get(&AV, (size_t)n * dmax));
+    TRY_ALLOC(ctx, buf.get(&W, (size_t)n * p));
+    TRY_ALLOC(ctx, buf.get(&Wk, (size_t)n * std::max<int64_t>(p, kout)));
+    TRY_ALLOC(ctx, buf.get(&T, (size_t)n * std::max<int64_t>(p, kout)));
+    TRY_ALLOC(ctx, buf.get(&Gp, (size_t)p * p));
+    TRY_ALLOC(ctx, buf.get(&Rinv, (size_t)p * p));
+    TRY_ALLOC(ctx, buf.get(&Hc, (size_t)dmax * p));
+    TRY_ALLOC(ctx, buf.get(&H, (size_t)dmax * dmax));
+    TRY_ALLOC(ctx, buf.get(&Q, (size_t)dmax * dmax));
+    TRY_ALLOC(ctx, buf.get(&theta_d, (size_t)dmax));
+    TRY_ALLOC(ctx, buf.get(&Qsel, (size_t)dmax * kout));
+    TRY_ALLOC(ctx, buf.get(&resid_d, (size_t)kout));
+    TRY_ALLOC(ctx, buf.get(&rr, (size_t)2 * kout));
+    TRY_ALLOC(ctx, buf.get(&be, (size_t)kout));
+    TRY_ALLOC(ctx, buf.get(&info, 1));
+    int rc;
+    const unsigned gcopy = cdiv(n * p, 256);
+    // V_1 = CholQR_B(V0)
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(W, V0, sizeof(double) * n * p, cudaMemcpyDeviceToDevice, st));
+    if ((rc = cholqr_b(f, W, Wk, p, Gp, Rinv, info, buf)) != SS_OK) return rc;
+    ss_launch(ctx, SS_K_MISC, ssd::k_copy_cols, gcopy, 256, 0, st, n, p, (const double *)W, (int64_t)p, Vb, dmax);
+    int64_t cur = p;
+    int refine_total = 0, blocks = 1;
+    for (int blk = 1; blk < m; ++blk) {
+        // W = O V_blk = (A - sigma B)^-1 B V_blk
+        if ((rc = spmm_launch_ld(s, f->b_vals, f->b_vals, nullptr, nullptr, Vb + (cur - p), dmax, p, T, p)) != SS_OK)
+            return rc;
+        int done_ref = 0;
+        if ((rc = solve_apply(f, j, T, p, W, refine, &done_ref)) != SS_OK) return rc;
+        refine_total += done_ref;
+        for (int pass = 0; pass < 2; ++pass) {    // W -= V (V^T B W), twice
+            if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, p, T)) != SS_OK) return rc;
+            if ((rc = gram_ld(ctx, Vb, dmax, n, (int)cur, T, p, p, Hc)) != SS_OK) return rc;
+            if ((rc = gemm_ld(ctx, Vb, dmax, n, (int)cur, Hc, p, 0, -1.0, 1.0, W, p)) != SS_OK) return rc;
+        }
+        if ((rc = cholqr_b(f, W, Wk, p, Gp, Rinv, info, buf)) != SS_OK) return rc;
+        ss_launch(ctx, SS_K_MISC, ssd::k_copy_cols, gcopy, 256, 0, st, n, p, (const double *)W, (int64_t)p,
+                  Vb + cur, dmax);
+        cur += p;
+        ++blocks;
+    }
+    // Rayleigh-Ritz on the basis: H = V^T A V
+    const int d = (int)cur;
+    if ((rc = spmm_launch_ld(s, f->a_vals, f->a_vals, nullptr, nullptr, Vb, dmax, d, AV, dmax)) != SS_OK) return rc;
+    if ((rc = gram_ld(ctx, Vb, dmax, n, d, AV, dmax, d, H)) != SS_OK) return rc;
+    if ((rc = sym_eig(ctx, H, d, theta_d, Q, buf)) != SS_OK) return rc;
+    std::vector<double> th(d), hq((size_t)d * d);
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(th.data(), theta_d, sizeof(double) * d, cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(hq.data(), Q, sizeof(double) * d * d, cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    // the kout Ritz values nearest sigma, returned in ascending order
+    std::vector<int> idx(d);
+    for (int i = 0; i < d; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        return std::fabs(th[x] - sigma) < std::fabs(th[y] - sigma);
+    });
+    idx.resize(kout);
+    std::sort(idx.begin(), idx.end());
+    std::vector<double> qs((size_t)d * kout);
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < kout; ++c) qs[(size_t)r * kout + c] = hq[(size_t)r * d + idx[c]];
+    std::vector<double> ths(kout);
+    for (int c = 0; c < kout; ++c) ths[c] = th[idx[c]];
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(Qsel, qs.data(), sizeof(double) * d * kout, cudaMemcpyHostToDevice, st));
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(theta_d, ths.data(), sizeof(double) * kout, cudaMemcpyHostToDevice, st));
+    if ((rc = gemm_ld(ctx, Vb, dmax, n, d, Qsel, kout, 0, 1.0, 0.0, X, kout)) != SS_OK) return rc;
+    // residuals ||A x - theta B x|| / (||A||_1 ||x||)
+    ss_launch(ctx, SS_K_MISC, ssd::k_neg_scale, cdiv(kout, 256), 256, 0, st, kout, (const double *)theta_d, be);
+    if ((rc = spmm_launch(s, f->a_vals, f->b_vals, nullptr, be, X, kout, T)) != SS_OK) return rc;
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(rr, 0, sizeof(double) * 2 * kout, st));
+    const int64_t per = 2048;
+    ss_launch(ctx, SS_K_MISC, ssd::k_col_sumsq, dim3(cdiv(kout, 128), cdiv(n, per)), 128, 0, st, n, kout,
+              (const double *)T, per, rr);
+    ss_launch(ctx, SS_K_MISC, ssd::k_col_sumsq, dim3(cdiv(kout, 128), cdiv(n, per)), 128, 0, st, n, kout,
+              (const double *)X, per, rr + kout);
+    ss_launch(ctx, SS_K_MISC, ssd::k_resid_finish, cdiv(kout, 256), 256, 0, st, kout, (const double *)rr,
+              (const double *)(rr + kout), f->norm_a1, resid_d);
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(resid, resid_d, sizeof(double) * kout, cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    std::memcpy(lambda, ths.data(), sizeof(double) * kout);
+    int nf = 0;
+    double maxr = 0.0;
+    for (int i = 0; i < kout; ++i)
+        if (ths[i] > lo && ths[i] <= hi && resid[i] <= tol) { ++nf; maxr = std::max(maxr, resid[i]); }
+    if (n_found) *n_found = nf;
+    const bool conv = o.n_expect > 0 ? nf >= o.n_expect : true;
+    if (stats) {
+        stats->iterations = blocks;
+        stats->refine_steps = refine_total;
+        stats->converged = conv ? 1 : 0;
+        stats->max_resid_in_slice = maxr;
+        stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!conv) return ctx->set_error(SS_ERR_NOCONV, "ss_slice_solve: fewer than n_expect converged Ritz pairs");
+    return SS_OK;
+}
+
+// B = P L D L^T P^T: the multifrontal LDL^T at sigma = 0 of the pencil (B, 0), FP64.
+// Fails with SS_ERR_NOT_SPD unless every eigenvalue of D is positive.
+int factor_spd_b(ss_symbolic *s, const double *b_vals, ss_numeric **out) {
+    ss_ctx *ctx = s->ctx;
+    const double zero = 0.0;
+    ss_numeric *fb = nullptr;
+    int rc = ss_factor_create(s, b_vals, b_vals, &zero, 1, SS_FP64, &fb);
+    if (rc != SS_OK && rc != SS_ERR_SINGULAR) return rc;
+    int64_t neg = 0, zr = 0, pos = 0;
+    ss_inertia(fb, 0, &neg, &zr, &pos, nullptr);
+    if (neg != 0 || zr != 0 || rc == SS_ERR_SINGULAR) {
+        ss_factor_destroy(fb);
+        return ctx->set_error(SS_ERR_NOT_SPD, "B is not positive definite (inertia " + std::to_string(neg) + "/" +
+                                                  std::to_string(zr) + "/" + std::to_string(pos) + ")");
+    }
+    *out = fb;
+    return SS_OK;
+}
+
+int lanczos_impl(ss_symbolic *s, ss_numeric *fb, const double *a_vals, const double *b_vals, int steps, int nv,
+                 const double *start, double *theta, double *zeta2, int32_t *m_run) {
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     const int64_t n = s->n;
-    const double zero = 0.0;
-    ss_numeric *fb = nullptr;
-    // B = P L D L^T P^T: the same multifrontal LDL^T at sigma = 0 of the pencil (B, 0)
-    int rc = ss_factor_create(s, b_vals, b_vals, &zero, 1, SS_FP64, &fb);
-    if (rc != SS_OK && rc != SS_ERR_SINGULAR) return rc;
-    struct Guard { ss_numeric *f; ~Guard() { ss_factor_destroy(f); } } guard{fb};
-    int64_t neg = 0, zr = 0, pos = 0;
-    ss_inertia(fb, 0, &neg, &zr, &pos, nullptr);
-    if (neg != 0 || zr != 0 || rc == SS_ERR_SINGULAR)
-        return ctx->set_error(SS_ERR_NOT_SPD, "ss_dos_estimate: B is not positive definite (inertia " +
-                                                  std::to_string(neg) + "/" + std::to_string(zr) + "/" +
-                                                  std::to_string(pos) + ")");
+    int rc;
     DevBuf buf(st);
     const int64_t blk = n * nv;
     double *X, *BX, *u, *w, *bw, *h, *alpha, *beta, *nrm;
@@ -366,9 +579,15 @@ extern "C" ss_status ss_slice_solve(ss_numeric *f, int32_t j, double lo, double 
         return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: bad argument");
     ss_solve_opts o{};
     if (opts) o = *opts;
-    if (o.driver != SS_SUBSPACE) return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: unsupported driver");
+    if (o.driver != SS_SUBSPACE && o.driver != SS_BLOCK_LANCZOS)
+        return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: unknown driver");
+    const int kout = o.k_out > 0 ? o.k_out : k;
+    if (o.driver == SS_SUBSPACE && kout != k)
+        return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: the subspace driver returns k pairs (k_out = k)");
     SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     try {
+        if (o.driver == SS_BLOCK_LANCZOS)
+            return block_lanczos_impl(f, j, lo, hi, o, V0, k, kout, lambda, X, resid, n_found, stats);
         return slice_solve_impl(f, j, lo, hi, o, V0, k, lambda, X, resid, n_found, stats);
     } catch (const std::bad_alloc &) {
         return ctx->set_error(SS_ERR_OOM, "ss_slice_solve: host allocation failed");
@@ -386,8 +605,41 @@ extern "C" ss_status ss_dos_estimate(ss_symbolic *s, const double *a_vals, const
         return ctx->set_error(SS_ERR_ARG, "ss_dos_estimate: bad argument (n_vec must divide 256)");
     SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     try {
-        return dos_impl(s, a_vals, b_vals, steps, n_vec, start, theta, zeta2, m_run);
+        ss_numeric *fb = nullptr;
+        int rc = factor_spd_b(s, b_vals, &fb);
+        if (rc != SS_OK) return rc;
+        double *x0 = nullptr;
+        rc = cudaMallocAsync((void **)&x0, sizeof(double) * s->n * n_vec, ctx->stream) == cudaSuccess ? SS_OK
+             : ctx->set_error(SS_ERR_OOM, "ss_dos_estimate: device allocation failed");
+        // start vectors of Lanczos on G^-1 A G^-T (B = G G^T) become x0 = G^-T y0 for the
+        // equivalent B-orthonormal Lanczos on B^-1 A
+        if (rc == SS_OK) rc = solve_half_backward(fb, 0, start, n_vec, x0);
+        if (rc == SS_OK) rc = lanczos_impl(s, fb, a_vals, b_vals, steps, n_vec, x0, theta, zeta2, m_run);
+        if (x0) cudaFreeAsync(x0, ctx->stream);
+        ss_factor_destroy(fb);
+        return rc;
     } catch (const std::bad_alloc &) {
         return ctx->set_error(SS_ERR_OOM, "ss_dos_estimate: host allocation failed");
+    }
+}
+
+extern "C" ss_status ss_dos_lanczos(ss_symbolic *s, const double *a_vals, const double *b_vals, int32_t steps,
+                                    int32_t n_vec, const double *x0, double *theta, double *zeta2, int32_t *m_run) {
+    if (!s) return SS_ERR_ARG;
+    ss_ctx *ctx = s->ctx;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "ss_dos_lanczos: host-only context");
+    if (!a_vals || !b_vals || !x0 || !theta || !zeta2 || !m_run || steps <= 0 || steps > 2048 || n_vec <= 0 ||
+        256 % n_vec != 0)
+        return ctx->set_error(SS_ERR_ARG, "ss_dos_lanczos: bad argument (n_vec must divide 256)");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    try {
+        ss_numeric *fb = nullptr;
+        int rc = factor_spd_b(s, b_vals, &fb);
+        if (rc != SS_OK) return rc;
+        rc = lanczos_impl(s, fb, a_vals, b_vals, steps, n_vec, x0, theta, zeta2, m_run);
+        ss_factor_destroy(fb);
+        return rc;
+    } catch (const std::bad_alloc &) {
+        return ctx->set_error(SS_ERR_OOM, "ss_dos_lanczos: host allocation failed");
     }
 }

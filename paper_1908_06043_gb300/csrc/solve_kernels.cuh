@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
                                                    const double *__restrict__ dblk,
                                                    const int32_t *__restrict__ piv,
                                                    const T *__restrict__ zbuf, int use_z, T *x,
-                                                   int k) {
+                                                   int k, int dinv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T (*U)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw);
     T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KC + 1));
@@ -188,7 +188,9 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
         int i = rr + 8 * a;
         double u = 0.0;
         if (i < w && c < kc) {
-            if (se[i] != 0.0) {                     // first row of a 2x2 block
+            if (!dinv) {                            // half solve: D^-1/2 applied beforehand
+                u = (double)U[i][c];
+            } else if (se[i] != 0.0) {              // first row of a 2x2 block
                 double A = sd[i], B = se[i], C = sd[i + 1], det = A * C - B * B;
                 u = (C * (double)U[i][c] - B * (double)U[i + 1][c]) / det;
             } else if (i > 0 && se[i - 1] != 0.0) { // second row of a 2x2 block
@@ -215,6 +217,32 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
         for (int t = i; t < w; ++t) acc += Lm[t][i] * U[t][cc];
         x[(int64_t)(pd.g0 + piv[(int64_t)p * NB + i]) * k + c0 + cc] = acc;
     }
+}
+
+// y <- D^-1/2 y for every panel (SPD factor: 1x1 blocks d > 0, 2x2 blocks E with the
+// symmetric inverse square root E^-1/2 = [c+s, -b; -b, a+s] / (s t), s = sqrt(det E),
+// t = sqrt(a + c + 2 s)); y in the permuted order, N x k, written to yo.
+template <typename T>
+__global__ void k_dhalf(int64_t n, const int32_t *__restrict__ col_panel, const PanelDesc *__restrict__ panels,
+                        const double *__restrict__ dblk, const T *__restrict__ y, T *__restrict__ yo, int k) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n * k) return;
+    const int64_t i = q / k;
+    const int c = (int)(q - i * k);
+    const int p = col_panel[i];
+    const int li = (int)(i - panels[p].g0);
+    const double *dd = dblk + (int64_t)p * 2 * NB, *de = dd + NB;
+    double out;
+    if (de[li] != 0.0 || (li > 0 && de[li - 1] != 0.0)) {
+        const int f = de[li] != 0.0 ? li : li - 1;            // first row of the 2x2 block
+        const double a = dd[f], b = de[f], cc = dd[f + 1];
+        const double sd = sqrt(a * cc - b * b), t = sqrt(a + cc + 2.0 * sd);
+        const double y0 = (double)y[(i - (li - f)) * k + c], y1 = (double)y[(i - (li - f) + 1) * k + c];
+        out = (li == f) ? ((cc + sd) * y0 - b * y1) / (sd * t) : (-b * y0 + (a + sd) * y1) / (sd * t);
+    } else {
+        out = (double)y[q] / sqrt(dd[li]);
+    }
+    yo[q] = (T)out;
 }
 
 // row permutation: mode 0 gather dst[i] = src[perm[i]]; 1 scatter dst[perm[i]] = src[i];

@@ -15,8 +15,8 @@ namespace sss {
 __global__ void k_spmm_cols(int64_t n, const int64_t *__restrict__ rowptr,
                             const int32_t *__restrict__ colind, const double *__restrict__ a,
                             const double *__restrict__ b, const double *__restrict__ alpha,
-                            const double *__restrict__ beta, const double *__restrict__ X, int k,
-                            double *__restrict__ Y) {
+                            const double *__restrict__ beta, const double *__restrict__ X, int64_t ldx, int k,
+                            double *__restrict__ Y, int64_t ldy) {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -28,9 +28,62 @@ __global__ void k_spmm_cols(int64_t n, const int64_t *__restrict__ rowptr,
         double acc = 0.0;
         for (int64_t p = p0; p < p1; ++p) {
             double v = al * a[p] + (be != 0.0 ? be * b[p] : 0.0);
-            acc += v * X[(int64_t)colind[p] * k + c];
+            acc += v * X[(int64_t)colind[p] * ldx + c];
         }
-        Y[row * k + c] = acc;
+        Y[row * ldy + c] = acc;
+    }
+}
+
+// one warp per row, every column in one pass over the row: lane l owns columns
+// l, l+32, ..., NC accumulators (k <= 32 NC)
+template <int NC>
+__global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, const int64_t *__restrict__ rowptr,
+                                                   const int32_t *__restrict__ colind, const double *__restrict__ a,
+                                                   const double *__restrict__ b, const double *__restrict__ alpha,
+                                                   const double *__restrict__ beta, const double *__restrict__ X,
+                                                   int64_t ldx, int k, double *__restrict__ Y, int64_t ldy) {
+    // FP64 is the scarce unit: one FMA per (nonzero, column) for A alone, two when B
+    // takes part (sums of A x and B x kept apart, combined once per row)
+    const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const bool use_b = beta != nullptr;
+    double acc_a[NC], acc_b[NC];
+#pragma unroll
+    for (int t = 0; t < NC; ++t) { acc_a[t] = 0.0; acc_b[t] = 0.0; }
+    const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
+    if (use_b) {
+        for (int64_t p = p0; p < p1; ++p) {
+            const double av = a[p], bv = b[p];
+            const double *x = X + (int64_t)colind[p] * ldx;
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+                const int c = lane + 32 * t;
+                if (c < k) {
+                    const double xv = x[c];
+                    acc_a[t] += av * xv;
+                    acc_b[t] += bv * xv;
+                }
+            }
+        }
+    } else {
+        for (int64_t p = p0; p < p1; ++p) {
+            const double av = a[p];
+            const double *x = X + (int64_t)colind[p] * ldx;
+#pragma unroll
+            for (int t = 0; t < NC; ++t) {
+                const int c = lane + 32 * t;
+                if (c < k) acc_a[t] += av * x[c];
+            }
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < NC; ++t) {
+        const int c = lane + 32 * t;
+        if (c < k) {
+            const double al = alpha ? alpha[c] : 1.0;
+            Y[row * ldy + c] = use_b ? al * acc_a[t] + beta[c] * acc_b[t] : al * acc_a[t];
+        }
     }
 }
 
@@ -39,8 +92,8 @@ template <int KMAX>
 __global__ void k_spmm_nnz(int64_t n, const int64_t *__restrict__ rowptr,
                            const int32_t *__restrict__ colind, const double *__restrict__ a,
                            const double *__restrict__ b, const double *__restrict__ alpha,
-                           const double *__restrict__ beta, const double *__restrict__ X, int k,
-                           double *__restrict__ Y) {
+                           const double *__restrict__ beta, const double *__restrict__ X, int64_t ldx, int k,
+                           double *__restrict__ Y, int64_t ldy) {
     const int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -54,7 +107,7 @@ __global__ void k_spmm_nnz(int64_t n, const int64_t *__restrict__ rowptr,
     const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
     for (int64_t p = p0 + lane; p < p1; p += 32) {
         const double av = a[p], bv = b ? b[p] : 0.0;
-        const double *x = X + (int64_t)colind[p] * k;
+        const double *x = X + (int64_t)colind[p] * ldx;
 #pragma unroll
         for (int c = 0; c < KMAX; ++c)
             if (c < k) acc[c] += (al[c] * av + be[c] * bv) * x[c];
@@ -63,7 +116,7 @@ __global__ void k_spmm_nnz(int64_t n, const int64_t *__restrict__ rowptr,
     for (int c = 0; c < KMAX; ++c) {
         double v = acc[c];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0 && c < k) Y[row * k + c] = v;
+        if (lane == 0 && c < k) Y[row * ldy + c] = v;
     }
 }
 

@@ -110,9 +110,11 @@ def cdos_partition(model: DosModel, a: float, b: float, n_s: int):
 
 
 # ----------------------------------------------------------------- validation
-def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max, tol):
-    """Section 2.3.  probes[j] = (theta, resid).  Returns (selected [(probe, ritz)],
-    per-slice records (n_exact, n_cand, n_conv, status))."""
+def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max, tol, taus=None):
+    """Section 2.3.  probes[j] = (theta, resid); taus[s] (optional) is the point that
+    splits slice s = (shifts[s-1], shifts[s]) between its two probes (default: the
+    midpoint).  Returns (selected [(probe, ritz)], per-slice records (n_exact, n_cand,
+    n_conv, status))."""
     ns = len(shifts)
     bounds = [nneg_min] + list(nneg_shift) + [nneg_max]
     selected, info = [], []
@@ -127,7 +129,7 @@ def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max, t
             th = probes[ns - 1][0]
             cand += [(ns - 1, i) for i in np.nonzero((th > lo) & (th <= lam_max))[0]]
         else:
-            tau = 0.5 * (lo + hi)
+            tau = 0.5 * (lo + hi) if taus is None else taus[s]
             th = probes[s - 1][0]
             cand += [(s - 1, i) for i in np.nonzero((th > lo) & (th <= tau))[0]]
             th = probes[s][0]
@@ -232,10 +234,17 @@ class SliceSolver:
                 hi, c = mid, cm
         return lam_min, lo
 
-    def run(self, shifts, lam_min, lam_max, k, V0=None, max_rounds=60, iters_per_round=4, seed=0):
-        """Factor the shifts and the two region bounds in one batched call, then run
-        rounds of subspace iterations on the probes next to any slice that does not yet
-        validate (fewer converged candidates than its exact count)."""
+    def run(self, shifts, lam_min, lam_max, model: DosModel = None, k=None, V0=None, max_rounds=30,
+            block=64, seed=0, driver="subspace", iters_per_round=2, first_iters=80, splits=None, ks=None):
+        """Factor the shifts and the two region bounds in one batched call, build every
+        probe, validate every slice, and refine the probes next to any slice that does
+        not validate yet (fewer converged candidates than its exact count).
+
+        Subspace probes (Alg. 2, default): basis k = 2 c + 16 (rounded up to 16) for a
+        window holding about c eigenvalues (half of each neighbouring slice's exact count);
+        the first round iterates until c - 2 window Ritz pairs converge, later rounds add
+        `iters_per_round` iterations.  Block Lanczos probes: a Krylov basis of about 2.5x
+        the count in blocks of `block` columns, restarted from the Ritz vectors."""
         t0 = time.perf_counter()
         ns = len(shifts)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -247,42 +256,71 @@ class SliceSolver:
         torch.cuda.synchronize()
         t_factor = ev0.elapsed_time(ev1) / 1e3
         n = self.sym.n
-        if V0 is None:
-            g = torch.Generator(device="cuda").manual_seed(seed)
-            V0 = [torch.randn(n, k, generator=g, device="cuda", dtype=torch.float64) for _ in range(ns)]
-        Vs = list(V0)
-        probes = [None] * ns
+        tau = [None] + [0.5 * (shifts[s_ - 1] + shifts[s_]) if splits is None or splits[s_] is None else splits[s_]
+                        for s_ in range(1, ns)]
         windows = []
         for j in range(ns):
-            lo = lam_min if j == 0 else 0.5 * (shifts[j - 1] + shifts[j])
-            hi = lam_max if j == ns - 1 else 0.5 * (shifts[j] + shifts[j + 1])
+            lo = lam_min if j == 0 else tau[j]
+            hi = lam_max if j == ns - 1 else tau[j + 1]
             windows.append((lo, hi))
+        # basis sizes from the exact counts at the shifts (the window holds about half of
+        # each neighbouring slice) or the DOS
+        kout, m1, cnt = [], [], []
+        for j in range(ns):
+            left = (nneg[j] - (nneg[j - 1] if j > 0 else nneg_min)) * (0.5 if j > 0 else 1.0)
+            right = ((nneg[j + 1] if j < ns - 1 else nneg_max) - nneg[j]) * (0.5 if j < ns - 1 else 1.0)
+            c = int(math.ceil(left + right))
+            cnt.append(c)
+            ko = int(min(n, max(16, math.ceil(1.3 * c) + 16)))
+            kout.append(ko)
+            m1.append(int(max(2, math.ceil(2.5 * ko / block))))
+        g = torch.Generator(device="cuda").manual_seed(seed)
+        probes = [None] * ns
+        Xs = [None] * ns
         active = list(range(ns))
         rounds = 0
         t_solve = 0.0
         iters = [0] * ns
-        info = []
-        sel = []
+        info, sel = [], []
         while active and rounds < max_rounds:
             rounds += 1
             ts = time.perf_counter()
             for j in active:
                 lo, hi = windows[j]
-                pr = f.slice_solve(j, lo, hi, Vs[j], tol=self.tol, max_iter=iters_per_round,
-                                   refine=self.refine, n_expect=k + 1, allow_noconv=True)
+                if driver == "lanczos":
+                    if Xs[j] is None:
+                        v0 = V0[j] if V0 is not None else torch.randn(n, min(block, n), generator=g, device="cuda",
+                                                                     dtype=torch.float64)
+                        mb = min(m1[j], max(1, n // v0.shape[1]))
+                    else:
+                        v0, mb = Xs[j], 2
+                    ko = min(kout[j], mb * v0.shape[1])
+                    pr = f.slice_solve(j, lo, hi, v0, tol=self.tol, max_iter=mb, refine=self.refine,
+                                       driver="lanczos", k_out=ko, allow_noconv=True)
+                else:
+                    kk = k or (ks[j] if ks is not None else min(n, -(-(2 * cnt[j] + 16) // 16) * 16))
+                    kk = min(n, max(kk, -(-(cnt[j] + 16) // 16) * 16))
+                    if Xs[j] is None:
+                        v0 = V0[j] if V0 is not None else torch.randn(n, kk, generator=g, device="cuda",
+                                                                     dtype=torch.float64)
+                        mi, ne = first_iters, max(1, cnt[j] - 2)
+                    else:
+                        v0, mi, ne = Xs[j], iters_per_round, v0_never(Xs[j])
+                    pr = f.slice_solve(j, lo, hi, v0, tol=self.tol, max_iter=mi, refine=self.refine,
+                                       n_expect=ne, allow_noconv=True)
                 probes[j] = pr
-                Vs[j] = pr.X
+                Xs[j] = pr.X
                 iters[j] += pr.iterations
             t_solve += time.perf_counter() - ts
             sel, info = validate(shifts, lam_min, lam_max, [(p.theta, p.resid) for p in probes], nneg,
-                                 nneg_min, nneg_max, self.tol)
+                                 nneg_min, nneg_max, self.tol, taus=tau + [None])
             bad = set()
-            for s, (n_exact, n_cand, n_conv, status) in enumerate(info):
+            for s_, (n_exact, n_cand, n_conv, status) in enumerate(info):
                 if n_conv < n_exact:
-                    if s > 0:
-                        bad.add(s - 1)
-                    if s < ns:
-                        bad.add(s)
+                    if s_ > 0:
+                        bad.add(s_ - 1)
+                    if s_ < ns:
+                        bad.add(s_)
             active = sorted(bad)
         lam = np.array([probes[pj].theta[i] for pj, i in sel])
         res = np.array([probes[pj].resid[i] for pj, i in sel])
@@ -294,14 +332,79 @@ class SliceSolver:
                                 iterations=iters, n_below_max=nneg_max, n_below_min=nneg_min,
                                 converged=not active))
 
-    def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01):
+    def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,
-        lambda_max at Phi = (1 + margin) n_e + 1, n_s CDOS intervals between them."""
+        lambda_max at Phi = (1 + margin) n_e + 1, and n_s intervals between them, by the
+        CDOS roots of Eq. 15 with expectation shifts (mode "cdos") or by ball_partition
+        (mode "ball").  Returns (lambda_min, lambda_max, shifts, splits, basis sizes):
+        splits[s] divides slice s between probes s-1 and s (None: the midpoints)."""
         lo_t, hi_t = model.theta_range()
         lam_min = lo_t
         lam_max = model.root((1.0 + margin) * n_e + 1.0, lo_t, hi_t)
-        _, shifts = cdos_partition(model, lam_min, lam_max, n_s)
-        return lam_min, lam_max, shifts
+        if mode == "cdos":
+            _, shifts = cdos_partition(model, lam_min, lam_max, n_s)
+            return lam_min, lam_max, shifts, None, None
+        iv, shifts, balls = ball_partition(model, lam_min, lam_max, n_s)
+        splits = [None] + [iv[j][0] for j in range(1, n_s)]
+        ks = [int(-(-(1.15 * bc + 16) // 16) * 16) for bc in balls]
+        return lam_min, lam_max, shifts, splits, ks
+
+
+def v0_never(X) -> int:
+    """An n_expect no probe can reach: run exactly max_iter iterations."""
+    return X.shape[1] + 1
+
+
+def ball_partition(model: DosModel, a: float, b: float, n_s: int, ratio: float = 2.0):
+    """Intervals for shift-invert probes when the DOS is far from uniform.
+
+    A probe at sigma converges the eigenvalues of its interval [l, u] (sigma the midpoint,
+    half-width h) at a rate set by the first eigenvalue outside its basis; if its basis
+    holds every eigenvalue within ratio * h of sigma, that rate is about 1 / ratio per
+    iteration.  Greedily from a, each interval is made as wide as possible with
+    Phi(sigma + ratio h) - Phi(sigma - ratio h) <= K; the budget K is bisected until the
+    greedy pass uses at most n_s intervals, and the intervals with the largest counts are
+    then halved until there are exactly n_s.  Returns (intervals, shifts, ball counts)."""
+    def count(x, y):
+        return float(model.Phi(y)[0] - model.Phi(x)[0])
+
+    def greedy(K, limit):
+        iv, l = [], a
+        while l < b and len(iv) <= limit:
+            if count(2 * a - b, b) <= K:           # everything left fits in one ball
+                u = b
+            else:
+                lo, hi = l, b
+                for _ in range(60):
+                    u = 0.5 * (lo + hi)
+                    s_, h = 0.5 * (l + u), 0.5 * (u - l)
+                    if count(s_ - ratio * h, s_ + ratio * h) <= K:
+                        lo = u
+                    else:
+                        hi = u
+                u = lo if lo > l else hi
+                if count(u, b) < 0.5:               # nothing left for another interval
+                    u = b
+            iv.append((l, u))
+            l = u
+        return iv
+
+    Kl, Kh = 1.0, 2.0 * count(2 * a - b, 2 * b - a) + 16
+    for _ in range(50):
+        Km = 0.5 * (Kl + Kh)
+        if len(greedy(Km, n_s)) <= n_s:
+            Kh = Km
+        else:
+            Kl = Km
+    iv = greedy(Kh, n_s)
+    while len(iv) < n_s:
+        c = [count(l, u) for l, u in iv]
+        i = int(np.argmax(c))
+        l, u = iv[i]
+        iv[i:i + 1] = [(l, 0.5 * (l + u)), (0.5 * (l + u), u)]
+    shifts = [0.5 * (l + u) for l, u in iv]
+    balls = [count(s_ - ratio * 0.5 * (u - l), s_ + ratio * 0.5 * (u - l)) for s_, (l, u) in zip(shifts, iv)]
+    return iv, shifts, balls
 
 
 def default_basis_width(n_e: int, n_s: int) -> int:

@@ -42,7 +42,7 @@ def main():
     with open(os.path.join(HERE, "gauss16_eigs.txt"), "w") as f:
         f.write("# lowest 2048 eigenvalues, 16^3 Gaussian pencil (4 fn/atom, seed 2), dense oracle\n")
         for v in lam[:N_KEEP]:
-            f.write(f"{v!r}\n")
+            f.write(f"{float(v)!r}\n")
 
 
 if __name__ == "__main__":

@@ -1,0 +1,82 @@
+"""CPU tests of the host-side slicing logic (Sections 2.3, 3.1, 3.2) against the oracle's
+independent implementation and against invariants."""
+import numpy as np
+import pytest
+
+from oracle import dos as odos
+from oracle import partition as opart
+from paper_1908_06043_gb300.driver import DosModel, ball_partition, cdos_partition, kmeans_shifts, validate
+
+
+def _runs(seed, m=120, nv=3):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nv):
+        th = np.sort(np.concatenate([rng.uniform(-30, -5, 8), rng.uniform(-5, 4, m - 8)]))
+        z = rng.random(m)
+        out.append((th, z / z.sum()))
+    return out
+
+
+def test_dos_model_matches_oracle_formulas():
+    runs = _runs(1)
+    model = DosModel(5000, runs)
+    oruns = [(th, z2, odos.gaussian_widths(th)) for th, z2 in runs]
+    w = np.linspace(-35, 6, 57)
+    assert np.allclose(model.Phi(w), odos.cdos_Phi(w, 5000, oruns), rtol=1e-13, atol=1e-9)
+    assert np.allclose(model.phi(w), odos.dos_phi(w, 5000, oruns), rtol=1e-13, atol=1e-9)
+    assert model.expectation(-2.0, 1.0) == pytest.approx(odos.expectation_shift(-2.0, 1.0, 5000, oruns), rel=1e-12)
+
+
+def test_cdos_partition_matches_oracle():
+    runs = _runs(2)
+    model = DosModel(5000, runs)
+    oruns = [(th, z2, odos.gaussian_widths(th)) for th, z2 in runs]
+    iv, shifts = cdos_partition(model, -10.0, 3.0, 7)
+    oiv = opart.cdos_root_intervals(-10.0, 3.0, 7, 5000, oruns)
+    assert np.allclose(np.array(iv), np.array(oiv), atol=1e-9)
+
+
+def test_ball_partition_invariants():
+    runs = _runs(3)
+    model = DosModel(20000, runs)
+    a, b, ns = -32.0, 3.0, 12
+    iv, shifts, balls = ball_partition(model, a, b, ns)
+    assert len(iv) == ns and iv[0][0] == a and iv[-1][1] == b
+    assert all(iv[i][1] == iv[i + 1][0] for i in range(ns - 1))
+    assert all(l < s < u for (l, u), s in zip(iv, shifts))
+    # every ball stays within the largest budget used
+    K = max(balls)
+    for (l, u), s in zip(iv, shifts):
+        h = 0.5 * (u - l)
+        assert model.Phi(s + 2 * h)[0] - model.Phi(s - 2 * h)[0] <= K + 1e-6
+    # the sparse tail gets a wider, emptier interval than the dense body
+    counts = [model.Phi(u)[0] - model.Phi(l)[0] for l, u in iv]
+    assert counts[0] < np.median(counts)
+
+
+def test_validate_matches_oracle_with_midpoints():
+    rng = np.random.default_rng(4)
+    shifts = [0.0, 1.0, 2.0]
+    probes = [(np.sort(rng.uniform(-1, 3, 30)), rng.choice([1e-12, 1e-3], 30)) for _ in shifts]
+    nneg = [5, 12, 20]
+    sel, info = validate(shifts, -1.0, 3.0, probes, nneg, 0, 27, 1e-10)
+    osel, oinfo = opart.validate(shifts, -1.0, 3.0, probes, nneg, 0, 27)
+    assert sorted(map(tuple, sel)) == sorted(map(tuple, osel))
+    assert [i[3] for i in info] == [i[2] for i in oinfo]
+
+
+def test_validate_custom_split_point():
+    shifts = [0.0, 1.0]
+    probes = [(np.array([0.2, 0.7]), np.array([1e-12, 1e-12])), (np.array([0.7, 0.9]), np.array([1e-12, 1e-12]))]
+    # split at 0.8 instead of the midpoint: 0.7 belongs to the lower probe
+    sel, info = validate(shifts, -1.0, 2.0, probes, [0, 3], 0, 3, 1e-10, taus=[None, 0.8, None])
+    assert info[1][:3] == (3, 3, 3)
+    assert (0, 1) in sel and (1, 0) not in sel
+
+
+def test_kmeans_matches_oracle():
+    rng = np.random.default_rng(5)
+    x = np.sort(np.concatenate([rng.normal(0, 0.1, 50), rng.normal(3, 0.2, 80), rng.normal(7, 0.1, 40)]))
+    u = rng.random(3)
+    assert np.allclose(kmeans_shifts(x, 3, u), opart.kmeans_shifts(x, 3, u), atol=1e-14)

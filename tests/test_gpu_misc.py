@@ -23,12 +23,13 @@ def test_spmm_matches_oracle(gpu_lib, k):
     assert np.abs(Y - ref).max() <= 1e-12 * np.abs(ref).max()
 
 
-def test_dos_matches_oracle_lanczos(gpu_lib):
+def test_dos_lanczos_matches_oracle_lanczos(gpu_lib):
+    # explicit B-orthonormal start vectors: the GPU run and the oracle's see the same x0
     p = config_pencil(1)
     ctx, sym, a, b = setup(gpu_lib, p)
     steps, nv = 60, 4
     X0 = normal_block(p.n, nv, 21)
-    runs = sym.dos_estimate(a, b, steps, torch.tensor(X0, device="cuda"))
+    runs = sym.dos_lanczos(a, b, steps, torch.tensor(X0, device="cuda"))
     A, B = p.dense("a"), p.dense("b")
     for c in range(nv):
         th_o, z_o, _, _ = dos.lanczos_ritz(A, B, X0[:, c], steps)
@@ -50,3 +51,23 @@ def test_band_energy_grad_matches_oracle(gpu_lib):
     ga_o, gb_o = grad.band_energy_grad(p, lam[:ne], X[:, :ne])
     assert np.abs(ga.cpu().numpy() - ga_o).max() <= 1e-12 * np.abs(ga_o).max()
     assert np.abs(gb.cpu().numpy() - gb_o).max() <= 1e-12 * np.abs(gb_o).max()
+
+
+def test_dos_estimate_is_unbiased(gpu_lib):
+    # Lanczos on G^-1 A G^-T from i.i.d. N(0,1) vectors: averaged over start vectors the
+    # CDOS estimate approaches the exact eigenvalue count (Eq. 14), whatever square root
+    # G of B the factorisation provides
+    from paper_1908_06043_gb300.driver import DosModel
+    p = config_pencil(1)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    Y0 = torch.tensor(normal_block(p.n, 32, 77), device="cuda")
+    runs = []
+    for c0 in range(0, 32, 8):
+        runs += sym.dos_estimate(a, b, 80, Y0[:, c0:c0 + 8].contiguous())
+    model = DosModel(p.n, runs)
+    for i in (20, 86, 300, 600):
+        w = 0.5 * (lam[i] + lam[i + 1])
+        assert abs(float(model.Phi(w)[0]) - (i + 1)) <= 0.08 * (i + 1) + 4
+    for th, z2 in runs:
+        assert abs(z2.sum() - 1.0) <= 1e-10

@@ -54,3 +54,72 @@ def test_config1_probe(gpu_lib, precision):
     pr = f.slice_solve(0, lo, hi, V0, max_iter=300, n_expect=20)
     assert pr.converged and pr.n_found == 20
     _check_probe(p, lam, lo, hi, pr)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config1_block_lanczos_probe(gpu_lib, precision):
+    p = config_pencil(1)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    s = 0.5 * (lam[60] + lam[61])
+    lo, hi = 0.5 * (lam[45] + lam[46]), 0.5 * (lam[75] + lam[76])
+    f = sym.factor(a, b, [s], precision)
+    # Krylov extraction converges slowly at the edge of a wide window, so the first run
+    # is followed by restarts from its Ritz vectors until the window validates
+    V0 = torch.tensor(normal_block(p.n, 32, 5), device="cuda")
+    pr = f.slice_solve(0, lo, hi, V0, driver="lanczos", max_iter=6, k_out=64, allow_noconv=True)
+    assert pr.X.shape == (p.n, 64)
+    for _ in range(40):
+        if pr.n_found >= 30:
+            break
+        pr = f.slice_solve(0, lo, hi, pr.X, driver="lanczos", max_iter=2, k_out=64, allow_noconv=True)
+    assert pr.n_found == 30
+    _check_probe(p, lam, lo, hi, pr)
+
+
+def test_laplacian_block_lanczos_restart(gpu_lib):
+    # a first short Krylov run, then a restart from its Ritz vectors (two blocks)
+    n = 600
+    p = laplacian_1d(n)
+    lam = np.sort(2 - 2 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1)))
+    ctx, sym, a, b = setup(gpu_lib, p, nd_leaf=32)
+    s = 0.5 * (lam[300] + lam[301])
+    lo, hi = 0.5 * (lam[290] + lam[291]), 0.5 * (lam[310] + lam[311])
+    f = sym.factor(a, b, [s], "mixed")
+    V0 = torch.tensor(normal_block(n, 16, 6), device="cuda")
+    pr = f.slice_solve(0, lo, hi, V0, driver="lanczos", max_iter=4, k_out=40, allow_noconv=True)
+    for _ in range(40):
+        if pr.n_found >= 20:
+            break
+        pr = f.slice_solve(0, lo, hi, pr.X, driver="lanczos", max_iter=2, k_out=40, allow_noconv=True)
+    assert pr.n_found == 20
+    _check_probe(p, lam, lo, hi, pr)
+
+
+def _gauss16_golden():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "gauss16_eigs.txt")
+    return np.array([float(l) for l in open(path) if not l.startswith("#")])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_gauss16_probe_matches_dense_golden(gpu_lib, precision):
+    # full-size pencil of the benchmark (N = 16,384): a 60-eigenvalue window around a
+    # shift in the middle of the wanted region, against the dense-oracle eigenvalues
+    from workloads.pencils import config_pencil
+    lam = _gauss16_golden()
+    p = config_pencil(2)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    i = 1000
+    s = 0.5 * (lam[i] + lam[i + 1])
+    lo, hi = 0.5 * (lam[i - 31] + lam[i - 30]), 0.5 * (lam[i + 29] + lam[i + 30])
+    f = sym.factor(a, b, [s], precision)
+    assert f.inertia(0)[0] == i + 1
+    V0 = torch.tensor(normal_block(p.n, 136, 9), device="cuda")
+    pr = f.slice_solve(0, lo, hi, V0, n_expect=60, max_iter=80)
+    inside = (pr.theta > lo) & (pr.theta <= hi) & (pr.resid <= 1e-10)
+    ref = lam[(lam > lo) & (lam <= hi)]
+    assert inside.sum() == ref.size == 60
+    assert np.all(np.abs(pr.theta[inside] - ref) <= 1e-10 * np.maximum(np.abs(ref), 1.0))
+    X = pr.X.cpu().numpy()[:, inside]
+    assert spectral.residual_norms(p, pr.theta[inside], X).max() <= 1e-10

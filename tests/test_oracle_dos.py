@@ -82,3 +82,20 @@ def test_uniform_spectrum_gives_equispaced_shifts():
     assert np.allclose(widths, 0.1, rtol=2e-3)
     shifts = [dos.expectation_shift(l, u, 1000, runs) for l, u in iv]
     assert np.allclose(shifts, [0.5 * (l + u) for l, u in iv], atol=1e-3)
+
+
+def test_cholesky_frame_start_is_unbiased_on_gaussian_pencil():
+    # with an N(0,1) start in the Cholesky frame the averaged CDOS tracks the exact count
+    # even though B is ill-conditioned (an i.i.d. start in the original basis does not)
+    from workloads.pencils import config_pencil
+    p = config_pencil(1)
+    A, B = p.dense("a"), p.dense("b")
+    lam, _ = dense.gen_eig(A, B, vectors=False)
+    Y = normal_block(p.n, 16, 8)
+    runs = []
+    for c in range(16):
+        th, z2, _, _ = dos.lanczos_ritz_cholesky_frame(A, B, Y[:, c], 60)
+        runs.append((th, z2, dos.gaussian_widths(th)))
+    for i in (20, 86, 300):
+        w = 0.5 * (lam[i] + lam[i + 1])
+        assert abs(dos.cdos_Phi(w, p.n, runs)[0] - (i + 1)) <= 0.1 * (i + 1) + 4
