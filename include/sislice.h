@@ -100,7 +100,11 @@ typedef struct ss_solve_opts {
                                    lie in (lo, hi] (e.g. an inertia count) [0]        */
     int32_t k_out;              /* Ritz pairs returned (SS_BLOCK_LANCZOS: the k_out
                                    nearest sigma, <= k * max_iter) [k]               */
-    int32_t reserved[2];
+    int32_t refine_from_start;  /* SS_SUBSPACE: 1 refines every solve from the first
+                                   iteration (a restart from converging vectors); 0
+                                   starts refining once the window is within 1e-6 or
+                                   its residuals stop improving [0]                  */
+    int32_t reserved;
 } ss_solve_opts;
 
 /* ---- context ---------------------------------------------------------------------

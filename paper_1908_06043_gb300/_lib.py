@@ -39,7 +39,7 @@ class ss_probe_stats(C.Structure):
 class ss_solve_opts(C.Structure):
     _fields_ = [("driver", C.c_int32), ("max_iter", C.c_int32), ("check_every", C.c_int32),
                 ("refine", C.c_int32), ("tol", C.c_double), ("n_expect", C.c_int32),
-                ("k_out", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("k_out", C.c_int32), ("refine_from_start", C.c_int32), ("reserved", C.c_int32)]
 
 
 EXPORTS = ["ss_create", "ss_destroy", "ss_last_error", "ss_analyze", "ss_symbolic_info_get",

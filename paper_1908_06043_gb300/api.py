@@ -245,7 +245,8 @@ def solve(f: Factor, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
 
 def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: float = 1e-10,
                 max_iter: int = 0, check_every: int = 1, refine: int = 2, n_expect: int = 0,
-                allow_noconv: bool = False, driver: str = "subspace", k_out: int = 0) -> ProbeResult:
+                allow_noconv: bool = False, driver: str = "subspace", k_out: int = 0,
+                refine_from_start: bool = False) -> ProbeResult:
     """Spectral probe of shift j: shift-invert subspace iteration (Alg. 2; max_iter
     iterations) or shift-invert block Lanczos (max_iter blocks of width V0.shape[1],
     returning the k_out Ritz pairs nearest sigma_j)."""
@@ -256,6 +257,7 @@ def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: 
     opts.driver = {"subspace": L.SS_SUBSPACE, "lanczos": L.SS_BLOCK_LANCZOS}[driver]
     opts.max_iter, opts.check_every, opts.refine, opts.tol, opts.n_expect = max_iter, check_every, refine, tol, n_expect
     opts.k_out = kout
+    opts.refine_from_start = 1 if refine_from_start else 0
     lam = np.empty(kout)
     res = np.empty(kout)
     X = torch.empty((n, kout), dtype=torch.float64, device=V0.device)

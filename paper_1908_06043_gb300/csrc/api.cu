@@ -508,11 +508,26 @@ int spmm_launch_ld(ss_symbolic *s, const double *a, const double *b, const doubl
     else if (k < 16)
         ss_launch(ctx, SS_K_SPMM, sss::k_spmm_nnz<16>, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a,
                   b, alpha, beta, X, ldx, k, Y, ldy);
-    else if (k <= 32) SS_SPMM_ROWS(1);
-    else if (k <= 64) SS_SPMM_ROWS(2);
-    else if (k <= 128) SS_SPMM_ROWS(4);
-    else if (k <= 256) SS_SPMM_ROWS(8);
-    else if (k <= 512) SS_SPMM_ROWS(16);
+    else if (k <= 512) {
+        switch ((k + 31) / 32) {     // exactly as many accumulators as the columns need
+            case 1: SS_SPMM_ROWS(1); break;
+            case 2: SS_SPMM_ROWS(2); break;
+            case 3: SS_SPMM_ROWS(3); break;
+            case 4: SS_SPMM_ROWS(4); break;
+            case 5: SS_SPMM_ROWS(5); break;
+            case 6: SS_SPMM_ROWS(6); break;
+            case 7: SS_SPMM_ROWS(7); break;
+            case 8: SS_SPMM_ROWS(8); break;
+            case 9: SS_SPMM_ROWS(9); break;
+            case 10: SS_SPMM_ROWS(10); break;
+            case 11: SS_SPMM_ROWS(11); break;
+            case 12: SS_SPMM_ROWS(12); break;
+            case 13: SS_SPMM_ROWS(13); break;
+            case 14: SS_SPMM_ROWS(14); break;
+            case 15: SS_SPMM_ROWS(15); break;
+            default: SS_SPMM_ROWS(16); break;
+        }
+    }
     else
         ss_launch(ctx, SS_K_SPMM, sss::k_spmm_cols, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b,
                   alpha, beta, X, ldx, k, Y, ldy);
@@ -596,11 +611,39 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     int rc;
     if (steps_done) *steps_done = 0;
     if (f->shift_prec[j] == SS_FP64) {
-        double *w = nullptr;
+        // FP64 factor: X_0 = M^-1 R, then `refine` steps X += M^-1 (R - M X) (iterative
+        // refinement in the factor's own precision removes the effect of element growth
+        // on the solve's backward error)
+        double *w = nullptr, *x = nullptr, *y = nullptr, *co = nullptr;
         SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&w, sizeof(double) * tot, st));
+        if (refine > 0) {
+            SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&x, sizeof(double) * tot, st));
+            SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&y, sizeof(double) * tot, st));
+            SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&co, sizeof(double) * 2 * k, st));
+            ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, 1.0, co);
+            ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, -f->sigma[j], co + k);
+        }
+        double *out = refine > 0 ? x : X;
         ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm, R, w, 0);
         if ((rc = solve_permuted<double>(f, j, w, k)) != SS_OK) return rc;
-        ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm, w, X, 1);
+        ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
+                  (const double *)w, out, 1);
+        for (int it = 0; it < refine; ++it) {
+            if ((rc = spmm_launch(s, f->a_vals, f->b_vals, co, co + k, x, k, y)) != SS_OK) return rc;
+            ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, (const double *)y, y);
+            ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
+                      (const double *)y, w, 0);
+            if ((rc = solve_permuted<double>(f, j, w, k)) != SS_OK) return rc;
+            ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
+                      (const double *)w, x, 2);
+            if (steps_done) (*steps_done)++;
+        }
+        if (refine > 0) {
+            SS_CUDA_TRY(ctx, cudaMemcpyAsync(X, x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+            cudaFreeAsync(x, st);
+            cudaFreeAsync(y, st);
+            cudaFreeAsync(co, st);
+        }
         SS_CUDA_TRY(ctx, cudaFreeAsync(w, st));
         SS_CUDA_TRY(ctx, cudaGetLastError());
         return SS_OK;

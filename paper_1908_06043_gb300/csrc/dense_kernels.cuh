@@ -96,30 +96,79 @@ __global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__re
 
 // ---------------------------------------------------------------- small Cholesky
 // G (k x k, row-major, symmetric) -> lower R with G = R R^T, upper part zeroed.
-// info[0] = 0 ok, j+1 if the j-th pivot was not positive.  One block; right-looking,
-// warp w updates rows j+1+w, j+1+w+nwarps, ... of the trailing lower triangle.
+// info[0] = 0 ok, j+1 if the j-th pivot was not positive.  One block of 1024 threads,
+// blocked right-looking over 32-column panels: the panel's diagonal block is factored
+// by one warp, the rows below it are solved against it, the finished panel is staged in
+// shared memory and the trailing lower triangle is updated from there.
+// Dynamic shared memory: k * 33 doubles (the staged panel).
+constexpr int CH_NB = 32;
 __global__ void __launch_bounds__(1024) k_chol_small(double *G, int k, int *info) {
-    __shared__ double s_d;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *P = reinterpret_cast<double *>(smem_raw);          // panel rows, ld 33
+    __shared__ double Dg[CH_NB][CH_NB + 1];
     __shared__ int s_bad;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    for (int j = 0; j < k; ++j) {
-        if (tid == 0) {
-            double d = G[(int64_t)j * k + j];
-            if (!(d > 0.0)) { s_bad = j + 1; d = 1.0; }
-            s_d = sqrt(d);
-            G[(int64_t)j * k + j] = s_d;
+    for (int j0 = 0; j0 < k && !s_bad; j0 += CH_NB) {
+        const int w = min(CH_NB, k - j0);
+        // 1. factor the w x w diagonal block (warp 0, in shared memory)
+        for (int q = tid; q < w * w; q += nt) {
+            int i = q / w, c = q % w;
+            Dg[i][c] = (c <= i) ? G[(int64_t)(j0 + i) * k + j0 + c] : 0.0;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            for (int c = 0; c < w; ++c) {
+                double d = Dg[c][c];
+                if (!(d > 0.0)) {
+                    if (lane == 0 && !s_bad) s_bad = j0 + c + 1;
+                    d = 1.0;
+                }
+                const double sd = sqrt(d);
+                __syncwarp();
+                if (lane == 0) Dg[c][c] = sd;
+                __syncwarp();
+                const double inv = 1.0 / sd;
+                for (int i = c + 1 + lane; i < w; i += 32) Dg[i][c] *= inv;
+                __syncwarp();
+                for (int i = c + 1 + lane; i < w; i += 32)
+                    for (int l = c + 1; l <= i; ++l) Dg[i][l] -= Dg[i][c] * Dg[l][c];
+                __syncwarp();
+            }
         }
         __syncthreads();
         if (s_bad) break;
-        const double inv = 1.0 / s_d;
-        for (int i = j + 1 + tid; i < k; i += nt) G[(int64_t)i * k + j] *= inv;
+        for (int q = tid; q < w * w; q += nt) {
+            int i = q / w, c = q % w;
+            if (c <= i) G[(int64_t)(j0 + i) * k + j0 + c] = Dg[i][c];
+            P[i * 33 + c] = (c <= i) ? Dg[i][c] : 0.0;
+        }
+        // 2. rows below: L[i][J] = G[i][J] L_JJ^-T (forward substitution per row, one warp per row)
+        for (int i = j0 + w + wid; i < k; i += nw) {
+            double x = (lane < w) ? G[(int64_t)i * k + j0 + lane] : 0.0;
+            for (int c = 0; c < w; ++c) {
+                double xc = __shfl_sync(0xffffffffu, x, c) / Dg[c][c];
+                if (lane == c) x = xc;
+                if (lane > c && lane < w) x -= xc * Dg[lane][c];
+            }
+            if (lane < w) {
+                G[(int64_t)i * k + j0 + lane] = x;
+                P[(i - j0) * 33 + lane] = x;
+            }
+        }
         __syncthreads();
-        for (int i = j + 1 + wid; i < k; i += nw) {
-            const double gij = G[(int64_t)i * k + j];
+        // 3. trailing update G[i][l] -= sum_c L[i][c] L[l][c], j0+w <= l <= i
+        for (int i = j0 + w + wid; i < k; i += nw) {
+            const double *pi = P + (i - j0) * 33;
             double *gi = G + (int64_t)i * k;
-            for (int l = j + 1 + lane; l <= i; l += 32) gi[l] -= gij * G[(int64_t)l * k + j];
+            for (int l = j0 + w + lane; l <= i; l += 32) {
+                const double *pl = P + (l - j0) * 33;
+                double acc = 0.0;
+#pragma unroll 8
+                for (int c = 0; c < w; ++c) acc += pi[c] * pl[c];
+                gi[l] -= acc;
+            }
         }
         __syncthreads();
     }
@@ -131,16 +180,29 @@ __global__ void __launch_bounds__(1024) k_chol_small(double *G, int k, int *info
     }
 }
 
-// Rinv = R^-1 for lower-triangular R (k x k row-major); one thread per column.
-__global__ void k_trinv_lower(const double *__restrict__ R, int k, double *__restrict__ Rinv) {
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
-        for (int i = 0; i < j; ++i) Rinv[(int64_t)i * k + j] = 0.0;
-        Rinv[(int64_t)j * k + j] = 1.0 / R[(int64_t)j * k + j];
-        for (int i = j + 1; i < k; ++i) {
-            double acc = 0.0;
-            for (int t = j; t < i; ++t) acc -= R[(int64_t)i * k + t] * Rinv[(int64_t)t * k + j];
-            Rinv[(int64_t)i * k + j] = acc / R[(int64_t)i * k + i];
+// Rinv = R^-1 for lower-triangular R (k x k row-major).  Column blocks of R^-1 are
+// independent: block b solves R X = E for columns [32 b, 32 b + 32) by forward
+// substitution over the rows; per row the dot product is split across the 8 warps.
+__global__ void __launch_bounds__(256) k_trinv_lower(const double *__restrict__ R, int k, double *__restrict__ Rinv) {
+    __shared__ double part[8][33];
+    const int c0 = blockIdx.x * 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int c = c0 + lane;
+    for (int i = 0; i < k; ++i) {
+        const double *ri = R + (int64_t)i * k;
+        double acc = 0.0;
+        if (c < k)      // Rinv[t][c] = 0 for t < c, so every lane can walk the same t
+            for (int t = c0 + wid; t < i; t += 8) acc += ri[t] * Rinv[(int64_t)t * k + c];
+        part[wid][lane] = acc;
+        __syncthreads();
+        if (wid == 0 && c < k) {
+            double sum = 0.0;
+            for (int w = 0; w < 8; ++w) sum += part[w][lane];
+            double v = 0.0;
+            if (c <= i) v = ((c == i ? 1.0 : 0.0) - sum) / ri[i];
+            Rinv[(int64_t)i * k + c] = v;
         }
+        __syncthreads();
     }
 }
 

@@ -154,6 +154,18 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
     return SS_OK;
 }
 
+// the blocked Cholesky stages a k x 32 panel in shared memory (k <= 800)
+int chol_attr(ss_ctx *ctx, int k) {
+    if (k > 800) return ctx->set_error(SS_ERR_ARG, "Cholesky-QR: basis wider than 800 columns");
+    static bool done = false;
+    if (!done) {
+        SS_CUDA_TRY(ctx, cudaFuncSetAttribute(ssd::k_chol_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)(sizeof(double) * 33 * 800)));
+        done = true;
+    }
+    return SS_OK;
+}
+
 // V <- V R^-T with R R^T = V^T B V (Cholesky-QR in the B inner product, run twice; the
 // first pass adds a small diagonal shift when the plain Gram matrix is not numerically
 // positive definite -- shifted Cholesky-QR).  BV scratch n x k, G/Rinv k x k.
@@ -162,6 +174,7 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     int rc;
+    if ((rc = chol_attr(ctx, k)) != SS_OK) return rc;
     for (int pass = 0; pass < 2; ++pass) {
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, Wk)) != SS_OK) return rc;
         if ((rc = gram(ctx, V, s->n, k, Wk, k, G)) != SS_OK) return rc;
@@ -176,14 +189,14 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
                                    (attempt == 1 ? 1.0 : 1e4);
                 ss_launch(ctx, SS_K_SMALL_DENSE, k_add_shift_diag, 1, 256, 0, st, G, k, rel);
             }
-            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, 0, st, G, k, info);
+            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, sizeof(double) * 33 * (size_t)k, st, G, k, info);
             SS_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
             if (hinfo == 0) break;
         }
         if (hinfo != 0)
             return ctx->set_error(SS_ERR_NOCONV, "Cholesky-QR: basis is numerically rank deficient");
-        ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 128), 128, 0, st, G, k, Rinv);
+        ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 32), 256, 0, st, (const double *)G, k, Rinv);
         if ((rc = gemm_tall(ctx, V, s->n, k, Rinv, k, 1, Wk)) != SS_OK) return rc;
         std::swap(V, Wk);
     }
@@ -200,6 +213,7 @@ int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&B
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     int rc;
+    if ((rc = chol_attr(ctx, k)) != SS_OK) return rc;
     for (int pass = 0; pass < 2; ++pass) {
         int hinfo = 0;
         for (int attempt = 0; attempt < 3; ++attempt) {
@@ -210,13 +224,13 @@ int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&B
                                    (attempt == 1 ? 1.0 : 1e4);
                 ss_launch(ctx, SS_K_SMALL_DENSE, k_add_shift_diag, 1, 256, 0, st, G, k, rel);
             }
-            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, 0, st, G, k, info);
+            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, sizeof(double) * 33 * (size_t)k, st, G, k, info);
             SS_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
             if (hinfo == 0) break;
         }
         if (hinfo != 0) return ctx->set_error(SS_ERR_NOCONV, "Cholesky-QR: basis is numerically rank deficient");
-        ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 128), 128, 0, st, (const double *)G, k, Rinv);
+        ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 32), 256, 0, st, (const double *)G, k, Rinv);
         if ((rc = gemm_tall(ctx, W, s->n, k, Rinv, k, 1, Wt)) != SS_OK) return rc;
         if ((rc = gemm_tall(ctx, BW, s->n, k, Rinv, k, 1, BWt)) != SS_OK) return rc;
         std::swap(W, Wt);
@@ -258,7 +272,8 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     if ((rc = cholqr_track(f, V, BV, T1, T2, k, G, Rinv, info)) != SS_OK) return rc;
     std::vector<double> th(k), rs(k);
     int it = 0, refine_total = 0;
-    bool conv = false, have_rr = false, near_conv = false;
+    bool conv = false, have_rr = false, near_conv = o.refine_from_start != 0;
+    std::vector<double> hist;
     double maxr = 0.0, maxr_all = INFINITY;
     int nf = 0;
     const int max_iter = o.max_iter > 0 ? o.max_iter : 200;
@@ -271,7 +286,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // W = (A - sigma B)^-1 B V (Alg. 2 step 3); a mixed factor runs plain FP32 solves
         // while the window's residuals are above 1e-6 and FP64 refinement afterwards
         int done_ref = 0;
-        const int ref_now = (f->shift_prec[j] == SS_MIXED && !near_conv) ? 0 : refine;
+        const int ref_now = near_conv ? (f->shift_prec[j] == SS_MIXED ? refine : 1) : 0;
         if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref)) != SS_OK) return rc;
         refine_total += done_ref;
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;
@@ -324,12 +339,21 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         }
         const bool done = o.n_expect > 0 ? (nf >= o.n_expect) : (nf == nin);
         if (done && it >= 2) { conv = true; break; }
-        // FP64 refinement starts once the window's target count is within 1e-6
-        int n6 = 0;
-        for (int i = 0; i < k; ++i)
-            if (th[i] > lo && th[i] <= hi && rs[i] <= 1e-6) ++n6;
-        const int target = o.n_expect > 0 ? o.n_expect : std::max(1, nin - 2);
-        near_conv = near_conv || n6 >= target;
+        // refinement of the solves (FP64 residuals) starts once the window's target count
+        // is within 1e-6, or when the target-th best window residual stops improving
+        // (the solve's own error then limits the eigenvectors far from sigma)
+        {
+            std::vector<double> wr;
+            for (int i = 0; i < k; ++i)
+                if (th[i] > lo && th[i] <= hi) wr.push_back(rs[i]);
+            std::sort(wr.begin(), wr.end());
+            const int target = o.n_expect > 0 ? o.n_expect : std::max(1, nin - 2);
+            const double rt = (int)wr.size() >= target ? wr[target - 1] : INFINITY;
+            hist.push_back(rt);
+            const size_t h = hist.size();
+            const bool stalled = h >= 5 && !(hist[h - 1] < 0.5 * hist[h - 4]);
+            near_conv = near_conv || rt <= 1e-6 || stalled;
+        }
     }
     (void)have_rr;
     (void)maxr_all;

@@ -235,7 +235,7 @@ class SliceSolver:
         return lam_min, lo
 
     def run(self, shifts, lam_min, lam_max, model: DosModel = None, k=None, V0=None, max_rounds=30,
-            block=64, seed=0, driver="subspace", iters_per_round=2, first_iters=80, splits=None, ks=None):
+            block=64, seed=0, driver="subspace", iters_per_round=3, first_iters=80, splits=None, ks=None):
         """Factor the shifts and the two region bounds in one batched call, build every
         probe, validate every slice, and refine the probes next to any slice that does
         not validate yet (fewer converged candidates than its exact count).
@@ -277,6 +277,9 @@ class SliceSolver:
         g = torch.Generator(device="cuda").manual_seed(seed)
         probes = [None] * ns
         Xs = [None] * ns
+        f64 = {}                  # FP64 refactors of mixed shifts whose probes stalled
+        stall = [0] * ns
+        best = [np.inf] * ns
         active = list(range(ns))
         rounds = 0
         t_solve = 0.0
@@ -303,11 +306,15 @@ class SliceSolver:
                     if Xs[j] is None:
                         v0 = V0[j] if V0 is not None else torch.randn(n, kk, generator=g, device="cuda",
                                                                      dtype=torch.float64)
-                        mi, ne = first_iters, max(1, cnt[j] - 2)
+                        # stop the first round at 80% of the window's estimated count;
+                        # validation then tops up with short rounds
+                        est = (float(model.Phi(hi)[0] - model.Phi(lo)[0]) if model is not None else cnt[j])
+                        mi, ne = first_iters, max(1, int(0.8 * est))
                     else:
                         v0, mi, ne = Xs[j], iters_per_round, v0_never(Xs[j])
-                    pr = f.slice_solve(j, lo, hi, v0, tol=self.tol, max_iter=mi, refine=self.refine,
-                                       n_expect=ne, allow_noconv=True)
+                    fj, jj = (f64[j], 0) if j in f64 else (f, j)
+                    pr = fj.slice_solve(jj, lo, hi, v0, tol=self.tol, max_iter=mi, refine=self.refine,
+                                        n_expect=ne, allow_noconv=True, refine_from_start=Xs[j] is not None)
                 probes[j] = pr
                 Xs[j] = pr.X
                 iters[j] += pr.iterations
@@ -322,15 +329,30 @@ class SliceSolver:
                     if s_ < ns:
                         bad.add(s_)
             active = sorted(bad)
+            # a mixed-precision probe whose window residuals stop improving is moved to an
+            # FP64 factor of its shift (the FP32 factor limits its accuracy)
+            for j in active:
+                if self.precision != "mixed" or j in f64 or f.quality(j)[0] == "fp64":
+                    continue
+                lo, hi = windows[j]
+                pr = probes[j]
+                inw = (pr.theta > lo) & (pr.theta <= hi)
+                r = float(np.sort(pr.resid[inw])[-1]) if inw.any() else np.inf
+                stall[j] = stall[j] + 1 if not (r < 0.5 * best[j]) else 0
+                best[j] = min(best[j], r)
+                if stall[j] >= 3:
+                    f64[j] = self.sym.factor(self.a, self.b, [shifts[j]], "fp64")
         lam = np.array([probes[pj].theta[i] for pj, i in sel])
         res = np.array([probes[pj].resid[i] for pj, i in sel])
         order = np.argsort(lam, kind="stable")
         X = torch.stack([probes[sel[q][0]].X[:, sel[q][1]] for q in order], dim=1) if sel else None
         f.close()
+        for g64 in f64.values():
+            g64.close()
         return SliceResult(list(shifts), lam_min, lam_max, lam[order], X, res[order], info, probes, rounds,
                            dict(factor_s=t_factor, solve_s=t_solve, total_s=time.perf_counter() - t0,
                                 iterations=iters, n_below_max=nneg_max, n_below_min=nneg_min,
-                                converged=not active))
+                                converged=not active, fp64_refactors=sorted(f64)))
 
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,
