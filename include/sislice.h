@@ -255,7 +255,8 @@ ss_status ss_spmm(ss_symbolic *sym, const double *a_vals, const double *b_vals,
 ss_status ss_sync(ss_ctx *ctx);
 
 /* ---- measurement hooks (no paper counterpart) -------------------------------------
- * Kernel classes, for per-class timing.  ss_launch_count returns the number of
+ * Kernel classes, for per-class timing (bit c of a mask = class c; at most 32).
+ * ss_launch_count returns the number of
  * kernels this library has launched since it was loaded (all contexts).
  * ss_profile(ctx, mask) starts timing every launch of the classes whose bit is set
  * in mask (bit c = class c) with CUDA events recorded on the launching stream, and
@@ -265,11 +266,16 @@ ss_status ss_sync(ss_ctx *ctx);
 enum {
     SS_K_ASSEMBLE = 0, SS_K_EXTEND_ADD, SS_K_DIAG_BK, SS_K_PANEL, SS_K_SCHUR, SS_K_FWD_DIAG,
     SS_K_FWD_UPDATE, SS_K_BWD_GATHER, SS_K_BWD_DIAG, SS_K_PERMUTE, SS_K_SPMM, SS_K_GRAM,
-    SS_K_GEMM, SS_K_SMALL_DENSE, SS_K_JACOBI, SS_K_LANCZOS, SS_K_SDDMM, SS_K_MISC, SS_K_COUNT
+    SS_K_GEMM, SS_K_SMALL_DENSE, SS_K_JACOBI, SS_K_LANCZOS, SS_K_SDDMM, SS_K_MISC,
+    SS_K_PANEL_F32, SS_K_SCHUR_F32, SS_K_FWD_UPDATE_F32, SS_K_BWD_GATHER_F32, SS_K_COUNT
 };
 int64_t ss_launch_count(void);
 ss_status ss_profile(ss_ctx *ctx, uint32_t mask);
-ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds);
+/* *flops (may be NULL): algorithmic flops of the timed launches of the classes that
+ * count them (panel, Schur, solve sweeps, SpMM, Gram, GEMM; 2 per multiply-add, lower
+ * triangle only for the Schur update); 0 for the others.  Classes ending in _F32 are the
+ * FP32 instantiations of the mixed-precision factor and solves. */
+ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds, double *flops);
 
 #ifdef __cplusplus
 }

@@ -46,7 +46,8 @@ EXPORTS = ["ss_create", "ss_destroy", "ss_last_error", "ss_analyze", "ss_symboli
            "ss_symbolic_perm", "ss_symbolic_destroy", "ss_symbolic_validate", "ss_factor", "ss_factor_destroy", "ss_inertia", "ss_factor_stats", "ss_factor_quality",
            "ss_solve", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query"]
 KERNEL_CLASSES = ["assemble", "extend_add", "diag_bk", "panel", "schur", "fwd_diag", "fwd_update", "bwd_gather",
-                  "bwd_diag", "permute", "spmm", "gram", "gemm", "small_dense", "jacobi", "lanczos", "sddmm", "misc"]
+                  "bwd_diag", "permute", "spmm", "gram", "gemm", "small_dense", "jacobi", "lanczos", "sddmm", "misc",
+                  "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32"]
 
 _lib = None
 
@@ -85,7 +86,7 @@ def load():
         "ss_sync": ([P], i32),
         "ss_launch_count": ([], i64),
         "ss_profile": ([P, C.c_uint32], i32),
-        "ss_profile_query": ([P, i32, C.POINTER(i64), C.POINTER(dbl)], i32),
+        "ss_profile_query": ([P, i32, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)

@@ -83,11 +83,12 @@ class Context:
         self.check(self.lib.ss_profile(self.h, mask), "ss_profile")
 
     def profile_query(self, cls: str):
-        """(launches, seconds) of a kernel class since profile() (synchronises)."""
-        n, t = C.c_int64(), C.c_double()
-        self.check(self.lib.ss_profile_query(self.h, L.KERNEL_CLASSES.index(cls), C.byref(n), C.byref(t)),
+        """(launches, seconds, algorithmic flops) of a kernel class since profile()
+        (synchronises)."""
+        n, t, fl = C.c_int64(), C.c_double(), C.c_double()
+        self.check(self.lib.ss_profile_query(self.h, L.KERNEL_CLASSES.index(cls), C.byref(n), C.byref(t), C.byref(fl)),
                    "ss_profile_query")
-        return n.value, t.value
+        return n.value, t.value, fl.value
 
     def close(self):
         if getattr(self, "h", None):

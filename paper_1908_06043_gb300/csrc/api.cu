@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <cstring>
 #include <new>
 #include <string>
@@ -53,18 +54,23 @@ extern "C" ss_status ss_profile(ss_ctx *ctx, uint32_t mask) {
     if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     ctx->ev_used.clear();
-    for (int c = 0; c < SS_K_COUNT; ++c) { ctx->prof_launches[c] = 0; ctx->prof_seconds[c] = 0.0; }
+    for (int c = 0; c < SS_K_COUNT; ++c) {
+        ctx->prof_launches[c] = 0;
+        ctx->prof_seconds[c] = 0.0;
+        ctx->prof_flops[c] = 0.0;
+    }
     ctx->prof_mask = mask;
     return SS_OK;
 }
 
-extern "C" ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds) {
+extern "C" ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds, double *flops) {
     if (!ctx || cls < 0 || cls >= SS_K_COUNT) return SS_ERR_ARG;
     if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     prof_collect(ctx);
     if (launches) *launches = ctx->prof_launches[cls];
     if (seconds) *seconds = ctx->prof_seconds[cls];
+    if (flops) *flops = ctx->prof_flops[cls];
     return SS_OK;
 }
 
@@ -248,9 +254,17 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
             const StepTask *tk = s->d_tasks + sd.task_off;
             ss_launch(ctx, SS_K_DIAG_BK, k_diag_bk<T>, dim3(sd.count, ns), 256, kDiagSmem, st, tk, dp, 0);
             if (sd.tiles4 > 0)
-                ss_launch(ctx, SS_K_PANEL, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count, dp);
+            {
+                const int cls = std::is_same<T, float>::value ? SS_K_PANEL_F32 : SS_K_PANEL;
+                ss_launch(ctx, cls, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count, dp);
+                ctx->add_flops(cls, sd.flops4 * ns);
+            }
             if (sd.tiles3 > 0)
-                ss_launch(ctx, SS_K_SCHUR, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count, dp);
+            {
+                const int cls = std::is_same<T, float>::value ? SS_K_SCHUR_F32 : SS_K_SCHUR;
+                ss_launch(ctx, cls, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count, dp);
+                ctx->add_flops(cls, sd.flops3 * ns);
+            }
         }
     }
     SS_CUDA_TRY(ctx, cudaGetLastError());
@@ -457,8 +471,10 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
         ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, lp, s->d_panels, f->linv[j],
                                                                                f->piv[j], b, k);
         if (sl.row_tiles > 0)
-            ss_launch(ctx, SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
+            ss_launch(ctx, std::is_same<T, float>::value ? SS_K_FWD_UPDATE_F32 : SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k);
+        if (sl.row_tiles > 0)
+            ctx->add_flops(std::is_same<T, float>::value ? SS_K_FWD_UPDATE_F32 : SS_K_FWD_UPDATE, 2.0 * sl.offdiag * k);
     }
     if (!backward) return SS_OK;
     int32_t maxc = 0;
@@ -470,8 +486,9 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
         const int32_t *lp = s->d_solve_panels + sl.panel_off;
         if (sl.row_tiles > 0) {
             SS_CUDA_TRY(ctx, cudaMemsetAsync(z, 0, sizeof(T) * (int64_t)sl.count * NB * k, st));
-            ss_launch(ctx, SS_K_BWD_GATHER, k_bwd_gather<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
+            ss_launch(ctx, std::is_same<T, float>::value ? SS_K_BWD_GATHER_F32 : SS_K_BWD_GATHER, k_bwd_gather<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k, z);
+            ctx->add_flops(std::is_same<T, float>::value ? SS_K_BWD_GATHER_F32 : SS_K_BWD_GATHER, 2.0 * sl.offdiag * k);
         }
         ss_launch(ctx, SS_K_BWD_DIAG, k_bwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, 
             lp, s->d_panels, f->linv[j], f->dblk[j], f->piv[j], z, sl.row_tiles > 0 ? 1 : 0, b, k, dinv);
@@ -532,6 +549,7 @@ int spmm_launch_ld(ss_symbolic *s, const double *a, const double *b, const doubl
         ss_launch(ctx, SS_K_SPMM, sss::k_spmm_cols, grid, 256, 0, ctx->stream, s->n, s->d_rowptr, s->d_colind, a, b,
                   alpha, beta, X, ldx, k, Y, ldy);
 #undef SS_SPMM_ROWS
+    ctx->add_flops(SS_K_SPMM, (beta ? 4.0 : 2.0) * (double)s->nnz * k);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }

@@ -22,6 +22,10 @@ struct ss_ctx {
     std::vector<std::pair<int, size_t>> ev_used;     // (class, index of the start event)
     int64_t prof_launches[SS_K_COUNT] = {};
     double prof_seconds[SS_K_COUNT] = {};
+    double prof_flops[SS_K_COUNT] = {};
+    void add_flops(int cls, double f) {
+        if (prof_mask & (1u << cls)) prof_flops[cls] += f;
+    }
     int set_error(int code, const std::string &msg) {
         err = msg;
         return code;
@@ -83,6 +87,7 @@ struct StepDesc {
     int32_t count;       // fronts in this step
     int32_t tiles4, tiles3;
     int32_t level;
+    double flops4, flops3;   // algorithmic flops of the panel transform / Schur update
 };
 
 // Child -> parent extend-add unit: child front contribution block (rows [ncol, m))
@@ -102,6 +107,7 @@ struct SolveLevel {      // panels whose forward step can run together
     int64_t panel_off;   // into solve_panels
     int32_t count;
     int32_t row_tiles;   // total row tiles (64 rows) of the panels' below-diagonal rows
+    double offdiag;      // sum over its panels of (rows below the diagonal block) x w
 };
 
 struct ss_symbolic {

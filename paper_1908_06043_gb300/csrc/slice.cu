@@ -56,6 +56,7 @@ int gram_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const 
     nz = (n + per - 1) / per;
     ss_launch(ctx, SS_K_GRAM, ssd::k_gram, dim3(cdiv(k1, 32), cdiv(k2, 32), (unsigned)std::max<int64_t>(1, nz)), 256,
               0, st, n, X, ldx, k1, Y, ldy, k2, per, G);
+    ctx->add_flops(SS_K_GRAM, 2.0 * (double)n * k1 * k2);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }
@@ -69,6 +70,7 @@ int gemm_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const 
             double alpha, double beta, double *Y, int64_t ldy) {
     ss_launch(ctx, SS_K_GEMM, ssd::k_gemm_tall, dim3(cdiv(n, 64), cdiv(k2, 32)), 256, 0, ctx->stream, n, X, ldx, k1,
               Q, k2, transq, alpha, beta, Y, ldy);
+    ctx->add_flops(SS_K_GEMM, 2.0 * (double)n * k1 * k2);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }

@@ -52,28 +52,28 @@ __global__ void __launch_bounds__(256) k_spmm_rows(int64_t n, const int64_t *__r
 #pragma unroll
     for (int t = 0; t < NC; ++t) { acc_a[t] = 0.0; acc_b[t] = 0.0; }
     const int64_t p0 = rowptr[row], p1 = rowptr[row + 1];
-    if (use_b) {
-        for (int64_t p = p0; p < p1; ++p) {
-            const double av = a[p], bv = b[p];
-            const double *x = X + (int64_t)colind[p] * ldx;
+    // the row's column indices and values are loaded 32 at a time (one per lane) and
+    // broadcast, so consecutive X-row loads do not wait on each other
+    for (int64_t q0 = p0; q0 < p1; q0 += 32) {
+        const int cnt = (int)min((int64_t)32, p1 - q0);
+        const int64_t q = q0 + lane;
+        const int my_col = lane < cnt ? colind[q] : 0;
+        const double my_a = lane < cnt ? a[q] : 0.0;
+        const double my_b = (use_b && lane < cnt) ? b[q] : 0.0;
+#pragma unroll 4
+        for (int e = 0; e < cnt; ++e) {
+            const int col = __shfl_sync(0xffffffffu, my_col, e);
+            const double av = __shfl_sync(0xffffffffu, my_a, e);
+            const double bv = __shfl_sync(0xffffffffu, my_b, e);
+            const double *x = X + (int64_t)col * ldx;
 #pragma unroll
             for (int t = 0; t < NC; ++t) {
                 const int c = lane + 32 * t;
                 if (c < k) {
                     const double xv = x[c];
                     acc_a[t] += av * xv;
-                    acc_b[t] += bv * xv;
+                    if (use_b) acc_b[t] += bv * xv;
                 }
-            }
-        }
-    } else {
-        for (int64_t p = p0; p < p1; ++p) {
-            const double av = a[p];
-            const double *x = X + (int64_t)colind[p] * ldx;
-#pragma unroll
-            for (int t = 0; t < NC; ++t) {
-                const int c = lane + 32 * t;
-                if (c < k) acc_a[t] += av * x[c];
             }
         }
     }

@@ -424,7 +424,7 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
         int32_t T = 0;
         for (int32_t b : lev_sn[l]) T = std::max<int32_t>(T, (int32_t)cdiv(ncol(b), nb));
         for (int32_t t = 0; t < T; ++t) {
-            StepDesc sd{(int64_t)s->tasks.size(), 0, 0, 0, l};
+            StepDesc sd{(int64_t)s->tasks.size(), 0, 0, 0, l, 0.0, 0.0};
             int64_t wb = 0;
             for (int32_t b : lev_sn[l]) {
                 if ((int64_t)t * nb >= ncol(b)) continue;
@@ -443,6 +443,8 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
                 int32_t nt = (int32_t)cdiv(tk.r, 64);
                 sd.tiles4 += nt;
                 sd.tiles3 += nt * (nt + 1) / 2;
+                sd.flops4 += 2.0 * tk.r * (double)tk.w * tk.w;
+                sd.flops3 += (double)tk.w * tk.r * (tk.r + 1.0);
                 sd.count++;
                 s->tasks.push_back(tk);
             }
@@ -475,12 +477,13 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
     s->solve_levels.clear();
     s->solve_tile_pre.clear();
     for (int32_t l = 0; l < nplev; ++l) {
-        SolveLevel sl{(int64_t)s->solve_panels.size(), 0, 0};
+        SolveLevel sl{(int64_t)s->solve_panels.size(), 0, 0, 0.0};
         for (int32_t p : by_lev[l]) {
             const PanelDesc &pd = s->panels[p];
             s->solve_panels.push_back(p);
             s->solve_tile_pre.push_back(sl.row_tiles);
             sl.row_tiles += (int32_t)cdiv(pd.m - pd.k0 - pd.w, 64);
+            sl.offdiag += (double)(pd.m - pd.k0 - pd.w) * pd.w;
             sl.count++;
         }
         s->solve_levels.push_back(sl);
