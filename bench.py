@@ -224,9 +224,10 @@ def main():
         return ok
 
     if args.only_probe:
-        # one representative probe of the workload (shift 8 of the placement), for ncu
-        start = torch.tensor(normal_block(p.n, n_vec, 1000), device="cuda")
-        model = DosModel(p.n, sym.dos_estimate(a, b, steps_dos, start))
+        # one representative probe of the workload (shift 8 of the placement), for ncu; a
+        # short DOS run (20 steps, one vector) keeps the launch count small
+        start = torch.tensor(normal_block(p.n, 1, 1000), device="cuda")
+        model = DosModel(p.n, sym.dos_estimate(a, b, 20, start))
         solver = SliceSolver(sym, a, b, precision="fp64")
         lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
         j = n_s // 2

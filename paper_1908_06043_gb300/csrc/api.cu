@@ -464,11 +464,12 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     set_smem_attrs<T>();
     const T *arena = (const T *)f->arena[j];
     const int nchunk = (k + KC - 1) / KC;
+    const int ndchunk = (k + KD - 1) / KD;
     const int nlev = (int)s->solve_levels.size();
     for (int L = 0; forward && L < nlev; ++L) {
         const SolveLevel &sl = s->solve_levels[L];
         const int32_t *lp = s->d_solve_panels + sl.panel_off;
-        ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, lp, s->d_panels, f->linv[j],
+        ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<T>, dim3(sl.count, ndchunk), 256, diag_solve_smem<T>(), st, lp, s->d_panels, f->linv[j],
                                                                                f->piv[j], b, k);
         if (sl.row_tiles > 0)
             ss_launch(ctx, std::is_same<T, float>::value ? SS_K_FWD_UPDATE_F32 : SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
@@ -490,7 +491,7 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k, z);
             ctx->add_flops(std::is_same<T, float>::value ? SS_K_BWD_GATHER_F32 : SS_K_BWD_GATHER, 2.0 * sl.offdiag * k);
         }
-        ss_launch(ctx, SS_K_BWD_DIAG, k_bwd_diag<T>, dim3(sl.count, nchunk), 256, diag_solve_smem<T>(), st, 
+        ss_launch(ctx, SS_K_BWD_DIAG, k_bwd_diag<T>, dim3(sl.count, ndchunk), 256, diag_solve_smem<T>(), st, 
             lp, s->d_panels, f->linv[j], f->dblk[j], f->piv[j], z, sl.row_tiles > 0 ? 1 : 0, b, k, dinv);
     }
     SS_CUDA_TRY(ctx, cudaFreeAsync(z, st));

@@ -95,89 +95,93 @@ __global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__re
 }
 
 // ---------------------------------------------------------------- small Cholesky
-// G (k x k, row-major, symmetric) -> lower R with G = R R^T, upper part zeroed.
-// info[0] = 0 ok, j+1 if the j-th pivot was not positive.  One block of 1024 threads,
-// blocked right-looking over 32-column panels: the panel's diagonal block is factored
-// by one warp, the rows below it are solved against it, the finished panel is staged in
-// shared memory and the trailing lower triangle is updated from there.
-// Dynamic shared memory: k * 33 doubles (the staged panel).
 constexpr int CH_NB = 32;
-__global__ void __launch_bounds__(1024) k_chol_small(double *G, int k, int *info) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    double *P = reinterpret_cast<double *>(smem_raw);          // panel rows, ld 33
+
+// Multi-block blocked Cholesky, one 32-column panel per three launches:
+//   k_chol_diag  factors the panel's diagonal block (one warp, shared memory);
+//   k_chol_trsm  solves the rows below against it (one warp per row);
+//   k_chol_syrk  updates the trailing lower triangle, one 32 x 32 tile per block.
+// info[0] != 0 (a non-positive pivot) makes every later launch return at once.
+__global__ void __launch_bounds__(32) k_chol_diag(double *G, int k, int j0, int *info) {
     __shared__ double Dg[CH_NB][CH_NB + 1];
-    __shared__ int s_bad;
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-    if (tid == 0) s_bad = 0;
+    if (info[0]) return;
+    const int lane = threadIdx.x, w = min(CH_NB, k - j0);
+    for (int q = lane; q < w * w; q += 32) {
+        int i = q / w, c = q % w;
+        Dg[i][c] = (c <= i) ? G[(int64_t)(j0 + i) * k + j0 + c] : 0.0;
+    }
+    __syncwarp();
+    int bad = 0;
+    for (int c = 0; c < w; ++c) {
+        double d = Dg[c][c];
+        if (!(d > 0.0)) { if (!bad) bad = j0 + c + 1; d = 1.0; }
+        const double sd = sqrt(d);
+        __syncwarp();
+        if (lane == 0) Dg[c][c] = sd;
+        __syncwarp();
+        const double inv = 1.0 / sd;
+        for (int i = c + 1 + lane; i < w; i += 32) Dg[i][c] *= inv;
+        __syncwarp();
+        for (int i = c + 1 + lane; i < w; i += 32)
+            for (int l = c + 1; l <= i; ++l) Dg[i][l] -= Dg[i][c] * Dg[l][c];
+        __syncwarp();
+    }
+    for (int q = lane; q < w * w; q += 32) {
+        int i = q / w, c = q % w;
+        if (c <= i) G[(int64_t)(j0 + i) * k + j0 + c] = Dg[i][c];
+    }
+    if (lane == 0 && bad) info[0] = bad;
+}
+
+__global__ void __launch_bounds__(256) k_chol_trsm(double *G, int k, int j0, const int *info) {
+    __shared__ double Dg[CH_NB][CH_NB + 1];
+    if (info[0]) return;
+    const int w = min(CH_NB, k - j0), lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int q = threadIdx.x; q < w * w; q += 256) {
+        int i = q / w, c = q % w;
+        Dg[i][c] = (c <= i) ? G[(int64_t)(j0 + i) * k + j0 + c] : 0.0;
+    }
     __syncthreads();
-    for (int j0 = 0; j0 < k && !s_bad; j0 += CH_NB) {
-        const int w = min(CH_NB, k - j0);
-        // 1. factor the w x w diagonal block (warp 0, in shared memory)
-        for (int q = tid; q < w * w; q += nt) {
-            int i = q / w, c = q % w;
-            Dg[i][c] = (c <= i) ? G[(int64_t)(j0 + i) * k + j0 + c] : 0.0;
-        }
-        __syncthreads();
-        if (wid == 0) {
-            for (int c = 0; c < w; ++c) {
-                double d = Dg[c][c];
-                if (!(d > 0.0)) {
-                    if (lane == 0 && !s_bad) s_bad = j0 + c + 1;
-                    d = 1.0;
-                }
-                const double sd = sqrt(d);
-                __syncwarp();
-                if (lane == 0) Dg[c][c] = sd;
-                __syncwarp();
-                const double inv = 1.0 / sd;
-                for (int i = c + 1 + lane; i < w; i += 32) Dg[i][c] *= inv;
-                __syncwarp();
-                for (int i = c + 1 + lane; i < w; i += 32)
-                    for (int l = c + 1; l <= i; ++l) Dg[i][l] -= Dg[i][c] * Dg[l][c];
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        if (s_bad) break;
-        for (int q = tid; q < w * w; q += nt) {
-            int i = q / w, c = q % w;
-            if (c <= i) G[(int64_t)(j0 + i) * k + j0 + c] = Dg[i][c];
-            P[i * 33 + c] = (c <= i) ? Dg[i][c] : 0.0;
-        }
-        // 2. rows below: L[i][J] = G[i][J] L_JJ^-T (forward substitution per row, one warp per row)
-        for (int i = j0 + w + wid; i < k; i += nw) {
-            double x = (lane < w) ? G[(int64_t)i * k + j0 + lane] : 0.0;
-            for (int c = 0; c < w; ++c) {
-                double xc = __shfl_sync(0xffffffffu, x, c) / Dg[c][c];
-                if (lane == c) x = xc;
-                if (lane > c && lane < w) x -= xc * Dg[lane][c];
-            }
-            if (lane < w) {
-                G[(int64_t)i * k + j0 + lane] = x;
-                P[(i - j0) * 33 + lane] = x;
-            }
-        }
-        __syncthreads();
-        // 3. trailing update G[i][l] -= sum_c L[i][c] L[l][c], j0+w <= l <= i
-        for (int i = j0 + w + wid; i < k; i += nw) {
-            const double *pi = P + (i - j0) * 33;
-            double *gi = G + (int64_t)i * k;
-            for (int l = j0 + w + lane; l <= i; l += 32) {
-                const double *pl = P + (l - j0) * 33;
-                double acc = 0.0;
+    const int i = j0 + w + blockIdx.x * 8 + wid;
+    if (i >= k) return;
+    double x = (lane < w) ? G[(int64_t)i * k + j0 + lane] : 0.0;
+    for (int c = 0; c < w; ++c) {
+        double xc = __shfl_sync(0xffffffffu, x, c) / Dg[c][c];
+        if (lane == c) x = xc;
+        if (lane > c && lane < w) x -= xc * Dg[lane][c];
+    }
+    if (lane < w) G[(int64_t)i * k + j0 + lane] = x;
+}
+
+__global__ void __launch_bounds__(256) k_chol_syrk(double *G, int k, int j0, const int *info) {
+    __shared__ double Pi[CH_NB][CH_NB + 1], Pl[CH_NB][CH_NB + 1];
+    if (info[0]) return;
+    const int w = min(CH_NB, k - j0), base = j0 + w;
+    int q = blockIdx.x, bi = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
+    while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+    while (bi * (bi + 1) / 2 > q) --bi;
+    const int bj = q - bi * (bi + 1) / 2;
+    const int i0 = base + 32 * bi, l0 = base + 32 * bj;
+    for (int e = threadIdx.x; e < 32 * CH_NB; e += 256) {
+        int r = e / CH_NB, c = e % CH_NB;
+        Pi[r][c] = (i0 + r < k && c < w) ? G[(int64_t)(i0 + r) * k + j0 + c] : 0.0;
+        Pl[r][c] = (l0 + r < k && c < w) ? G[(int64_t)(l0 + r) * k + j0 + c] : 0.0;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * 32; e += 256) {
+        const int r = e >> 5, c = e & 31;
+        const int i = i0 + r, l = l0 + c;
+        if (i >= k || l > i) continue;
+        double acc = 0.0;
 #pragma unroll 8
-                for (int c = 0; c < w; ++c) acc += pi[c] * pl[c];
-                gi[l] -= acc;
-            }
-        }
-        __syncthreads();
+        for (int t = 0; t < CH_NB; ++t) acc += Pi[r][t] * Pl[c][t];
+        G[(int64_t)i * k + l] -= acc;
     }
-    if (tid == 0) info[0] = s_bad;
-    __syncthreads();
-    for (int64_t q = tid; q < (int64_t)k * k; q += nt) {
-        int i = (int)(q / k), l = (int)(q % k);
-        if (l > i) G[q] = 0.0;
-    }
+}
+
+__global__ void k_zero_upper(double *G, int k) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < (int64_t)k * k && q % k > q / k) G[q] = 0.0;
 }
 
 // Rinv = R^-1 for lower-triangular R (k x k row-major).  Column blocks of R^-1 are

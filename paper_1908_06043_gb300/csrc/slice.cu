@@ -156,15 +156,23 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
     return SS_OK;
 }
 
-// the blocked Cholesky stages a k x 32 panel in shared memory (k <= 800)
-int chol_attr(ss_ctx *ctx, int k) {
-    if (k > 800) return ctx->set_error(SS_ERR_ARG, "Cholesky-QR: basis wider than 800 columns");
-    static bool done = false;
-    if (!done) {
-        SS_CUDA_TRY(ctx, cudaFuncSetAttribute(ssd::k_chol_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)(sizeof(double) * 33 * 800)));
-        done = true;
+// G = R R^T in place (lower R, upper part zeroed) by the multi-block blocked Cholesky;
+// *info (device) is 0 or the first failing pivot index + 1.
+int chol_small(ss_ctx *ctx, double *G, int k, int *info) {
+    cudaStream_t st = ctx->stream;
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(info, 0, sizeof(int), st));
+    for (int j0 = 0; j0 < k; j0 += ssd::CH_NB) {
+        const int w = std::min(ssd::CH_NB, k - j0), rem = k - j0 - w;
+        ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_diag, 1, 32, 0, st, G, k, j0, info);
+        if (rem > 0) {
+            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_trsm, cdiv(rem, 8), 256, 0, st, G, k, j0, (const int *)info);
+            const int nt = (int)cdiv(rem, 32);
+            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_syrk, (unsigned)(nt * (nt + 1) / 2), 256, 0, st, G, k, j0,
+                      (const int *)info);
+        }
     }
+    ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_zero_upper, cdiv((int64_t)k * k, 256), 256, 0, st, G, k);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }
 
@@ -176,7 +184,6 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     int rc;
-    if ((rc = chol_attr(ctx, k)) != SS_OK) return rc;
     for (int pass = 0; pass < 2; ++pass) {
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, Wk)) != SS_OK) return rc;
         if ((rc = gram(ctx, V, s->n, k, Wk, k, G)) != SS_OK) return rc;
@@ -191,7 +198,7 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
                                    (attempt == 1 ? 1.0 : 1e4);
                 ss_launch(ctx, SS_K_SMALL_DENSE, k_add_shift_diag, 1, 256, 0, st, G, k, rel);
             }
-            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, sizeof(double) * 33 * (size_t)k, st, G, k, info);
+            if ((rc = chol_small(ctx, G, k, info)) != SS_OK) return rc;
             SS_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
             if (hinfo == 0) break;
@@ -210,13 +217,12 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
 // W <- W R^-T, BW <- BW R^-T, twice (Cholesky-QR2); a failed Cholesky is retried with
 // a diagonal shift of G (shifted Cholesky-QR).  Wt, BWt: n x k scratch (swapped in).
 int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&BWt, int k, double *G, double *Rinv,
-                 int *info) {
+                 int *info, int passes = 2) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     int rc;
-    if ((rc = chol_attr(ctx, k)) != SS_OK) return rc;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < passes; ++pass) {
         int hinfo = 0;
         for (int attempt = 0; attempt < 3; ++attempt) {
             if ((rc = gram(ctx, W, s->n, k, BW, k, G)) != SS_OK) return rc;
@@ -226,7 +232,7 @@ int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&B
                                    (attempt == 1 ? 1.0 : 1e4);
                 ss_launch(ctx, SS_K_SMALL_DENSE, k_add_shift_diag, 1, 256, 0, st, G, k, rel);
             }
-            ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_chol_small, 1, 1024, sizeof(double) * 33 * (size_t)k, st, G, k, info);
+            if ((rc = chol_small(ctx, G, k, info)) != SS_OK) return rc;
             SS_CUDA_TRY(ctx, cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, st));
             SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
             if (hinfo == 0) break;
@@ -292,8 +298,11 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref)) != SS_OK) return rc;
         refine_total += done_ref;
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;
-        if ((rc = cholqr_track(f, W, BW, T1, T2, k, G, Rinv, info)) != SS_OK) return rc;   // Alg. 2 step 4
-        if (it % every != 0 && it != max_iter) {
+        // Alg. 2 step 4; one Cholesky-QR pass when no Rayleigh-Ritz follows (the next
+        // solve only needs a well-conditioned basis), two before a Rayleigh-Ritz
+        const bool rr_now = (it % every == 0) || it == max_iter;
+        if ((rc = cholqr_track(f, W, BW, T1, T2, k, G, Rinv, info, rr_now ? 2 : 1)) != SS_OK) return rc;
+        if (!rr_now) {
             std::swap(V, W);
             std::swap(BV, BW);
             continue;

@@ -16,9 +16,12 @@
 
 namespace ssk {
 
-constexpr int KC = 32;     // right-hand-side columns per block
+constexpr int KC = 32;     // right-hand-side columns per block of the update / gather kernels
+constexpr int KD = 8;      // right-hand-side columns per block of the diagonal kernels: they
+                           // run alone on the long chain of root panels, so narrow chunks
+                           // spread each level over more SMs
 // dynamic shared memory of the solve kernels
-template <typename T> constexpr size_t diag_solve_smem() { return sizeof(T) * NB * ((KC + 1) + (NB + 1)); }
+template <typename T> constexpr size_t diag_solve_smem() { return sizeof(T) * NB * ((KD + 1) + (NB + 1)); }
 template <typename T> constexpr size_t tile_solve_smem() { return sizeof(T) * (NB * (TR + 1) + TR * (KC + 1)); }
 
 __device__ __forceinline__ void atomic_add_t(double *p, double v) { atomicAdd(p, v); }
@@ -31,14 +34,14 @@ __global__ void __launch_bounds__(256) k_fwd_diag(const int32_t *__restrict__ lv
                                                    const double *__restrict__ linv,
                                                    const int32_t *__restrict__ piv, T *b, int k) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*Y)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw);
-    T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KC + 1));
+    T (*Y)[KD + 1] = reinterpret_cast<T (*)[KD + 1]>(smem_raw);
+    T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KD + 1));
     const int p = lvl_panels[blockIdx.x];
     const PanelDesc pd = panels[p];
-    const int w = pd.w, c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const int w = pd.w, c0 = blockIdx.y * KD, kc = min(KD, k - c0);
     const int tid = threadIdx.x;
-    for (int q = tid; q < w * KC; q += 256) {
-        int i = q / KC, c = q % KC;
+    for (int q = tid; q < w * KD; q += 256) {
+        int i = q / KD, c = q % KD;
         int src = piv[(int64_t)p * NB + i];
         Y[i][c] = c < kc ? b[(int64_t)(pd.g0 + src) * k + c0 + c] : (T)0;
     }
@@ -47,8 +50,8 @@ __global__ void __launch_bounds__(256) k_fwd_diag(const int32_t *__restrict__ lv
         Lm[i][j] = (T)linv[(int64_t)p * NB * NB + i * NB + j];
     }
     __syncthreads();
-    for (int q = tid; q < w * KC; q += 256) {
-        int i = q / KC, c = q % KC;
+    for (int q = tid; q < w * KD; q += 256) {
+        int i = q / KD, c = q % KD;
         if (c >= kc) continue;
         T acc = 0;
         for (int t = 0; t <= i; ++t) acc += Lm[i][t] * Y[t][c];
@@ -160,13 +163,13 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
                                                    const T *__restrict__ zbuf, int use_z, T *x,
                                                    int k, int dinv) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*U)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw);
-    T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KC + 1));
+    T (*U)[KD + 1] = reinterpret_cast<T (*)[KD + 1]>(smem_raw);
+    T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KD + 1));
     __shared__ double sd[NB], se[NB];
     const int slot = blockIdx.x;
     const int p = lvl_panels[slot];
     const PanelDesc pd = panels[p];
-    const int w = pd.w, c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const int w = pd.w, c0 = blockIdx.y * KD, kc = min(KD, k - c0);
     const int tid = threadIdx.x;
     if (tid < NB) {
         sd[tid] = dblk[(int64_t)p * 2 * NB + tid];
@@ -176,16 +179,17 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
         int i = q / w, j = q % w;
         Lm[i][j] = (T)linv[(int64_t)p * NB * NB + i * NB + j];
     }
-    for (int q = tid; q < w * KC; q += 256) {
-        int i = q / KC, c = q % KC;
+    for (int q = tid; q < w * KD; q += 256) {
+        int i = q / KD, c = q % KD;
         U[i][c] = c < kc ? x[(int64_t)(pd.g0 + i) * k + c0 + c] : (T)0;
     }
     __syncthreads();
-    T val[NB / 8];
-    // u = Dinv y - z, each thread handles entries (i, c) with i = tid/32 + 8a
-    const int c = tid & 31, rr = tid >> 5;
-    for (int a = 0; a < NB / 8; ++a) {
-        int i = rr + 8 * a;
+    T val[NB * KD / 256];
+    // u = Dinv y - z, each thread handles entries (i, c) with i = tid/KD + (256/KD) a
+    const int c = tid % KD, rr = tid / KD;
+    constexpr int RS = 256 / KD;
+    for (int a = 0; a < NB * KD / 256; ++a) {
+        int i = rr + RS * a;
         double u = 0.0;
         if (i < w && c < kc) {
             if (!dinv) {                            // half solve: D^-1/2 applied beforehand
@@ -204,14 +208,14 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
         val[a] = (T)u;
     }
     __syncthreads();
-    for (int a = 0; a < NB / 8; ++a) {
-        int i = rr + 8 * a;
+    for (int a = 0; a < NB * KD / 256; ++a) {
+        int i = rr + RS * a;
         if (i < w) U[i][c] = val[a];
     }
     __syncthreads();
     // x'[i] = sum_{t >= i} Linv[t][i] u[t];  x[g0 + piv[i]] = x'[i]
-    for (int q = tid; q < w * KC; q += 256) {
-        int i = q / KC, cc = q % KC;
+    for (int q = tid; q < w * KD; q += 256) {
+        int i = q / KD, cc = q % KD;
         if (cc >= kc) continue;
         T acc = 0;
         for (int t = i; t < w; ++t) acc += Lm[t][i] * U[t][cc];
