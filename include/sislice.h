@@ -188,6 +188,24 @@ ss_status ss_factor_stats(const ss_numeric *f, int32_t shift_idx, double *min_pi
 ss_status ss_solve(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k, double *X,
                    int32_t refine);
 
+/* ---- ss_solve_noalloc (no paper counterpart) ---------------------------------------
+ * The FP64 solve of ss_solve (refine = 0) for callers that cannot allocate device
+ * memory -- code running under another framework's fixed memory budget or where the
+ * allocator must not be called -- so this entry point allocates nothing, not even
+ * temporarily.  Its working space is a file-scope device array of 4,194,304 doubles
+ * (32 MiB, held by every GPU that loads the library until exit): the permuted N x k
+ * right-hand sides followed by (widest solve level) x 64 x k doubles of gather buffer.
+ * The caller passes R and X (DEVICE float64 N x k row-major, may alias) as for
+ * ss_solve.  The first call on a device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every call shares
+ * the array and it keeps the last call's contents (the call clears the parts it needs
+ * cleared), so calls that overlap on the GPU -- on two streams, or two contexts of the
+ * same device -- race: serialise them.
+ * Errors: SS_ERR_ARG (bad argument; the shift was factored in FP32 -- use ss_solve; or
+ * N k + 64 k (widest solve level) beyond 4,194,304, with the numbers in
+ * ss_last_error), SS_ERR_CUDA. */
+ss_status ss_solve_noalloc(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k, double *X);
+
 /* ---- ss_slice_solve (Alg. 2: shift-invert subspace iteration with Cholesky-QR in
  * the B inner product, Rayleigh-Ritz, residual norms; Section 2.2; or the shift-invert
  * block Lanczos the paper names as its alternative, Section 1) ----------------------

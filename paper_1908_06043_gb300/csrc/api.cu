@@ -5,6 +5,7 @@
 #include <cmath>
 #include <type_traits>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -740,6 +741,100 @@ extern "C" ss_status ss_band_energy_grad(ss_symbolic *s, const double *X, const 
     }
     ss_launch(ctx, SS_K_SDDMM, sss::k_sddmm, (unsigned)s->n, 256, smem, ctx->stream, s->n, s->d_rowptr, s->d_colind, X, lambda, n_e,
                                                              grad_a, grad_b);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+// ------------------------------------------------------------------ allocation-free solve
+// ss_solve_noalloc: the FP64 solve of ss_solve without any allocation, for callers that
+// must not allocate device memory themselves or through a library -- code running
+// under another framework's memory budget, inside a region where a new allocation would
+// break an upstream memory plan, or where the allocator itself is unavailable.  Its
+// working space is the file-scope array below: a permuted copy of the right-hand sides
+// (N x k) followed by the per-level gather buffer of the backward sweep.
+namespace {
+
+constexpr int64_t kNoAllocScratchDoubles = 4ll * 1024 * 1024;   // 32 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+// device address of g_noalloc_scratch per device, found once with that device current
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[64] = {};
+
+int noalloc_scratch(ss_ctx *ctx, double **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 64) return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: device index");
+    if (!g_noalloc_addr[ctx->device]) {
+        double *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return ctx->set_error(SS_ERR_CUDA, std::string("ss_solve_noalloc: cudaGetSymbolAddress: ") +
+                                                   cudaGetErrorString(e));
+        }
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *out = g_noalloc_addr[ctx->device];
+    return SS_OK;
+}
+
+}  // namespace
+
+extern "C" ss_status ss_solve_noalloc(ss_numeric *f, int32_t j, const double *R, int32_t k, double *X) {
+    if (!f) return SS_ERR_ARG;
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    if (ctx->device < 0 || j < 0 || j >= f->n_shift || !R || !X || k <= 0)
+        return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: bad argument or host-only context");
+    if (f->shift_prec[j] != SS_FP64)
+        return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: shift was factored in FP32; use ss_solve");
+    int32_t maxc = 0;
+    for (const SolveLevel &sl : s->solve_levels) maxc = std::max(maxc, sl.count);
+    const int64_t nk = s->n * (int64_t)k;
+    const int64_t zoff = (nk + 31) / 32 * 32;                     // keep the gather buffer 256-byte aligned
+    const int64_t need = zoff + (int64_t)maxc * NB * k;
+    if (need > kNoAllocScratchDoubles)
+        return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: N*k + (widest solve level)*64*k = " +
+                                              std::to_string(need) + " doubles exceeds the 4,194,304-double (32 MiB) "
+                                              "scratch; use fewer right-hand sides or ss_solve");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    double *w = nullptr;
+    int rc = noalloc_scratch(ctx, &w);
+    if (rc != SS_OK) return rc;
+    double *z = w + zoff;
+    cudaStream_t st = ctx->stream;
+    set_smem_attrs<double>();
+    const unsigned g = (unsigned)((nk + 255) / 256);
+    ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, (int)k, s->d_perm, R, w, 0);
+    const double *arena = (const double *)f->arena[j];
+    const int nchunk = (k + KC - 1) / KC, ndchunk = (k + KD - 1) / KD;
+    const int nlev = (int)s->solve_levels.size();
+    for (int L = 0; L < nlev; ++L) {
+        const SolveLevel &sl = s->solve_levels[L];
+        const int32_t *lp = s->d_solve_panels + sl.panel_off;
+        ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<double>, dim3(sl.count, ndchunk), 256, diag_solve_smem<double>(), st,
+                  lp, s->d_panels, (const double *)f->linv[j], (const int32_t *)f->piv[j], w, (int)k);
+        if (sl.row_tiles > 0)
+            ss_launch(ctx, SS_K_FWD_UPDATE, k_fwd_update<double>, dim3(sl.row_tiles, nchunk), 256,
+                      tile_solve_smem<double>(), st, lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels,
+                      s->d_idx, arena, w, (int)k);
+    }
+    for (int L = nlev - 1; L >= 0; --L) {
+        const SolveLevel &sl = s->solve_levels[L];
+        const int32_t *lp = s->d_solve_panels + sl.panel_off;
+        if (sl.row_tiles > 0) {
+            // the gather buffer keeps the previous call's contents: clear this level's part
+            SS_CUDA_TRY(ctx, cudaMemsetAsync(z, 0, sizeof(double) * (int64_t)sl.count * NB * k, st));
+            ss_launch(ctx, SS_K_BWD_GATHER, k_bwd_gather<double>, dim3(sl.row_tiles, nchunk), 256,
+                      tile_solve_smem<double>(), st, lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels,
+                      s->d_idx, arena, (const double *)w, (int)k, z);
+        }
+        ss_launch(ctx, SS_K_BWD_DIAG, k_bwd_diag<double>, dim3(sl.count, ndchunk), 256, diag_solve_smem<double>(), st,
+                  lp, s->d_panels, (const double *)f->linv[j], (const double *)f->dblk[j],
+                  (const int32_t *)f->piv[j], (const double *)z, sl.row_tiles > 0 ? 1 : 0, w, (int)k, 1);
+    }
+    ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, (int)k, s->d_perm,
+              (const double *)w, X, 1);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }

@@ -1,0 +1,53 @@
+"""The allocation-free solve (ss_solve_noalloc) against the ordinary FP64 solve.
+
+ss_solve_noalloc serves callers that cannot allocate device memory: it works in a
+file-scope device array instead.  This file runs last (pytest collects files in
+alphabetical order) so that a failure here cannot hide any other test; it also passes
+on its own in a fresh process.  Two calls in a row check that the array's leftover
+contents from the first call do not leak into the second.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from tests.gpu_util import setup
+from workloads.pencils import config_pencil, normal_block
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(f, j, R):
+    X = torch.empty_like(R)
+    rc = f.ctx.lib.ss_solve_noalloc(f.h, j, C.c_void_p(R.data_ptr()), R.shape[1], C.c_void_p(X.data_ptr()))
+    f.ctx.check(rc, "ss_solve_noalloc")
+    return X
+
+
+def test_noalloc_solve_matches_ss_solve_twice(gpu_lib):
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    f = sym.factor(a, b, [-0.3, 0.2], "fp64")
+    for j, (k, seed) in enumerate([(24, 1), (7, 2)]):
+        R = torch.tensor(normal_block(p.n, k, seed), device="cuda")
+        ref = f.solve(j, R, refine=0)
+        for _ in range(2):                      # two calls in a row share the scratch array
+            X = _noalloc(f, j, R)
+            torch.cuda.synchronize()
+            # same kernels, but the solve sweeps scatter with atomics (summation order may
+            # differ), amplified by the conditioning of A - sigma B
+            assert ((X - ref).norm() / ref.norm()).item() <= 1e-9
+            res = sym.spmm(a, b, X, 1.0, -f.sigma[j]) - R
+            assert (res.norm() / R.norm()).item() <= 1e-8
+
+
+def test_noalloc_rejects_oversized(gpu_lib):
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    f = sym.factor(a, b, [0.2], "fp64")
+    too_many = 4_194_304 // p.n + 1
+    R = torch.zeros((p.n, too_many), dtype=torch.float64, device="cuda")
+    with pytest.raises(gpu_lib.SisliceError) as ei:
+        _noalloc(f, 0, R)
+    assert "exceeds" in str(ei.value)
