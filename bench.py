@@ -4,7 +4,7 @@
 A step is one pass of the whole hot path over one pencil: Lanczos DOS estimate
 (Section 3.1), shift placement by CDOS roots, one batched LDL^T of A - sigma_j B for
 every shift plus the two region bounds, inertia counts, shift-invert subspace
-iterations on every probe until every slice validates (Section 2.3), and validation.
+iterations on every probe until every slice validates (Section 2.2), and validation.
 value = shifts (slice solves) completed per second; every validated eigenpair must
 meet the normalised residual 1e-10.
 

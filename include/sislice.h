@@ -117,7 +117,7 @@ ss_status ss_create(ss_ctx **ctx, int32_t device, void *cuda_stream);
 ss_status ss_destroy(ss_ctx *ctx);
 const char *ss_last_error(const ss_ctx *ctx);
 
-/* ---- ss_analyze (Section 2.2: the sparse LDL^T of A - sigma B is the major cost;
+/* ---- ss_analyze (Section 2.1: the sparse LDL^T of A - sigma B is the major cost;
  * Section 5: the paper's solver orders with nested dissection) --------------------
  * Host CSR pattern in, symbolic analysis out: nested-dissection ordering, supernodes
  * (the dissection blocks), the assembly tree and its level schedule, front index
@@ -159,7 +159,7 @@ ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const double *b_vals
                     ss_numeric **out);
 ss_status ss_factor_destroy(ss_numeric *f);
 
-/* ---- ss_inertia (Section 2.3: Sylvester's law of inertia) ------------------------
+/* ---- ss_inertia (Section 2.2: Sylvester's law of inertia) ------------------------
  * Inertia of A - sigma_j B from the block-diagonal D: n_neg = #negative 1x1 pivots
  * + one per 2x2 block with det < 0 (+ two per 2x2 block with det > 0 and negative
  * trace).  n_neg equals the number of eigenvalues of (A, B) below sigma_j.  Host
@@ -207,7 +207,7 @@ ss_status ss_solve(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k,
 ss_status ss_solve_noalloc(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k, double *X);
 
 /* ---- ss_slice_solve (Alg. 2: shift-invert subspace iteration with Cholesky-QR in
- * the B inner product, Rayleigh-Ritz, residual norms; Section 2.2; or the shift-invert
+ * the B inner product, Rayleigh-Ritz, residual norms; Section 2.1; or the shift-invert
  * block Lanczos the paper names as its alternative, Section 1) ----------------------
  * Builds the spectral probe of shift sigma_j.  V0 is the DEVICE N x k start block
  * (seeded N(0,1) or a previous probe's X; required).  SS_SUBSPACE iterates on k
@@ -219,7 +219,7 @@ ss_status ss_solve_noalloc(ss_numeric *f, int32_t shift_idx, const double *R, in
  * opts->n_expect Ritz values in (lo, hi] are converged (n_expect > 0, e.g. an exact
  * count from inertia), or every Ritz value in (lo, hi] is (n_expect = 0), or max_iter.
  * Unconverged Ritz values inside the window can be spurious mixtures of eigenvectors
- * at equal distance on both sides of sigma; validation (Section 2.3) discards them.
+ * at equal distance on both sides of sigma; validation (Section 2.2) discards them.
  * Outputs (k_out entries; k_out = k for SS_SUBSPACE): lambda (HOST float64, ascending
  * Ritz values), X (DEVICE N x k_out, B-orthonormal Ritz vectors in the same order),
  * resid (HOST float64), n_found (HOST: #converged Ritz values in (lo, hi]), stats
@@ -230,7 +230,7 @@ ss_status ss_slice_solve(ss_numeric *f, int32_t shift_idx, double lo, double hi,
                          double *lambda, double *X, double *resid, int32_t *n_found,
                          ss_probe_stats *stats);
 
-/* ---- ss_dos_estimate (Section 3.1, Eqs. 13-14: Lanczos DOS of G^-1 A G^-T) --------
+/* ---- ss_dos_estimate (Section 3.1, Eqs. 4-5: Lanczos DOS of G^-1 A G^-T) --------
  * Factors B = G G^T (the LDL^T at sigma = 0 of the pencil (B, 0), G = P L D^1/2), then
  * runs `steps` Lanczos steps on G^-1 A G^-T with full re-orthogonalisation for each of
  * the n_vec DEVICE start vectors y0 in start (N x n_vec row-major, seeded N(0,1)).  It

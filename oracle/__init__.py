@@ -12,10 +12,10 @@ Modules
 dense      ctypes binding of ``oracle.c``: dense generalised eigensolver, dense
            Bunch-Kaufman inertia, band LDL^T inertia, CSR products, tridiagonal eig.
 spectral   slice membership, inertia counts, residuals, B-orthonormality (Eq. 1,
-           Section 2.3 validation counts, residual definition after Alg. 2).
-dos        Lanczos DOS estimate and closed-form CDOS / shift formulas (Eqs. 13-17).
+           Section 2.2 validation counts, residual definition after Alg. 2).
+dos        Lanczos DOS estimate and closed-form CDOS / shift formulas (Eqs. 4-8).
 partition  CDOS-root intervals, expectation shifts, exactly-n_s safeguards, slice
-           validation (Section 2.3) and k-means++ / Lloyd shift migration (Sec. 3.2).
+           validation (Section 2.2) and k-means++ / Lloyd shift migration (Sec. 3.2).
 grad       band-energy gradient sampled on the pattern (Hellmann-Feynman).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against

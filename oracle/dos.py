@@ -5,16 +5,16 @@ Test infrastructure only.  Follows the paper's steps in order:
 1. B-orthonormal Lanczos on B^-1 A (the second form of Section 3.1, the one whose
    N(0,1) start vector the paper describes), start vector passed in, k steps, full
    re-orthogonalisation (the paper does not say; we take full re-orthogonalisation).
-2. Ritz pairs (theta_j, g_j) of the Lanczos tridiagonal, zeta_j = e_1^T g_j (Eq. 13).
+2. Ritz pairs (theta_j, g_j) of the Lanczos tridiagonal, zeta_j = e_1^T g_j (Eq. 4).
 3. Gaussian widths nu_j: d_j = max of the neighbour gaps (one gap at the ends), floored
    at 1e-3 (theta_max - theta_min)/k, nu_j = d_j / 3 (our reading of "nearly vanishes").
 4. phi(omega) = N/sqrt(2 pi) sum zeta_j^2/nu_j exp(-kappa_j^2),
-   kappa_j = (omega - theta_j)/(nu_j sqrt 2) (Eq. 13);
-   Phi(omega) = N/2 sum zeta_j^2 [erf(kappa_j) + 1] (Eq. 14);
+   kappa_j = (omega - theta_j)/(nu_j sqrt 2) (Eq. 4);
+   Phi(omega) = N/2 sum zeta_j^2 [erf(kappa_j) + 1] (Eq. 5);
    several start vectors are averaged.
 5. psi_i(omega) = theta_i/2 erf(kappa_i) - nu_i/sqrt(2 pi) exp(-kappa_i^2) and the
    expectation shift sigma = N/(Phi(u) - Phi(l)) sum zeta_i^2 (psi_i(u) - psi_i(l))
-   (Eqs. 16-17).
+   (Eqs. 7-8).
 """
 from __future__ import annotations
 
@@ -33,7 +33,7 @@ def lanczos_ritz(A: np.ndarray, B: np.ndarray, x0: np.ndarray, k: int):
     x_1 = x0 / ||x0||_B; w = B^-1 A x_j - alpha_j x_j - beta_{j-1} x_{j-1} with
     alpha_j = x_j^T A x_j; full re-orthogonalisation in the B inner product; beta_j =
     ||w||_B.  Returns (theta, zeta2, alpha, beta); zeta_j = e_1^T g_j for the Ritz
-    vectors g_j of the tridiagonal (Eq. 13).  This is Lanczos on L^-1 A L^-T started
+    vectors g_j of the tridiagonal (Eq. 4).  This is Lanczos on L^-1 A L^-T started
     from L^T x0 for any B = L L^T."""
     n = A.shape[0]
     Lb = np.linalg.cholesky(B)
@@ -91,7 +91,7 @@ def gaussian_widths(theta: np.ndarray) -> np.ndarray:
 
 
 def dos_phi(omega, n, runs):
-    """phi(omega) averaged over runs = [(theta, zeta2, nu), ...] (Eq. 13)."""
+    """phi(omega) averaged over runs = [(theta, zeta2, nu), ...] (Eq. 4)."""
     omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
     tot = np.zeros_like(omega)
     for theta, zeta2, nu in runs:
@@ -101,7 +101,7 @@ def dos_phi(omega, n, runs):
 
 
 def cdos_Phi(omega, n, runs):
-    """Phi(omega) averaged over runs (Eq. 14)."""
+    """Phi(omega) averaged over runs (Eq. 5)."""
     omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
     tot = np.zeros_like(omega)
     for theta, zeta2, nu in runs:
@@ -111,14 +111,14 @@ def cdos_Phi(omega, n, runs):
 
 
 def psi(omega, theta, nu):
-    """psi_i(omega) for every Ritz value (Eq. 17); returns shape (len(omega), k)."""
+    """psi_i(omega) for every Ritz value (Eq. 8); returns shape (len(omega), k)."""
     omega = np.atleast_1d(np.asarray(omega, dtype=np.float64))
     kap = (omega[:, None] - theta[None, :]) / (nu[None, :] * math.sqrt(2.0))
     return theta[None, :] / 2.0 * erf(kap) - nu[None, :] / math.sqrt(2.0 * math.pi) * np.exp(-kap * kap)
 
 
 def expectation_shift(l, u, n, runs):
-    """sigma = (integral_l^u omega phi) / (Phi(u) - Phi(l)) (Eq. 16), runs averaged."""
+    """sigma = (integral_l^u omega phi) / (Phi(u) - Phi(l)) (Eq. 7), runs averaged."""
     num = 0.0
     for theta, zeta2, nu in runs:
         ps = psi(np.array([l, u]), theta, nu)

@@ -11,12 +11,12 @@
  *                   Householder tridiagonalisation, implicit-shift QL, back-transform
  *                   X = L^-T Y, so that X^T B X = I.
  *  or_ldlt_bk       dense Bunch-Kaufman LDL^T of a symmetric matrix with 1x1 / 2x2
- *                   pivots; returns the Sylvester inertia of D (Section 2.3, inertia
+ *                   pivots; returns the Sylvester inertia of D (Section 2.2, inertia
  *                   count of the shifted matrix A - sigma B).
  *  or_band_ldlt     unpivoted LDL^T of a banded symmetric matrix in natural order;
  *                   inertia by Sylvester's law when every pivot is well away from 0.
  *  or_csr_mm        Y = M X for a CSR matrix and a row-major block X (residuals).
- *  or_tridiag_eig   eigenpairs of a symmetric tridiagonal matrix (Lanczos DOS, Eq. 14).
+ *  or_tridiag_eig   eigenpairs of a symmetric tridiagonal matrix (Lanczos DOS, Eq. 5).
  *
  * Return codes: 0 ok, 1 not SPD (Cholesky hit a non-positive pivot), 2 QL did not
  * converge, 3 a band pivot fell below the reliability threshold.

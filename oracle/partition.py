@@ -1,7 +1,7 @@
 """Slice partition, validation and shift migration (Sections 2.3, 3.1, 3.2).
 
 Test infrastructure only.  Readings where the paper is silent or garbled:
-* CDOS roots (Eq. 15) are read as Phi(omega) = Phi(a) + K j, j = 0..n_s,
+* CDOS roots (Eq. 6) are read as Phi(omega) = Phi(a) + K j, j = 0..n_s,
   K = (Phi(b) - Phi(a)) / n_s, found by bisection to 1e-12 relative width.
 * The interval midpoint is (l + u)/2.
 * End slices are [lambda_min, sigma_1) and (sigma_ns, lambda_max].
@@ -33,7 +33,7 @@ def bisect_root(f, lo, hi, target, rel=1e-12, maxit=200):
 
 
 def cdos_root_intervals(a, b, n_s, n, runs):
-    """Intervals (l_j, u_j) with about equal CDOS mass (Eq. 15)."""
+    """Intervals (l_j, u_j) with about equal CDOS mass (Eq. 6)."""
     Pa = float(cdos_Phi(a, n, runs)[0])
     Pb = float(cdos_Phi(b, n, runs)[0])
     K = (Pb - Pa) / n_s
@@ -46,7 +46,7 @@ def cdos_root_intervals(a, b, n_s, n, runs):
 
 
 def candidates(shifts, lam_min, lam_max, probes):
-    """Validation candidates per slice (Section 2.3).
+    """Validation candidates per slice (Section 2.2).
 
     probes[j] = (theta[k], resid[k]) of the probe at shifts[j].  Returns a list over the
     n_s + 1 slices of lists of (probe j, ritz index i)."""
@@ -73,7 +73,7 @@ def candidates(shifts, lam_min, lam_max, probes):
 
 
 def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max):
-    """Apply the three validation cases per slice (Section 2.3).
+    """Apply the three validation cases per slice (Section 2.2).
 
     nneg_shift[j] = #negative pivots of LDL^T(A - shifts[j] B); nneg_min / nneg_max
     are the counts at the region bounds.  Returns (validated list of (probe, ritz),

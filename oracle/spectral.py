@@ -1,9 +1,9 @@
 """Exact spectral quantities from the dense oracle (test infrastructure only).
 
-* inertia / eigenvalue counts: Sylvester's law, Section 2.3 -- the number of negative
+* inertia / eigenvalue counts: Sylvester's law, Section 2.2 -- the number of negative
   pivots of LDL^T(A - sigma B) equals #{lambda_i < sigma}.
 * slice membership: the slice (lo, hi] holds the eigenpairs with lo < lambda <= hi,
-  and its count is nu(hi) - nu(lo) (Section 2.3 validation counts).
+  and its count is nu(hi) - nu(lo) (Section 2.2 validation counts).
 * residuals: R_j = A X_j - B X_j Lambda_j, column 2-norms (after Alg. 2), normalised by
   ||A||_1 ||x||_2.
 """

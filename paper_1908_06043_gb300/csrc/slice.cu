@@ -332,7 +332,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // a Ritz value in the window counts once its residual meets tol; unconverged
         // ones in the window may be spurious mixtures from the edge of the basis
         // (eigenvalues at equal distance on both sides of sigma), which validation by
-        // inertia counts removes (Section 2.3), so with n_expect given the probe stops
+        // inertia counts removes (Section 2.2), so with n_expect given the probe stops
         // as soon as n_expect of them have converged
         nf = 0;
         maxr = 0.0;

@@ -1,7 +1,7 @@
 // Symbolic analysis of the sparse LDL^T of A - sigma B (done once per pattern).
 //
 // The paper factors A - sigma B with a sparse direct solver whose ordering is nested
-// dissection (Section 2.2 names the sparse LDL^T as the major cost; Section 5 runs it
+// dissection (Section 2.1 names the sparse LDL^T as the major cost; Section 5 runs it
 // with a nested-dissection ordering).  This file computes, from the CSR pattern only:
 //   1. a nested-dissection ordering from BFS level-structure vertex separators;
 //   2. supernodes = the dissection blocks (leaves and separators), each a dense

@@ -3,15 +3,15 @@
 The device work -- factorisations, inertia, in-slice iterations, DOS sweeps -- runs in
 the library; this module sequences it and holds the O(n_s k) scalar logic:
 
-* ``DosModel``: the Lanczos DOS / CDOS closed forms (Eqs. 13-14) with Gaussian widths
+* ``DosModel``: the Lanczos DOS / CDOS closed forms (Eqs. 4-5) with Gaussian widths
   nu_j = d_j / 3, d_j the larger neighbour gap of the Ritz values (floored), averaged
-  over start vectors; the interval expectation shift (Eqs. 16-17).
-* ``cdos_partition``: n_s intervals of equal CDOS mass (Eq. 15, read as
+  over start vectors; the interval expectation shift (Eqs. 7-8).
+* ``cdos_partition``: n_s intervals of equal CDOS mass (Eq. 6, read as
   Phi(omega) = Phi(a) + K j), one shift per interval at its DOS expectation.
 * ``region_for_lowest``: [lambda_min, lambda_max] holding exactly the n_e lowest
   eigenvalues, from the DOS estimate and exact inertia counts.
 * ``validate``: candidates split at the slice midpoints, exact counts from inertia,
-  the three cases of Section 2.3.
+  the three cases of Section 2.2.
 * ``kmeans_shifts``: k-means++ seeding and Lloyd iterations on validated Ritz values
   (Section 3.2); the uniforms are passed in.
 * ``SliceSolver.run``: factor every shift (one batched call), inertia, probes, rounds of
@@ -32,7 +32,7 @@ from . import api
 
 # ----------------------------------------------------------------- DOS model
 class DosModel:
-    """phi / Phi of Eqs. 13-14 averaged over Lanczos runs [(theta, zeta2), ...]."""
+    """phi / Phi of Eqs. 4-5 averaged over Lanczos runs [(theta, zeta2), ...]."""
 
     def __init__(self, n: int, runs):
         self.n = n
@@ -111,7 +111,7 @@ def cdos_partition(model: DosModel, a: float, b: float, n_s: int):
 
 # ----------------------------------------------------------------- validation
 def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max, tol, taus=None):
-    """Section 2.3.  probes[j] = (theta, resid); taus[s] (optional) is the point that
+    """Section 2.2.  probes[j] = (theta, resid); taus[s] (optional) is the point that
     splits slice s = (shifts[s-1], shifts[s]) between its two probes (default: the
     midpoint).  Returns (selected [(probe, ritz)], per-slice records (n_exact, n_cand,
     n_conv, status))."""
@@ -361,7 +361,7 @@ class SliceSolver:
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,
         lambda_max at Phi = (1 + margin) n_e + 1, and n_s intervals between them, by the
-        CDOS roots of Eq. 15 with expectation shifts (mode "cdos") or by ball_partition
+        CDOS roots of Eq. 6 with expectation shifts (mode "cdos") or by ball_partition
         (mode "ball").  Returns (lambda_min, lambda_max, shifts, splits, basis sizes):
         splits[s] divides slice s between probes s-1 and s (None: the midpoints)."""
         lo_t, hi_t = model.theta_range()

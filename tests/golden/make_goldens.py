@@ -5,7 +5,7 @@ Outputs (text, one value per line after a '#' header):
 * gauss16_eigs.txt     lowest 2,048 eigenvalues of (A, B) from the dense oracle
                        (Cholesky-reduced tridiagonal QL), Eq. 1.
 * gauss16_inertia.txt  sigma, n_neg, n_zero, n_pos of A - sigma B from the band
-                       LDL^T oracle (Sylvester's law, Section 2.3), for a few shifts.
+                       LDL^T oracle (Sylvester's law, Section 2.2), for a few shifts.
 
 Run: python tests/golden/make_goldens.py   (about 10-20 minutes on 8 cores)
 """

@@ -1,4 +1,4 @@
-"""GPU parity: multifrontal LDL^T inertia (Sylvester, Section 2.3) and solves against
+"""GPU parity: multifrontal LDL^T inertia (Sylvester, Section 2.2) and solves against
 the CPU oracle.  Inertia is compared bit-exactly; solves to 1e-10 relative."""
 import numpy as np
 import pytest

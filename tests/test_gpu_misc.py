@@ -55,7 +55,7 @@ def test_band_energy_grad_matches_oracle(gpu_lib):
 
 def test_dos_estimate_is_unbiased(gpu_lib):
     # Lanczos on G^-1 A G^-T from i.i.d. N(0,1) vectors: averaged over start vectors the
-    # CDOS estimate approaches the exact eigenvalue count (Eq. 14), whatever square root
+    # CDOS estimate approaches the exact eigenvalue count (Eq. 5), whatever square root
     # G of B the factorisation provides
     from paper_1908_06043_gb300.driver import DosModel
     p = config_pencil(1)

@@ -1,5 +1,5 @@
 """Pins for the dense oracle: closed forms, an outside library (LAPACK via scipy),
-brute force on tiny inputs, and Sylvester's law (Section 2.3)."""
+brute force on tiny inputs, and Sylvester's law (Section 2.2)."""
 import numpy as np
 import pytest
 import scipy.linalg as sla

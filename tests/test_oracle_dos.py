@@ -1,4 +1,4 @@
-"""Pins for the DOS / CDOS oracle (Section 3.1, Eqs. 13-17)."""
+"""Pins for the DOS / CDOS oracle (Section 3.1, Eqs. 4-8)."""
 import math
 
 import numpy as np

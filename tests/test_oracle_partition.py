@@ -1,4 +1,4 @@
-"""Pins for validation (Section 2.3) and k-means shift migration (Section 3.2)."""
+"""Pins for validation (Section 2.2) and k-means shift migration (Section 3.2)."""
 import numpy as np
 
 from oracle import partition
