@@ -215,7 +215,8 @@ def main():
                   f"probes {res.timings['solve_s']:.3f}s total {time.perf_counter() - t0:.3f}s rounds {res.rounds} "
                   f"found {len(res.eigenvalues)} (nu(max)={res.timings['n_below_max']}) "
                   f"maxres {res.residuals.max() if len(res.residuals) else -1:.2e} "
-                  f"slices {[i[:3] for i in res.slices]}", file=sys.stderr, flush=True)
+                  f"slices {[i[:3] for i in res.slices]} "
+                  f"quality {[(q[0], float(f'{q[1]:.2e}')) for q in res.timings['quality']]}", file=sys.stderr, flush=True)
         return res
 
     def check(res):
@@ -336,14 +337,15 @@ def main():
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": wl["name"], "precision": args.precision,
-                      "probe_driver": "shift-invert subspace iteration (Alg. 2) with Rayleigh-Ritz every iteration",
+                      "probe_driver": "shift-invert subspace iteration (Alg. 2), Rayleigh-Ritz every 2nd iteration in the first round, once per later round",
                       "shift_placement": "DOS ball partition (radius 2h ball <= basis)",
                       "lanczos_steps": steps_dos, "lanczos_vectors": n_vec, "parallelism": f"replicas x{ws}",
                       "l2": "inputs larger than L2 (factor arena > 129 MB)",
                       "eigenpairs_validated": int(len(r0.eigenvalues)), "all_validated": all_ok,
                       "max_resid": float(r0.residuals.max()) if len(r0.residuals) else None,
                       "factor_tflops": factor_tflops, "factor_s_per_step": factor_s,
-                      "rounds": r0.rounds, "probe_iterations": r0.timings["iterations"]},
+                      "rounds": r0.rounds, "probe_iterations": r0.timings["iterations"],
+                      "shift_solve_precision": [q[0] for q in r0.timings["quality"]]},
            "fp64_side": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk,
            "profile_ms": {c: round(1e3 * v[1], 3) for c, v in prof.items() if v[0]},

@@ -44,6 +44,7 @@ enum {
 };
 
 enum { SS_FP64 = 0, SS_MIXED = 1 };      /* factor precision                     */
+enum { SS_FP64_SOLVE32 = 2 };              /* reported only: FP64 factor, FP32 solves */
 enum { SS_SUBSPACE = 0, SS_BLOCK_LANCZOS = 1 };  /* in-slice driver             */
 
 typedef struct ss_ctx ss_ctx;
@@ -117,6 +118,16 @@ ss_status ss_create(ss_ctx **ctx, int32_t device, void *cuda_stream);
 ss_status ss_destroy(ss_ctx *ctx);
 const char *ss_last_error(const ss_ctx *ctx);
 
+/* How the level-scheduled triangular sweeps of every solve (ss_solve, the probes of
+ * ss_slice_solve, the DOS Lanczos) are launched -- an implementation choice with no
+ * paper counterpart.  SS_SOLVE_SWEEP_KERNEL (default): one cooperative launch per solve
+ * that walks all levels with a bounded grid barrier between steps (a barrier that waits
+ * about 1 s makes the solve return SS_ERR_TIMEOUT); SS_SOLVE_PER_STEP: one launch per
+ * level and step.  Both compute the same sums; the atomics make the rounding order
+ * differ.  ss_solve_noalloc always launches per step.  Errors: SS_ERR_ARG. */
+enum { SS_SOLVE_SWEEP_KERNEL = 0, SS_SOLVE_PER_STEP = 1 };
+ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
+
 /* ---- ss_analyze (Section 2.1: the sparse LDL^T of A - sigma B is the major cost;
  * Section 5: the paper's solver orders with nested dissection) --------------------
  * Host CSR pattern in, symbolic analysis out: nested-dissection ordering, supernodes
@@ -150,7 +161,10 @@ ss_status ss_symbolic_validate(const ss_symbolic *sym);
  * and Schur updates in FP32 with FP64 diagonal blocks, and solves with FP64 iterative
  * refinement.  SS_MIXED checks every shift's FP32 factor: one FP32 solve of a fixed
  * probe vector must reduce the residual to rho <= 1e-2 of the right-hand side, else that
- * shift is refactored in FP64 (ss_factor_quality reports which).
+ * shift is refactored in FP64.  The FP64 factor of such a shift is then rounded once to
+ * FP32; if one FP32 solve from the rounded copy contracts by rho <= 0.25, the shift's
+ * solves run in FP32 inside FP64 refinement, else in FP64 (ss_factor_quality reports
+ * which).
  * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_SINGULAR (a pivot fell below
  * 64 u ||A - sigma B||_1 for some shift; the factor is still returned and
  * ss_inertia reports which shift). */
@@ -168,8 +182,10 @@ ss_status ss_factor_destroy(ss_numeric *f);
 ss_status ss_inertia(const ss_numeric *f, int32_t shift_idx, int64_t *n_neg, int64_t *n_zero,
                      int64_t *n_pos, int32_t *tiny_pivot);
 
-/* Precision shift j was finally factored in (SS_FP64 after a mixed-precision
- * fallback) and, for an FP32 factor, its measured contraction factor rho.
+/* Precision shift j was finally factored and solved in: SS_MIXED (FP32 factor),
+ * SS_FP64 (FP64 factor and solves) or SS_FP64_SOLVE32 (FP64 factor, FP32 solves from its
+ * rounded copy), and the measured contraction factor rho of one FP32 solve (of the FP32
+ * factor, or of the rounded copy when one is kept; 0 for precision = SS_FP64).
  * Host outputs, each may be NULL.  Errors: SS_ERR_ARG. */
 ss_status ss_factor_quality(const ss_numeric *f, int32_t shift_idx, int32_t *precision_used,
                             double *rho);
@@ -285,7 +301,9 @@ enum {
     SS_K_ASSEMBLE = 0, SS_K_EXTEND_ADD, SS_K_DIAG_BK, SS_K_PANEL, SS_K_SCHUR, SS_K_FWD_DIAG,
     SS_K_FWD_UPDATE, SS_K_BWD_GATHER, SS_K_BWD_DIAG, SS_K_PERMUTE, SS_K_SPMM, SS_K_GRAM,
     SS_K_GEMM, SS_K_SMALL_DENSE, SS_K_JACOBI, SS_K_LANCZOS, SS_K_SDDMM, SS_K_MISC,
-    SS_K_PANEL_F32, SS_K_SCHUR_F32, SS_K_FWD_UPDATE_F32, SS_K_BWD_GATHER_F32, SS_K_COUNT
+    SS_K_PANEL_F32, SS_K_SCHUR_F32, SS_K_FWD_UPDATE_F32, SS_K_BWD_GATHER_F32,
+    SS_K_SOLVE, SS_K_SOLVE_F32,   /* whole-solve sweep kernel (SS_SOLVE_SWEEP_KERNEL) */
+    SS_K_COUNT
 };
 int64_t ss_launch_count(void);
 ss_status ss_profile(ss_ctx *ctx, uint32_t mask);

@@ -13,7 +13,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libsislice.so")
 
 SS_OK, SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_SINGULAR, SS_ERR_NOT_SPD, SS_ERR_NOCONV, \
     SS_ERR_TIMEOUT, SS_ERR_INTERNAL = range(9)
-SS_FP64, SS_MIXED = 0, 1
+SS_FP64, SS_MIXED, SS_FP64_SOLVE32 = 0, 1, 2
+SS_SOLVE_SWEEP_KERNEL, SS_SOLVE_PER_STEP = 0, 1
 SS_SUBSPACE, SS_BLOCK_LANCZOS = 0, 1
 STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_SINGULAR",
                 5: "SS_ERR_NOT_SPD", 6: "SS_ERR_NOCONV", 7: "SS_ERR_TIMEOUT", 8: "SS_ERR_INTERNAL"}
@@ -44,10 +45,10 @@ class ss_solve_opts(C.Structure):
 
 EXPORTS = ["ss_create", "ss_destroy", "ss_last_error", "ss_analyze", "ss_symbolic_info_get",
            "ss_symbolic_perm", "ss_symbolic_destroy", "ss_symbolic_validate", "ss_factor", "ss_factor_destroy", "ss_inertia", "ss_factor_stats", "ss_factor_quality",
-           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query"]
+           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode"]
 KERNEL_CLASSES = ["assemble", "extend_add", "diag_bk", "panel", "schur", "fwd_diag", "fwd_update", "bwd_gather",
                   "bwd_diag", "permute", "spmm", "gram", "gemm", "small_dense", "jacobi", "lanczos", "sddmm", "misc",
-                  "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32"]
+                  "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32", "solve", "solve_f32"]
 
 _lib = None
 
@@ -66,6 +67,7 @@ def load():
         "ss_create": ([PP, i32, P], i32),
         "ss_destroy": ([P], i32),
         "ss_last_error": ([P], C.c_char_p),
+        "ss_set_solve_mode": ([P, i32], i32),
         "ss_analyze": ([P, i64, P, P, C.POINTER(ss_options), PP], i32),
         "ss_symbolic_info_get": ([P, C.POINTER(ss_symbolic_info)], i32),
         "ss_symbolic_perm": ([P, P], i32),

@@ -71,6 +71,12 @@ class Context:
     def analyze(self, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0) -> "Symbolic":
         return analyze(self, rowptr, colind, nd_leaf)
 
+    def set_solve_mode(self, mode: str):
+        """"sweep": one cooperative launch per solve (default); "per_step": one launch per
+        solve level and step."""
+        m = {"sweep": L.SS_SOLVE_SWEEP_KERNEL, "per_step": L.SS_SOLVE_PER_STEP}[mode]
+        self.check(self.lib.ss_set_solve_mode(self.h, m), "ss_set_solve_mode")
+
     def launch_count(self) -> int:
         """Kernels launched by the library since it was loaded."""
         return int(self.lib.ss_launch_count())
@@ -206,10 +212,13 @@ class Factor:
         return mp.value, ml.value, n2.value
 
     def quality(self, j: int = 0):
-        """(precision the shift was factored in, FP32 contraction factor rho)."""
+        """(how shift j was factored and solved: "fp64", "mixed" (FP32 factor) or
+        "fp64+f32solve" (FP64 factor, FP32 solves from its rounded copy), contraction factor
+        rho of one FP32 solve)."""
         pr, rho = C.c_int32(), C.c_double()
         self.ctx.check(self.ctx.lib.ss_factor_quality(self.h, j, C.byref(pr), C.byref(rho)), "ss_factor_quality")
-        return ("fp64" if pr.value == L.SS_FP64 else "mixed"), rho.value
+        name = {L.SS_FP64: "fp64", L.SS_MIXED: "mixed", L.SS_FP64_SOLVE32: "fp64+f32solve"}[pr.value]
+        return name, rho.value
 
     def solve(self, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
         return solve(self, j, R, refine)

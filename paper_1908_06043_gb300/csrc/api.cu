@@ -103,6 +103,14 @@ extern "C" ss_status ss_destroy(ss_ctx *ctx) {
 
 extern "C" const char *ss_last_error(const ss_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+extern "C" ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode) {
+    if (!ctx) return SS_ERR_ARG;
+    if (mode != SS_SOLVE_SWEEP_KERNEL && mode != SS_SOLVE_PER_STEP)
+        return ctx->set_error(SS_ERR_ARG, "ss_set_solve_mode: unknown mode");
+    ctx->solve_mode = mode;
+    return SS_OK;
+}
+
 extern "C" ss_status ss_sync(ss_ctx *ctx) {
     if (!ctx) return SS_ERR_ARG;
     if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
@@ -143,6 +151,13 @@ int ss_symbolic_upload(ss_symbolic *s) {
     for (size_t p = 0; p < s->panels.size(); ++p)
         for (int i = 0; i < s->panels[p].w; ++i) col_panel[s->panels[p].g0 + i] = (int32_t)p;
     UP(col_panel, s->d_col_panel);
+    std::vector<SweepLevel> lev(s->solve_levels.size());
+    for (size_t L = 0; L < lev.size(); ++L)
+        lev[L] = SweepLevel{(int32_t)s->solve_levels[L].panel_off, s->solve_levels[L].count,
+                            s->solve_levels[L].row_tiles, 0};
+    SweepLevel *dl = nullptr;
+    UP(lev, dl);
+    s->d_sweep_lev = dl;
 #undef UP
     return SS_OK;
 }
@@ -150,13 +165,14 @@ int ss_symbolic_upload(ss_symbolic *s) {
 void ss_symbolic_free_device(ss_symbolic *s) {
     void *ptrs[] = {s->d_rowptr, s->d_colind, s->d_iperm, s->d_perm, s->d_idx, s->d_asm_e,
                     s->d_asm_dest, s->d_relmap, s->d_ext_tasks, s->d_panels, s->d_tasks,
-                    s->d_solve_panels, s->d_solve_tile_pre, s->d_col_panel};
+                    s->d_solve_panels, s->d_solve_tile_pre, s->d_col_panel, s->d_sweep_lev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->d_rowptr = nullptr; s->d_colind = nullptr; s->d_iperm = nullptr; s->d_perm = nullptr;
     s->d_idx = nullptr; s->d_asm_e = nullptr; s->d_asm_dest = nullptr; s->d_relmap = nullptr;
     s->d_ext_tasks = nullptr; s->d_panels = nullptr; s->d_tasks = nullptr;
     s->d_solve_panels = nullptr; s->d_solve_tile_pre = nullptr; s->d_col_panel = nullptr;
+    s->d_sweep_lev = nullptr;
 }
 
 // ------------------------------------------------------------------ norms
@@ -196,8 +212,9 @@ static void set_smem_attrs() {
     cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_smem<T>());
     cudaFuncSetAttribute(k_fwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_solve_smem<T>());
     cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_solve_smem<T>());
-    cudaFuncSetAttribute(k_fwd_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_solve_smem<T>());
-    cudaFuncSetAttribute(k_bwd_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_solve_smem<T>());
+    cudaFuncSetAttribute(k_fwd_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_kernel_smem<T>());
+    cudaFuncSetAttribute(k_bwd_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_kernel_smem<T>());
+    cudaFuncSetAttribute(k_solve_sweeps<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<T>());
 }
 
 template <typename T>
@@ -276,13 +293,23 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
     return SS_OK;
 }
 
+// largest contraction factor of one FP32 solve for which an FP64 factor's rounded copy
+// serves the solves
+constexpr double kRoundedRhoMax = 0.25;
+
+__global__ void k_round_f32(int64_t n, const double *__restrict__ x, float *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
 static void factor_free(ss_numeric *f) {
     for (void *p : f->arena) if (p) cudaFree(p);
+    for (float *p : f->arena_lo) if (p) cudaFree(p);
     for (double *p : f->linv) if (p) cudaFree(p);
     for (double *p : f->dblk) if (p) cudaFree(p);
     for (int32_t *p : f->piv) if (p) cudaFree(p);
     if (f->d_counts) cudaFree(f->d_counts);
-    f->arena.clear(); f->linv.clear(); f->dblk.clear(); f->piv.clear();
+    f->arena.clear(); f->arena_lo.clear(); f->linv.clear(); f->dblk.clear(); f->piv.clear();
     f->d_counts = nullptr;
 }
 
@@ -305,6 +332,7 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
     if ((rc = ss_norm1(sym, a_vals, &f->norm_a1)) != SS_OK) { delete f; return rc; }
     if ((rc = ss_norm1(sym, b_vals, &f->norm_b1)) != SS_OK) { delete f; return rc; }
     f->arena.assign(n_shift, nullptr);
+    f->arena_lo.assign(n_shift, nullptr);
     f->linv.assign(n_shift, nullptr);
     f->dblk.assign(n_shift, nullptr);
     f->piv.assign(n_shift, nullptr);
@@ -336,9 +364,10 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
             rc = solve_contraction(f, j, &f->rho[j]);
             if (rc == SS_OK && !(f->rho[j] <= 1e-2)) redo.push_back(j);
         }
+        // the FP32 arena of a refactored shift is kept for the FP32 rounding below
         for (int j : redo) {
             if (rc != SS_OK) break;
-            cudaFree(f->arena[j]);
+            f->arena_lo[j] = (float *)f->arena[j];
             f->arena[j] = nullptr;
             cudaError_t e2 = cudaMalloc(&f->arena[j], sizeof(double) * std::max<int64_t>(1, sym->arena));
             if (e2 != cudaSuccess) {
@@ -348,6 +377,26 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
             f->shift_prec[j] = SS_FP64;
         }
         if (rc == SS_OK) rc = factor_run<double>(f, redo);
+        // FP64 factor, FP32 solves: the FP64 fronts rounded once to FP32 avoid the error
+        // that FP32 Schur updates accumulate; the rounded copy is kept where one FP32
+        // solve from it contracts by rho <= kRoundedRhoMax, else solves stay FP64
+        for (int j : redo) {
+            if (rc != SS_OK) break;
+            const int64_t na = std::max<int64_t>(1, sym->arena);
+            const unsigned g = (unsigned)std::min<int64_t>((na + 255) / 256, (int64_t)ctx->sm_count * 16);
+            ss_launch(ctx, SS_K_MISC, k_round_f32, g, 256, 0, ctx->stream, na, (const double *)f->arena[j],
+                      f->arena_lo[j]);
+            double rho_lo = INFINITY;
+            rc = solve_contraction(f, j, &rho_lo);
+            if (rc != SS_OK) break;
+            if (rho_lo <= kRoundedRhoMax) {
+                f->rho[j] = rho_lo;
+            } else {
+                SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+                cudaFree(f->arena_lo[j]);
+                f->arena_lo[j] = nullptr;
+            }
+        }
     } else {
         rc = factor_run<double>(f, all);
     }
@@ -413,7 +462,7 @@ extern "C" ss_status ss_inertia(const ss_numeric *f, int32_t j, int64_t *n_neg, 
 
 extern "C" ss_status ss_factor_quality(const ss_numeric *f, int32_t j, int32_t *precision_used, double *rho) {
     if (!f || j < 0 || j >= f->n_shift) return SS_ERR_ARG;
-    if (precision_used) *precision_used = f->shift_prec[j];
+    if (precision_used) *precision_used = f->arena_lo[j] ? SS_FP64_SOLVE32 : f->shift_prec[j];
     if (rho) *rho = f->rho[j];
     return SS_OK;
 }
@@ -457,6 +506,69 @@ int solve_half_backward(ss_numeric *f, int j, const double *y, int k, double *x)
     return SS_OK;
 }
 
+// Both sweeps in one cooperative launch of k_solve_sweeps (every block resident, a
+// bounded grid barrier between steps).  Returns SS_ERR_TIMEOUT if a barrier gave up.
+template <typename T>
+static int solve_sweeps(ss_numeric *f, int j, T *b, int k, bool forward, bool backward, int dinv, const T *arena) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    const int cls = std::is_same<T, float>::value ? SS_K_SOLVE_F32 : SS_K_SOLVE;
+    if (!ctx->d_bar) SS_CUDA_TRY(ctx, cudaMalloc((void **)&ctx->d_bar, sizeof(GridBar)));
+    int &per_sm = ctx->sweep_blocks_per_sm[std::is_same<T, float>::value ? 1 : 0];
+    if (per_sm == 0) {
+        SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_sweeps<T>, 256,
+                                                                       sweep_smem<T>()));
+        if (per_sm <= 0) return ctx->set_error(SS_ERR_CUDA, "solve: sweep kernel cannot be resident");
+    }
+    const int nchunk = (k + KC - 1) / KC, ndchunk = (k + KD - 1) / KD;
+    int64_t items = 1;
+    double flops = 0.0;
+    for (const SolveLevel &sl : s->solve_levels) {
+        items = std::max<int64_t>(items, std::max<int64_t>((int64_t)sl.count * ndchunk, (int64_t)sl.row_tiles * nchunk));
+        flops += ((forward ? 2.0 : 0.0) + (backward ? 2.0 : 0.0)) * sl.offdiag * k;
+    }
+    const int nb = (int)std::min<int64_t>((int64_t)per_sm * ctx->sm_count, items);
+    const int64_t zn = std::max<int64_t>(1, (int64_t)s->panels.size()) * NB * k;
+    T *zall = nullptr;
+    if (backward) {
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&zall, sizeof(T) * zn, st));
+        SS_CUDA_TRY(ctx, cudaMemsetAsync(zall, 0, sizeof(T) * zn, st));
+    }
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBar), st));
+    SweepArgs a{};
+    a.lev = (const SweepLevel *)s->d_sweep_lev;
+    a.nlev = (int32_t)s->solve_levels.size();
+    a.k = k;
+    a.solve_panels = s->d_solve_panels;
+    a.tile_pre = s->d_solve_tile_pre;
+    a.panels = s->d_panels;
+    a.idx = s->d_idx;
+    a.linv = f->linv[j];
+    a.dblk = f->dblk[j];
+    a.piv = f->piv[j];
+    a.forward = forward ? 1 : 0;
+    a.backward = backward ? 1 : 0;
+    a.dinv = dinv;
+    a.bar = ctx->d_bar;
+    a.limit = 20000000;        // polls of about 64 ns: ~1 s per barrier
+    void *args[] = {(void *)&a, (void *)&arena, (void *)&b, (void *)&zall};
+    g_ss_launches.fetch_add(1, std::memory_order_relaxed);
+    size_t slot = 0;
+    const bool prof = ctx->prof_mask & (1u << cls);
+    if (prof) slot = ss_prof_begin(ctx, cls);
+    SS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)k_solve_sweeps<T>, dim3(nb), dim3(256), args,
+                                                 sweep_smem<T>(), st));
+    if (prof) ss_prof_end(ctx, cls, slot);
+    ctx->add_flops(cls, flops);
+    int herr = 0;
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, &ctx->d_bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (zall) SS_CUDA_TRY(ctx, cudaFreeAsync(zall, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (herr) return ctx->set_error(SS_ERR_TIMEOUT, "solve: grid barrier of the sweep kernel timed out");
+    return SS_OK;
+}
+
 template <typename T>
 static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool backward, int dinv) {
     ss_symbolic *s = f->sym;
@@ -464,6 +576,8 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     cudaStream_t st = ctx->stream;
     set_smem_attrs<T>();
     const T *arena = (const T *)f->arena[j];
+    if (std::is_same<T, float>::value && f->arena_lo[j]) arena = (const T *)f->arena_lo[j];
+    if (ctx->solve_mode == SS_SOLVE_SWEEP_KERNEL) return solve_sweeps<T>(f, j, b, k, forward, backward, dinv, arena);
     const int nchunk = (k + KC - 1) / KC;
     const int ndchunk = (k + KD - 1) / KD;
     const int nlev = (int)s->solve_levels.size();
@@ -473,7 +587,7 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
         ss_launch(ctx, SS_K_FWD_DIAG, k_fwd_diag<T>, dim3(sl.count, ndchunk), 256, diag_solve_smem<T>(), st, lp, s->d_panels, f->linv[j],
                                                                                f->piv[j], b, k);
         if (sl.row_tiles > 0)
-            ss_launch(ctx, std::is_same<T, float>::value ? SS_K_FWD_UPDATE_F32 : SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
+            ss_launch(ctx, std::is_same<T, float>::value ? SS_K_FWD_UPDATE_F32 : SS_K_FWD_UPDATE, k_fwd_update<T>, dim3(sl.row_tiles, nchunk), 256, tile_kernel_smem<T>(), st,
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k);
         if (sl.row_tiles > 0)
             ctx->add_flops(std::is_same<T, float>::value ? SS_K_FWD_UPDATE_F32 : SS_K_FWD_UPDATE, 2.0 * sl.offdiag * k);
@@ -488,7 +602,7 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
         const int32_t *lp = s->d_solve_panels + sl.panel_off;
         if (sl.row_tiles > 0) {
             SS_CUDA_TRY(ctx, cudaMemsetAsync(z, 0, sizeof(T) * (int64_t)sl.count * NB * k, st));
-            ss_launch(ctx, std::is_same<T, float>::value ? SS_K_BWD_GATHER_F32 : SS_K_BWD_GATHER, k_bwd_gather<T>, dim3(sl.row_tiles, nchunk), 256, tile_solve_smem<T>(), st, 
+            ss_launch(ctx, std::is_same<T, float>::value ? SS_K_BWD_GATHER_F32 : SS_K_BWD_GATHER, k_bwd_gather<T>, dim3(sl.row_tiles, nchunk), 256, tile_kernel_smem<T>(), st,
                 lp, s->d_solve_tile_pre + sl.panel_off, sl.count, s->d_panels, s->d_idx, arena, b, k, z);
             ctx->add_flops(std::is_same<T, float>::value ? SS_K_BWD_GATHER_F32 : SS_K_BWD_GATHER, 2.0 * sl.offdiag * k);
         }
@@ -630,7 +744,7 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     const unsigned g = (unsigned)((tot + 255) / 256);
     int rc;
     if (steps_done) *steps_done = 0;
-    if (f->shift_prec[j] == SS_FP64) {
+    if (!ss_solves_f32(f, j)) {
         // FP64 factor: X_0 = M^-1 R, then `refine` steps X += M^-1 (R - M X) (iterative
         // refinement in the factor's own precision removes the effect of element growth
         // on the solve's backward error)

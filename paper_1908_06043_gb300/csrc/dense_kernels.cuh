@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "grid_sync.cuh"
+
 namespace ssd {
 
 // ---------------------------------------------------------------- Gram G += X^T Y
@@ -327,42 +329,8 @@ __global__ void __launch_bounds__(1024) k_jacobi_block(double *H, double *V, int
 }
 
 // ---------------------------------------------------------------- grid-wide Jacobi
-// Grid barrier for a cooperative launch (every block resident).  The spin on the
-// generation word is bounded: after `limit` polls the block records a timeout in *err
-// and every block leaves the kernel at its next barrier.
-struct GridBar {
-    unsigned int count;
-    unsigned int gen;
-    int err;
-    int pad;
-};
-
-__device__ __forceinline__ bool grid_barrier(GridBar *bar, unsigned int nblocks, long long limit) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &bar->gen;
-        const unsigned int g = *vgen;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblocks - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            long long it = 0;
-            while (*vgen == g) {
-                if (++it > limit || *(volatile int *)&bar->err) {
-                    atomicExch(&bar->err, 1);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return *(volatile int *)&bar->err == 0;
-}
+using ::GridBar;
+using ::grid_barrier;
 
 // The same parallel-ordered Jacobi as k_jacobi_block, spread over a cooperative grid:
 // per round the rotations go to global scratch (pairs / cs), a grid barrier, the 2 x 2

@@ -11,11 +11,16 @@
 
 #include "../../include/sislice.h"
 
+struct GridBar;   // grid_sync.cuh
+
 struct ss_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
+    int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
+    GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
+    int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)
     // per-class launch timing (ss_profile): event pairs recorded around launches
     uint32_t prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -32,6 +37,7 @@ struct ss_ctx {
     }
     ~ss_ctx() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (d_bar) cudaFree(d_bar);
     }
 };
 
@@ -166,6 +172,7 @@ struct ss_symbolic {
     int32_t *d_solve_panels = nullptr;
     int32_t *d_solve_tile_pre = nullptr;
     int32_t *d_col_panel = nullptr;          // permuted column -> panel
+    void *d_sweep_lev = nullptr;             // solve levels for the sweep kernel (SweepLevel)
 };
 
 struct ss_numeric {
@@ -179,6 +186,7 @@ struct ss_numeric {
     double norm_a1 = 0, norm_b1 = 0;
     // per shift
     std::vector<void *> arena;            // front arena (double or float)
+    std::vector<float *> arena_lo;        // FP32 rounding of an FP64 arena that solves read, or null
     std::vector<double *> linv;           // npanels * nb * nb, L11^-1 of each panel
     std::vector<double *> dblk;           // npanels * nb * 2: D diagonal, D sub-diagonal
     std::vector<int32_t *> piv;           // npanels * nb: local pivot order
@@ -186,6 +194,11 @@ struct ss_numeric {
     std::vector<unsigned long long> h_counts;
     bool counts_valid = false;
 };
+
+// solves of shift j run in FP32 (an FP32 factor, or an FP64 factor with a rounded copy)
+inline bool ss_solves_f32(const ss_numeric *f, int j) {
+    return f->shift_prec[j] == SS_MIXED || f->arena_lo[j] != nullptr;
+}
 
 // helpers implemented in the .cu files
 int ss_symbolic_upload(ss_symbolic *s);

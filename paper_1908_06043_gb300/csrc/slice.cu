@@ -294,7 +294,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // W = (A - sigma B)^-1 B V (Alg. 2 step 3); a mixed factor runs plain FP32 solves
         // while the window's residuals are above 1e-6 and FP64 refinement afterwards
         int done_ref = 0;
-        const int ref_now = near_conv ? (f->shift_prec[j] == SS_MIXED ? refine : 1) : 0;
+        const int ref_now = near_conv ? (ss_solves_f32(f, j) ? refine : 1) : 0;
         if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref)) != SS_OK) return rc;
         refine_total += done_ref;
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;

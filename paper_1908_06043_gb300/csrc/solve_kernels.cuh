@@ -7,11 +7,22 @@
 //             x1 = P^T L11^-T (D^-1 y - z)                                 (scatter)
 // Panels in one solve level are independent; levels run in order (forward) or reverse
 // order (backward).  T is the factor / right-hand-side type.
+//
+// Each step is a device function over one work item (a panel or a row tile, times a
+// chunk of right-hand-side columns).  Two drivers run them: one kernel launch per level
+// and step (k_fwd_diag, k_fwd_update, ...), or k_solve_sweeps, a single cooperative
+// launch that walks every level of both sweeps with a bounded grid barrier between
+// steps.  The right-hand sides and the gather buffer are written by other blocks of the
+// same launch there, so they are read through plain (coherent) loads, never through the
+// read-only path.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
+#include "grid_sync.cuh"
 #include "internal.h"
 
 namespace ssk {
@@ -20,26 +31,60 @@ constexpr int KC = 32;     // right-hand-side columns per block of the update / 
 constexpr int KD = 8;      // right-hand-side columns per block of the diagonal kernels: they
                            // run alone on the long chain of root panels, so narrow chunks
                            // spread each level over more SMs
-// dynamic shared memory of the solve kernels
+constexpr int LT_LD = NB + 4;   // row stride of the FP32 gather's transposed panel tile
+
+// dynamic shared memory of the solve steps
 template <typename T> constexpr size_t diag_solve_smem() { return sizeof(T) * NB * ((KD + 1) + (NB + 1)); }
 template <typename T> constexpr size_t tile_solve_smem() { return sizeof(T) * (NB * (TR + 1) + TR * (KC + 1)); }
+constexpr size_t tile_solve_smem_f32() { return sizeof(float) * (TR * LT_LD + TR * KC); }
+// shared memory of the per-step update / gather kernels for T
+template <typename T> constexpr size_t tile_kernel_smem() {
+    return std::is_same<T, float>::value ? tile_solve_smem_f32() : tile_solve_smem<T>();
+}
+template <typename T> constexpr size_t sweep_smem() {
+    return diag_solve_smem<T>() > tile_kernel_smem<T>() ? diag_solve_smem<T>() : tile_kernel_smem<T>();
+}
 
 __device__ __forceinline__ void atomic_add_t(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void atomic_add_t(float *p, float v) { atomicAdd(p, v); }
 
-// forward diagonal step: block (panel in level, rhs chunk)
+__device__ __forceinline__ void atomic_add_pair(float *p, float v0, float v1, bool both, bool paired) {
+    if (paired) {
+        atomicAdd(reinterpret_cast<float2 *>(p), make_float2(v0, v1));
+    } else {
+        atomicAdd(p, v0);
+        if (both) atomicAdd(p + 1, v1);
+    }
+}
+
+// panel slot of a row tile: the last slot whose tile prefix is <= tile
+__device__ __forceinline__ int tile_slot(const int32_t *__restrict__ tile_pre, int32_t count, int tile) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tile_pre[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- step bodies
+// Each body starts with a block barrier, so a block may run several items in a row on
+// the same shared memory.
+
+// forward diagonal step of panel slot `slot`, right-hand-side chunk `chunk` (KD columns)
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_diag(const int32_t *__restrict__ lvl_panels,
-                                                   const PanelDesc *__restrict__ panels,
-                                                   const double *__restrict__ linv,
-                                                   const int32_t *__restrict__ piv, T *b, int k) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fwd_diag_item(unsigned char *smem_raw, int slot, int chunk,
+                                              const int32_t *__restrict__ lvl_panels,
+                                              const PanelDesc *__restrict__ panels,
+                                              const double *__restrict__ linv,
+                                              const int32_t *__restrict__ piv, T *b, int k) {
     T (*Y)[KD + 1] = reinterpret_cast<T (*)[KD + 1]>(smem_raw);
     T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KD + 1));
-    const int p = lvl_panels[blockIdx.x];
+    const int p = lvl_panels[slot];
     const PanelDesc pd = panels[p];
-    const int w = pd.w, c0 = blockIdx.y * KD, kc = min(KD, k - c0);
+    const int w = pd.w, c0 = chunk * KD, kc = min(KD, k - c0);
     const int tid = threadIdx.x;
+    __syncthreads();
     for (int q = tid; q < w * KD; q += 256) {
         int i = q / KD, c = q % KD;
         int src = piv[(int64_t)p * NB + i];
@@ -59,31 +104,26 @@ __global__ void __launch_bounds__(256) k_fwd_diag(const int32_t *__restrict__ lv
     }
 }
 
-// forward update: block (row tile of a panel in level, rhs chunk): b2 -= L21 y
+// forward update of row tile `tile`, chunk `chunk` (KC columns): b2 -= L21 y
 template <typename T>
-__global__ void __launch_bounds__(256) k_fwd_update(const int32_t *__restrict__ lvl_panels,
-                                                     const int32_t *__restrict__ tile_pre,
-                                                     int32_t count, const PanelDesc *__restrict__ panels,
-                                                     const int32_t *__restrict__ idx,
-                                                     const T *__restrict__ arena, T *b, int k) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void fwd_update_item(unsigned char *smem_raw, int tile, int chunk,
+                                                const int32_t *__restrict__ lvl_panels,
+                                                const int32_t *__restrict__ tile_pre, int32_t count,
+                                                const PanelDesc *__restrict__ panels,
+                                                const int32_t *__restrict__ idx,
+                                                const T *__restrict__ arena, T *b, int k) {
     T (*Ls)[TR + 1] = reinterpret_cast<T (*)[TR + 1]>(smem_raw);                 // Ls[t][row]
     T (*Y)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw + sizeof(T) * NB * (TR + 1));
-    const int tile = blockIdx.x;
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tile_pre[mid] <= tile) lo = mid; else hi = mid - 1;
-    }
+    const int lo = tile_slot(tile_pre, count, tile);
     const PanelDesc pd = panels[lvl_panels[lo]];
     const int w = pd.w, m = pd.m;
     const int r0 = (tile - tile_pre[lo]) * TR;
-    const int rbelow = m - pd.k0 - w;
-    const int nr = min(TR, rbelow - r0);
-    const int c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const int nr = min(TR, m - pd.k0 - w - r0);
+    const int c0 = chunk * KC, kc = min(KC, k - c0);
     const T *F = arena + pd.front_off;
     const int64_t rowbase = pd.k0 + w + r0;
     const int tid = threadIdx.x;
+    __syncthreads();
     for (int q = tid; q < w * TR; q += 256) {
         int t = q / TR, i = q % TR;
         Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
@@ -107,33 +147,78 @@ __global__ void __launch_bounds__(256) k_fwd_update(const int32_t *__restrict__ 
     }
 }
 
-// backward gather: z[slot][t][c] += sum_rows L21[row][t] x[idx[row]][c]
-template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_gather(const int32_t *__restrict__ lvl_panels,
-                                                     const int32_t *__restrict__ tile_pre,
-                                                     int32_t count, const PanelDesc *__restrict__ panels,
-                                                     const int32_t *__restrict__ idx,
-                                                     const T *__restrict__ arena, const T *__restrict__ x,
-                                                     int k, T *zbuf) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T (*Ls)[TR + 1] = reinterpret_cast<T (*)[TR + 1]>(smem_raw);
-    T (*Xs)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw + sizeof(T) * NB * (TR + 1));
-    const int tile = blockIdx.x;
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (tile_pre[mid] <= tile) lo = mid; else hi = mid - 1;
-    }
+// FP32 forward update.  With FP32 arithmetic the one-FMA-per-two-shared-loads loop above
+// is bound by shared-memory bandwidth, so each thread keeps a 4 x 2 register tile (one
+// 16-byte and one 8-byte shared load per 8 FMAs) and adds with paired atomics where the
+// row stride allows.
+__device__ __forceinline__ void fwd_update_f32_item(unsigned char *smem_raw, int tile, int chunk,
+                                                    const int32_t *__restrict__ lvl_panels,
+                                                    const int32_t *__restrict__ tile_pre, int32_t count,
+                                                    const PanelDesc *__restrict__ panels,
+                                                    const int32_t *__restrict__ idx,
+                                                    const float *__restrict__ arena, float *b, int k) {
+    float (*Ls)[TR] = reinterpret_cast<float (*)[TR]>(smem_raw);                 // Ls[t][row]
+    float (*Y)[KC] = reinterpret_cast<float (*)[KC]>(smem_raw + sizeof(float) * NB * TR);
+    const int lo = tile_slot(tile_pre, count, tile);
     const PanelDesc pd = panels[lvl_panels[lo]];
     const int w = pd.w, m = pd.m;
     const int r0 = (tile - tile_pre[lo]) * TR;
-    const int rbelow = m - pd.k0 - w;
-    const int nr = min(TR, rbelow - r0);
-    const int c0 = blockIdx.y * KC, kc = min(KC, k - c0);
+    const int nr = min(TR, m - pd.k0 - w - r0);
+    const int c0 = chunk * KC, kc = min(KC, k - c0);
+    const float *F = arena + pd.front_off;
+    const int64_t rowbase = pd.k0 + w + r0;
+    const int tid = threadIdx.x;
+    __syncthreads();
+    for (int q = tid; q < w * TR; q += 256) {
+        int t = q / TR, i = q % TR;
+        Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
+    }
+    for (int q = tid; q < w * KC; q += 256) {
+        int t = q / KC, c = q % KC;
+        Y[t][c] = c < kc ? b[(int64_t)(pd.g0 + t) * k + c0 + c] : 0.f;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;          // columns 2tx, 2tx+1; rows 4ty .. 4ty+3
+    float acc[4][2] = {};
+    for (int t = 0; t < w; ++t) {
+        const float4 l = *reinterpret_cast<const float4 *>(&Ls[t][4 * ty]);
+        const float2 y = *reinterpret_cast<const float2 *>(&Y[t][2 * tx]);
+        acc[0][0] += l.x * y.x; acc[0][1] += l.x * y.y;
+        acc[1][0] += l.y * y.x; acc[1][1] += l.y * y.y;
+        acc[2][0] += l.z * y.x; acc[2][1] += l.z * y.y;
+        acc[3][0] += l.w * y.x; acc[3][1] += l.w * y.y;
+    }
+    const int c = 2 * tx;
+    if (c >= kc) return;
+    const bool both = c + 1 < kc, paired = both && (k % 2 == 0);
+    const int *gi = idx + pd.idx_off + rowbase;
+    for (int r = 0; r < 4; ++r) {
+        const int i = 4 * ty + r;
+        if (i < nr) atomic_add_pair(&b[(int64_t)gi[i] * k + c0 + c], -acc[r][0], -acc[r][1], both, paired);
+    }
+}
+
+// backward gather of row tile `tile`: z[slot][t][c] += sum_rows L21[row][t] x[idx[row]][c]
+template <typename T>
+__device__ __forceinline__ void bwd_gather_item(unsigned char *smem_raw, int tile, int chunk,
+                                                const int32_t *__restrict__ lvl_panels,
+                                                const int32_t *__restrict__ tile_pre, int32_t count,
+                                                const PanelDesc *__restrict__ panels,
+                                                const int32_t *__restrict__ idx,
+                                                const T *__restrict__ arena, const T *x, int k, T *zbuf) {
+    T (*Ls)[TR + 1] = reinterpret_cast<T (*)[TR + 1]>(smem_raw);
+    T (*Xs)[KC + 1] = reinterpret_cast<T (*)[KC + 1]>(smem_raw + sizeof(T) * NB * (TR + 1));
+    const int lo = tile_slot(tile_pre, count, tile);
+    const PanelDesc pd = panels[lvl_panels[lo]];
+    const int w = pd.w, m = pd.m;
+    const int r0 = (tile - tile_pre[lo]) * TR;
+    const int nr = min(TR, m - pd.k0 - w - r0);
+    const int c0 = chunk * KC, kc = min(KC, k - c0);
     const T *F = arena + pd.front_off;
     const int64_t rowbase = pd.k0 + w + r0;
     const int *gi = idx + pd.idx_off + rowbase;
     const int tid = threadIdx.x;
+    __syncthreads();
     for (int q = tid; q < w * TR; q += 256) {
         int t = q / TR, i = q % TR;
         Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
@@ -153,24 +238,73 @@ __global__ void __launch_bounds__(256) k_bwd_gather(const int32_t *__restrict__ 
     }
 }
 
-// backward diagonal step: x1 = P^T L11^-T (D^-1 y - z)
+// FP32 backward gather with a 4 x 2 register tile per thread (see the FP32 update)
+__device__ __forceinline__ void bwd_gather_f32_item(unsigned char *smem_raw, int tile, int chunk,
+                                                    const int32_t *__restrict__ lvl_panels,
+                                                    const int32_t *__restrict__ tile_pre, int32_t count,
+                                                    const PanelDesc *__restrict__ panels,
+                                                    const int32_t *__restrict__ idx,
+                                                    const float *__restrict__ arena, const float *x, int k,
+                                                    float *zbuf) {
+    float (*Lt)[LT_LD] = reinterpret_cast<float (*)[LT_LD]>(smem_raw);          // Lt[row][t]
+    float (*Xs)[KC] = reinterpret_cast<float (*)[KC]>(smem_raw + sizeof(float) * TR * LT_LD);
+    const int lo = tile_slot(tile_pre, count, tile);
+    const PanelDesc pd = panels[lvl_panels[lo]];
+    const int w = pd.w, m = pd.m;
+    const int r0 = (tile - tile_pre[lo]) * TR;
+    const int nr = min(TR, m - pd.k0 - w - r0);
+    const int c0 = chunk * KC, kc = min(KC, k - c0);
+    const float *F = arena + pd.front_off;
+    const int64_t rowbase = pd.k0 + w + r0;
+    const int *gi = idx + pd.idx_off + rowbase;
+    const int tid = threadIdx.x;
+    __syncthreads();
+    for (int q = tid; q < NB * TR; q += 256) {
+        int t = q / TR, i = q % TR;
+        Lt[i][t] = (i < nr && t < w) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
+    }
+    for (int q = tid; q < TR * KC; q += 256) {
+        int i = q / KC, c = q % KC;
+        Xs[i][c] = (i < nr && c < kc) ? x[(int64_t)gi[i] * k + c0 + c] : 0.f;
+    }
+    __syncthreads();
+    const int tx = tid & 15, ty = tid >> 4;          // columns 2tx, 2tx+1; panel columns 4ty .. 4ty+3
+    float acc[4][2] = {};
+    for (int i = 0; i < nr; ++i) {
+        const float4 l = *reinterpret_cast<const float4 *>(&Lt[i][4 * ty]);
+        const float2 v = *reinterpret_cast<const float2 *>(&Xs[i][2 * tx]);
+        acc[0][0] += l.x * v.x; acc[0][1] += l.x * v.y;
+        acc[1][0] += l.y * v.x; acc[1][1] += l.y * v.y;
+        acc[2][0] += l.z * v.x; acc[2][1] += l.z * v.y;
+        acc[3][0] += l.w * v.x; acc[3][1] += l.w * v.y;
+    }
+    const int c = 2 * tx;
+    if (c >= kc) return;
+    const bool both = c + 1 < kc, paired = both && (k % 2 == 0);
+    float *z = zbuf + (int64_t)lo * NB * k;
+    for (int r = 0; r < 4; ++r) {
+        const int t = 4 * ty + r;
+        if (t < w) atomic_add_pair(&z[(int64_t)t * k + c0 + c], acc[r][0], acc[r][1], both, paired);
+    }
+}
+
+// backward diagonal step of panel slot `slot`: x1 = P^T L11^-T (D^-1 y - z)
 template <typename T>
-__global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lvl_panels,
-                                                   const PanelDesc *__restrict__ panels,
-                                                   const double *__restrict__ linv,
-                                                   const double *__restrict__ dblk,
-                                                   const int32_t *__restrict__ piv,
-                                                   const T *__restrict__ zbuf, int use_z, T *x,
-                                                   int k, int dinv) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void bwd_diag_item(unsigned char *smem_raw, int slot, int chunk,
+                                              const int32_t *__restrict__ lvl_panels,
+                                              const PanelDesc *__restrict__ panels,
+                                              const double *__restrict__ linv,
+                                              const double *__restrict__ dblk,
+                                              const int32_t *__restrict__ piv,
+                                              const T *zbuf, int use_z, T *x, int k, int dinv) {
     T (*U)[KD + 1] = reinterpret_cast<T (*)[KD + 1]>(smem_raw);
     T (*Lm)[NB + 1] = reinterpret_cast<T (*)[NB + 1]>(smem_raw + sizeof(T) * NB * (KD + 1));
     __shared__ double sd[NB], se[NB];
-    const int slot = blockIdx.x;
     const int p = lvl_panels[slot];
     const PanelDesc pd = panels[p];
-    const int w = pd.w, c0 = blockIdx.y * KD, kc = min(KD, k - c0);
+    const int w = pd.w, c0 = chunk * KD, kc = min(KD, k - c0);
     const int tid = threadIdx.x;
+    __syncthreads();
     if (tid < NB) {
         sd[tid] = dblk[(int64_t)p * 2 * NB + tid];
         se[tid] = dblk[(int64_t)p * 2 * NB + NB + tid];
@@ -220,6 +354,136 @@ __global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lv
         T acc = 0;
         for (int t = i; t < w; ++t) acc += Lm[t][i] * U[t][cc];
         x[(int64_t)(pd.g0 + piv[(int64_t)p * NB + i]) * k + c0 + cc] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- one launch per step
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_diag(const int32_t *__restrict__ lvl_panels,
+                                                   const PanelDesc *__restrict__ panels,
+                                                   const double *__restrict__ linv,
+                                                   const int32_t *__restrict__ piv, T *b, int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fwd_diag_item<T>(smem_raw, blockIdx.x, blockIdx.y, lvl_panels, panels, linv, piv, b, k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fwd_update(const int32_t *__restrict__ lvl_panels,
+                                                     const int32_t *__restrict__ tile_pre,
+                                                     int32_t count, const PanelDesc *__restrict__ panels,
+                                                     const int32_t *__restrict__ idx,
+                                                     const T *__restrict__ arena, T *b, int k) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (std::is_same<T, float>::value)
+        fwd_update_f32_item(smem_raw, blockIdx.x, blockIdx.y, lvl_panels, tile_pre, count, panels, idx, arena, b, k);
+    else
+        fwd_update_item<T>(smem_raw, blockIdx.x, blockIdx.y, lvl_panels, tile_pre, count, panels, idx, arena, b, k);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_gather(const int32_t *__restrict__ lvl_panels,
+                                                     const int32_t *__restrict__ tile_pre,
+                                                     int32_t count, const PanelDesc *__restrict__ panels,
+                                                     const int32_t *__restrict__ idx,
+                                                     const T *__restrict__ arena, const T *x,
+                                                     int k, T *zbuf) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (std::is_same<T, float>::value)
+        bwd_gather_f32_item(smem_raw, blockIdx.x, blockIdx.y, lvl_panels, tile_pre, count, panels, idx, arena, x, k,
+                            zbuf);
+    else
+        bwd_gather_item<T>(smem_raw, blockIdx.x, blockIdx.y, lvl_panels, tile_pre, count, panels, idx, arena, x, k,
+                           zbuf);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bwd_diag(const int32_t *__restrict__ lvl_panels,
+                                                   const PanelDesc *__restrict__ panels,
+                                                   const double *__restrict__ linv,
+                                                   const double *__restrict__ dblk,
+                                                   const int32_t *__restrict__ piv,
+                                                   const T *zbuf, int use_z, T *x, int k, int dinv) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    bwd_diag_item<T>(smem_raw, blockIdx.x, blockIdx.y, lvl_panels, panels, linv, dblk, piv, zbuf, use_z, x, k,
+                     dinv);
+}
+
+// ---------------------------------------------------------------- one launch per solve
+struct SweepLevel {        // device copy of a solve level
+    int32_t panel_off;     // into the level-ordered panel list
+    int32_t count;         // panels
+    int32_t row_tiles;     // row tiles of their below-diagonal rows
+    int32_t pad;
+};
+
+struct SweepArgs {
+    const SweepLevel *lev;
+    int32_t nlev;
+    int32_t k;
+    const int32_t *solve_panels;
+    const int32_t *tile_pre;
+    const PanelDesc *panels;
+    const int32_t *idx;
+    const double *linv;
+    const double *dblk;
+    const int32_t *piv;
+    int32_t forward, backward, dinv, pad;
+    GridBar *bar;
+    long long limit;
+};
+
+// Forward and/or backward sweep over every level in one cooperative launch.  The work
+// items of a step are spread over the resident blocks; a grid barrier separates
+// consecutive steps.  zall: (number of panels) x NB x k, zero on entry (each level
+// gathers into its own slots).  On a barrier timeout bar->err is set and every block
+// returns.
+template <typename T>
+__global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__restrict__ arena, T *b, T *zall) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int k = a.k;
+    const int nchunk = (k + KC - 1) / KC, ndchunk = (k + KD - 1) / KD;
+    const unsigned nb = gridDim.x;
+    if (a.forward) {
+        for (int L = 0; L < a.nlev; ++L) {
+            const SweepLevel lv = a.lev[L];
+            const int32_t *lp = a.solve_panels + lv.panel_off;
+            for (int q = blockIdx.x; q < lv.count * ndchunk; q += nb)
+                fwd_diag_item<T>(smem_raw, q % lv.count, q / lv.count, lp, a.panels, a.linv, a.piv, b, k);
+            if (!grid_barrier(a.bar, nb, a.limit)) return;
+            if (lv.row_tiles == 0) continue;
+            const int32_t *tp = a.tile_pre + lv.panel_off;
+            for (int q = blockIdx.x; q < lv.row_tiles * nchunk; q += nb) {
+                if constexpr (std::is_same<T, float>::value)
+                    fwd_update_f32_item(smem_raw, q % lv.row_tiles, q / lv.row_tiles, lp, tp, lv.count, a.panels,
+                                        a.idx, arena, b, k);
+                else
+                    fwd_update_item<T>(smem_raw, q % lv.row_tiles, q / lv.row_tiles, lp, tp, lv.count, a.panels,
+                                       a.idx, arena, b, k);
+            }
+            if (!grid_barrier(a.bar, nb, a.limit)) return;
+        }
+    }
+    if (!a.backward) return;
+    for (int L = a.nlev - 1; L >= 0; --L) {
+        const SweepLevel lv = a.lev[L];
+        const int32_t *lp = a.solve_panels + lv.panel_off;
+        T *z = zall + (int64_t)lv.panel_off * NB * k;
+        if (lv.row_tiles > 0) {
+            const int32_t *tp = a.tile_pre + lv.panel_off;
+            for (int q = blockIdx.x; q < lv.row_tiles * nchunk; q += nb) {
+                if constexpr (std::is_same<T, float>::value)
+                    bwd_gather_f32_item(smem_raw, q % lv.row_tiles, q / lv.row_tiles, lp, tp, lv.count, a.panels,
+                                        a.idx, arena, b, k, z);
+                else
+                    bwd_gather_item<T>(smem_raw, q % lv.row_tiles, q / lv.row_tiles, lp, tp, lv.count, a.panels,
+                                       a.idx, arena, b, k, z);
+            }
+            if (!grid_barrier(a.bar, nb, a.limit)) return;
+        }
+        for (int q = blockIdx.x; q < lv.count * ndchunk; q += nb)
+            bwd_diag_item<T>(smem_raw, q % lv.count, q / lv.count, lp, a.panels, a.linv, a.dblk, a.piv, z,
+                             lv.row_tiles > 0 ? 1 : 0, b, k, a.dinv);
+        if (L > 0 && !grid_barrier(a.bar, nb, a.limit)) return;
     }
 }
 

@@ -350,13 +350,14 @@ class SliceSolver:
         res = np.array([probes[pj].resid[i] for pj, i in sel])
         order = np.argsort(lam, kind="stable")
         X = torch.stack([probes[sel[q][0]].X[:, sel[q][1]] for q in order], dim=1) if sel else None
+        quality = [("fp64", 0.0) if j in f64 else f.quality(j) for j in range(ns)]
         f.close()
         for g64 in f64.values():
             g64.close()
         return SliceResult(list(shifts), lam_min, lam_max, lam[order], X, res[order], info, probes, rounds,
                            dict(factor_s=t_factor, solve_s=t_solve, total_s=time.perf_counter() - t0,
                                 iterations=iters, n_below_max=nneg_max, n_below_min=nneg_min,
-                                converged=not active, fp64_refactors=sorted(f64)))
+                                converged=not active, fp64_refactors=sorted(f64), quality=quality))
 
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,

@@ -151,3 +151,54 @@ def test_gauss16_inertia_golden(gpu_lib):
             neg, zero, pos, _ = f.inertia(j)
             assert (neg, zero, pos) == (int(r[1]), int(r[2]), int(r[3])), (precision, r[0], f.quality(j))
         del f
+
+
+@pytest.mark.parametrize("k", [5, 34])
+def test_gauss16_rounded_fp32_solves(gpu_lib, k):
+    # interior shifts of the N = 16,384 pencil whose FP32 factor fails the quality gate
+    # are refactored in FP64 and solved in FP32 from the rounded factor inside FP64
+    # refinement; the refined solve must match the FP64 solve
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "gauss16_eigs.txt")
+    lam = np.array([float(l) for l in open(path) if not l.startswith("#")])
+    p = config_pencil(2)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    idx = [400, 800, 1200, 1600]
+    sig = mid_gap_shifts(lam, idx)
+    fm = sym.factor(a, b, sig, "mixed")
+    f64 = sym.factor(a, b, sig, "fp64")
+    R = torch.tensor(np.random.default_rng(k).standard_normal((p.n, k)), device="cuda")
+    kinds = []
+    for j, i in enumerate(idx):
+        kind, rho = fm.quality(j)
+        kinds.append(kind)
+        assert fm.inertia(j)[0] == i + 1
+        if kind != "fp64+f32solve":
+            continue
+        assert 0.0 < rho <= 0.25
+        x = fm.solve(j, R, refine=1)
+        ref = f64.solve(j, R, refine=1)
+        assert ((x - ref).norm() / ref.norm()).item() <= 1e-9, (i, rho)
+    assert "fp64+f32solve" in kinds, kinds
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("k", [1, 7, 40])
+def test_sweep_kernel_matches_per_step_launches(gpu_lib, precision, k):
+    # the single cooperative launch and the per-level launches run the same steps; only
+    # the order of the atomic additions differs
+    p = config_pencil(1)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    sig = mid_gap_shifts(lam, [10, 60, 300])
+    f = sym.factor(a, b, sig, precision)
+    R = torch.tensor(np.random.default_rng(k).standard_normal((p.n, k)), device="cuda")
+    M = [p.dense("a") - s * p.dense("b") for s in sig]
+    for j in range(len(sig)):
+        ctx.set_solve_mode("per_step")
+        x1 = f.solve(j, R, refine=2)
+        ctx.set_solve_mode("sweep")
+        x2 = f.solve(j, R, refine=2)
+        assert ((x1 - x2).norm() / x1.norm()).item() <= 1e-9
+        ref = np.linalg.solve(M[j], R.cpu().numpy())
+        assert np.abs(x2.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
