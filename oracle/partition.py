@@ -1,4 +1,4 @@
-"""Slice partition, validation and shift migration (Sections 2.3, 3.1, 3.2).
+"""Slice partition, validation and shift migration (Sections 2.2, 3.1, 3.2).
 
 Test infrastructure only.  Readings where the paper is silent or garbled:
 * CDOS roots (Eq. 6) are read as Phi(omega) = Phi(a) + K j, j = 0..n_s,
@@ -9,6 +9,13 @@ Test infrastructure only.  Readings where the paper is silent or garbled:
   (residual, probe index, Ritz index).
 * k-means++ draws its uniforms from an input array (one per centroid) so that both
   sides see the same random numbers.
+* Probe update after clustering (Section 3.2): a cluster maps to the probe that
+  produced most of its values (ties: the probe whose old shift is nearest the cluster
+  centroid, then the lower index).  The 2-means split of the largest cluster starts
+  from its smallest and largest values; the old probe keeps the part holding more of
+  its own values (ties: the part whose centroid is nearer its old shift), the inserted
+  probe takes the other.  An empty k-means cluster maps to no probe.  If the largest
+  cluster has a single distinct value it cannot be split and fewer probes result.
 """
 from __future__ import annotations
 
@@ -136,3 +143,79 @@ def lloyd(x, cent, maxit=1000):
 def kmeans_shifts(ritz_values, n_s, uniforms):
     """New shifts = k-means centroids of the validated Ritz values (Section 3.2)."""
     return lloyd(ritz_values, kmeans_pp_init(ritz_values, n_s, uniforms))
+
+
+def _assign(x, cent):
+    """Index of the nearest centroid of each value (the lower index on a tie)."""
+    return np.argmin(np.abs(np.asarray(x)[:, None] - np.asarray(cent)[None, :]), axis=1)
+
+
+def lloyd_assign(x, cent, maxit=1000):
+    """Lloyd iterations from the given centroids, keeping their order; an empty
+    cluster keeps its centroid.  Returns (centroids, assignment)."""
+    x = np.asarray(x, dtype=np.float64)
+    cent = np.asarray(cent, dtype=np.float64).copy()
+    a = _assign(x, cent)
+    for _ in range(maxit):
+        for c in range(cent.size):
+            if (a == c).any():
+                cent[c] = x[a == c].mean()
+        a2 = _assign(x, cent)
+        if np.array_equal(a2, a):
+            break
+        a = a2
+    return cent, a
+
+
+def migrate(values, owner, old_shifts, init_centroids):
+    """Shift migration between two SCF steps (Section 3.2).
+
+    values: validated eigenvalues of the previous step; owner[i]: the probe that
+    produced values[i]; old_shifts: that step's shifts (one per probe);
+    init_centroids: the k-means start (k-means++ after a DOS placement, else the old
+    shifts).  Steps, in the paper's order: k-means into n_s clusters; each cluster to
+    the probe with maximal overlap; clusters on one probe merged (shift = centroid of
+    the merged values); probes with no cluster deleted; for each deletion the largest
+    cluster split by 2-means, one part kept by its probe and the other given to an
+    inserted probe.  Returns a list of (shift, member indices into values), sorted by
+    shift; an inserted probe's start vectors are the Ritz vectors of its members."""
+    x = np.asarray(values, dtype=np.float64)
+    owner = np.asarray(owner)
+    old = np.asarray(old_shifts, dtype=np.float64)
+    n_s = old.size
+    cent, a = lloyd_assign(x, init_centroids)
+    members = {p: [] for p in range(n_s)}
+    for c in range(cent.size):
+        idx = np.nonzero(a == c)[0]
+        if idx.size == 0:
+            continue
+        overlap = np.array([(owner[idx] == p).sum() for p in range(n_s)])
+        best = np.nonzero(overlap == overlap.max())[0]
+        mu = x[idx].mean()
+        p = min(best, key=lambda q: (abs(old[q] - mu), q))
+        members[p].extend(idx.tolist())
+    probes = []          # (old probe index or -1 for an inserted one, member indices)
+    for p in range(n_s):
+        if members[p]:
+            probes.append([p, sorted(members[p])])
+    deleted = n_s - len(probes)
+    for _ in range(deleted):
+        big = max(range(len(probes)), key=lambda q: (len(probes[q][1]), -q))
+        p, idx = probes[big]
+        idx = np.array(idx)
+        v = x[idx]
+        if v.min() == v.max():
+            break
+        _, a2 = lloyd_assign(v, [v.min(), v.max()])
+        parts = [idx[a2 == 0], idx[a2 == 1]]
+        home = p if p >= 0 else None
+        def keep_key(part):
+            own = int((owner[part] == home).sum()) if home is not None else 0
+            ref = old[home] if home is not None else x[idx].mean()
+            return (-own, abs(x[part].mean() - ref))
+        order = sorted(range(2), key=lambda t: keep_key(parts[t]))
+        probes[big] = [p, sorted(parts[order[0]].tolist())]
+        probes.append([-1, sorted(parts[order[1]].tolist())])
+    out = [(float(x[np.array(m)].mean()), m) for _, m in probes]
+    out.sort(key=lambda t: t[0])
+    return out

@@ -308,6 +308,8 @@ static void factor_free(ss_numeric *f) {
     for (double *p : f->linv) if (p) cudaFree(p);
     for (double *p : f->dblk) if (p) cudaFree(p);
     for (int32_t *p : f->piv) if (p) cudaFree(p);
+    for (double *p : f->mvals) if (p) cudaFree(p);
+    f->mvals.clear();
     if (f->d_counts) cudaFree(f->d_counts);
     f->arena.clear(); f->arena_lo.clear(); f->linv.clear(); f->dblk.clear(); f->piv.clear();
     f->d_counts = nullptr;
@@ -333,6 +335,7 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
     if ((rc = ss_norm1(sym, b_vals, &f->norm_b1)) != SS_OK) { delete f; return rc; }
     f->arena.assign(n_shift, nullptr);
     f->arena_lo.assign(n_shift, nullptr);
+    f->mvals.assign(n_shift, nullptr);
     f->linv.assign(n_shift, nullptr);
     f->dblk.assign(n_shift, nullptr);
     f->piv.assign(n_shift, nullptr);
@@ -735,6 +738,29 @@ int solve_contraction(ss_numeric *f, int j, double *rho) {
     return SS_OK;
 }
 
+__global__ void k_shifted_vals(int64_t nnz, const double *__restrict__ a, const double *__restrict__ b, double sigma,
+                               double *__restrict__ m) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz; q += (int64_t)gridDim.x * blockDim.x)
+        m[q] = a[q] - sigma * b[q];
+}
+
+// values of A - sigma_j B, made once per shift: a refinement residual then costs one
+// multiply-add per nonzero and column instead of two
+static int shifted_values(ss_numeric *f, int j, const double **out) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    if (!f->mvals[j]) {
+        double *m = nullptr;
+        SS_CUDA_TRY(ctx, cudaMalloc((void **)&m, sizeof(double) * std::max<int64_t>(1, s->nnz)));
+        const unsigned g = (unsigned)std::min<int64_t>((s->nnz + 255) / 256, (int64_t)ctx->sm_count * 16);
+        ss_launch(ctx, SS_K_MISC, k_shifted_vals, std::max(1u, g), 256, 0, ctx->stream, s->nnz, f->a_vals, f->b_vals,
+                  f->sigma[j], m);
+        f->mvals[j] = m;
+    }
+    *out = f->mvals[j];
+    return SS_OK;
+}
+
 // X = (A - sigma B)^-1 R in the original order; FP64 R, X (may alias).
 int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done) {
     ss_symbolic *s = f->sym;
@@ -748,14 +774,11 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
         // FP64 factor: X_0 = M^-1 R, then `refine` steps X += M^-1 (R - M X) (iterative
         // refinement in the factor's own precision removes the effect of element growth
         // on the solve's backward error)
-        double *w = nullptr, *x = nullptr, *y = nullptr, *co = nullptr;
+        double *w = nullptr, *x = nullptr, *y = nullptr;
         SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&w, sizeof(double) * tot, st));
         if (refine > 0) {
             SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&x, sizeof(double) * tot, st));
             SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&y, sizeof(double) * tot, st));
-            SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&co, sizeof(double) * 2 * k, st));
-            ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, 1.0, co);
-            ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, -f->sigma[j], co + k);
         }
         double *out = refine > 0 ? x : X;
         ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm, R, w, 0);
@@ -763,7 +786,9 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
         ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
                   (const double *)w, out, 1);
         for (int it = 0; it < refine; ++it) {
-            if ((rc = spmm_launch(s, f->a_vals, f->b_vals, co, co + k, x, k, y)) != SS_OK) return rc;
+            const double *mv = nullptr;
+            if ((rc = shifted_values(f, j, &mv)) != SS_OK) return rc;
+            if ((rc = spmm_launch(s, mv, mv, nullptr, nullptr, x, k, y)) != SS_OK) return rc;
             ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, (const double *)y, y);
             ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
                       (const double *)y, w, 0);
@@ -776,7 +801,6 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
             SS_CUDA_TRY(ctx, cudaMemcpyAsync(X, x, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
             cudaFreeAsync(x, st);
             cudaFreeAsync(y, st);
-            cudaFreeAsync(co, st);
         }
         SS_CUDA_TRY(ctx, cudaFreeAsync(w, st));
         SS_CUDA_TRY(ctx, cudaGetLastError());
@@ -788,20 +812,18 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     if (refine > 0 && f->rho[j] > 0.0 && f->rho[j] < 1.0)
         refine = std::max(refine, std::min(8, (int)std::ceil(std::log(1e-13) / std::log(f->rho[j])) - 1));
     float *wf = nullptr;
-    double *r = nullptr, *y = nullptr, *al = nullptr, *be = nullptr, *x = nullptr;
+    double *r = nullptr, *y = nullptr, *x = nullptr;
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wf, sizeof(float) * tot, st));
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&r, sizeof(double) * tot, st));
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&y, sizeof(double) * tot, st));
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&x, sizeof(double) * tot, st));
-    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&al, sizeof(double) * 2 * k, st));
-    be = al + k;
-    ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, 1.0, al);
-    ss_launch(ctx, SS_K_MISC, k_fill_const, (k + 255) / 256, 256, 0, st, k, -f->sigma[j], be);
     SS_CUDA_TRY(ctx, cudaMemsetAsync(x, 0, sizeof(double) * tot, st));
     for (int it = 0; it <= refine; ++it) {
         const double *rhs = R;
         if (it > 0) {
-            if ((rc = spmm_launch(s, f->a_vals, f->b_vals, al, be, x, k, y)) != SS_OK) return rc;
+            const double *mv = nullptr;
+            if ((rc = shifted_values(f, j, &mv)) != SS_OK) return rc;
+            if ((rc = spmm_launch(s, mv, mv, nullptr, nullptr, x, k, y)) != SS_OK) return rc;
             ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, y, r);
             rhs = r;
         }
@@ -815,7 +837,6 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     cudaFreeAsync(r, st);
     cudaFreeAsync(y, st);
     cudaFreeAsync(x, st);
-    cudaFreeAsync(al, st);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }

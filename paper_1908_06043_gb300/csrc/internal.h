@@ -190,6 +190,8 @@ struct ss_numeric {
     std::vector<double *> linv;           // npanels * nb * nb, L11^-1 of each panel
     std::vector<double *> dblk;           // npanels * nb * 2: D diagonal, D sub-diagonal
     std::vector<int32_t *> piv;           // npanels * nb: local pivot order
+    std::vector<double *> mvals;          // values of A - sigma_j B on the pattern (made by the
+                                          // first refined solve of shift j), or null
     unsigned long long *d_counts = nullptr;   // per shift: neg, zero, pos, tiny
     std::vector<unsigned long long> h_counts;
     bool counts_valid = false;

@@ -176,6 +176,84 @@ def kmeans_shifts(values, n_s, uniforms, max_iter=1000):
     return np.sort(cent)
 
 
+def _nearest(x, cent):
+    return np.argmin(np.abs(x[:, None] - cent[None, :]), axis=1)
+
+
+def _lloyd_keep_order(x, cent, max_iter=1000):
+    """Lloyd steps from `cent` (order kept, empty clusters keep their centroid)."""
+    cent = np.array(cent, dtype=np.float64)
+    lab = _nearest(x, cent)
+    for _ in range(max_iter):
+        sums = np.bincount(lab, weights=x, minlength=cent.size)
+        cnts = np.bincount(lab, minlength=cent.size)
+        cent = np.where(cnts > 0, sums / np.maximum(cnts, 1), cent)
+        new = _nearest(x, cent)
+        if np.array_equal(new, lab):
+            break
+        lab = new
+    return cent, lab
+
+
+def kmeans_pp_seeds(values, n_s, uniforms):
+    """k-means++ starting centroids (Section 3.2): the first uniformly, each next one
+    with probability proportional to the squared distance to the nearest chosen one."""
+    x = np.asarray(values, dtype=np.float64)
+    n = x.size
+    seeds = [x[min(n - 1, int(uniforms[0] * n))]]
+    for c in range(1, n_s):
+        d2 = np.min((x[:, None] - np.asarray(seeds)[None, :]) ** 2, axis=1)
+        tot = d2.sum()
+        pick = (min(n - 1, int(uniforms[c] * n)) if tot <= 0
+                else min(n - 1, int(np.searchsorted(np.cumsum(d2) / tot, uniforms[c], side="right"))))
+        seeds.append(x[pick])
+    return np.asarray(seeds)
+
+
+def migrate_probes(values, owner, old_shifts, init):
+    """Move the probes of one SCF step to the next (Section 3.2).
+
+    The validated eigenvalues `values` (owner[i] = probe that produced values[i]) are
+    split into len(old_shifts) clusters by k-means started from `init`.  Every
+    non-empty cluster goes to the probe that produced most of its values (ties: nearest
+    old shift, then lower index); clusters sharing a probe merge.  A probe left without
+    a cluster is dropped and replaced: the largest cluster is split in two by 2-means
+    (started from its extreme values), its probe keeps the half with more of its own
+    values (ties: the half nearer its old shift) and a new probe takes the other half.
+    Returns [(shift, member indices)] sorted by shift, shift = mean of the members."""
+    x = np.asarray(values, dtype=np.float64)
+    owner = np.asarray(owner)
+    old = np.asarray(old_shifts, dtype=np.float64)
+    n_s = old.size
+    _, lab = _lloyd_keep_order(x, init)
+    owned = [[] for _ in range(n_s)]
+    for c in np.unique(lab):
+        idx = np.flatnonzero(lab == c)
+        votes = np.bincount(owner[idx], minlength=n_s)
+        top = np.flatnonzero(votes == votes.max())
+        mu = x[idx].mean()
+        owned[min(top, key=lambda q: (abs(old[q] - mu), q))].extend(idx.tolist())
+    groups = [(p, np.array(sorted(m))) for p, m in enumerate(owned) if m]
+    for _ in range(n_s - len(groups)):
+        g = max(range(len(groups)), key=lambda q: (groups[q][1].size, -q))
+        p, idx = groups[g]
+        v = x[idx]
+        if v.min() == v.max():
+            break
+        _, lab2 = _lloyd_keep_order(v, [v.min(), v.max()])
+        halves = [idx[lab2 == 0], idx[lab2 == 1]]
+
+        def rank(h):
+            if p < 0:
+                return (0, abs(x[h].mean() - x[idx].mean()))
+            return (-int(np.count_nonzero(owner[h] == p)), abs(x[h].mean() - old[p]))
+        keep = 0 if rank(halves[0]) <= rank(halves[1]) else 1
+        groups[g] = (p, halves[keep])
+        groups.append((-1, halves[1 - keep]))
+    out = [(float(x[m].mean()), m.tolist()) for _, m in groups]
+    return sorted(out, key=lambda t: t[0])
+
+
 # ----------------------------------------------------------------- solver
 @dataclass
 class SliceResult:
@@ -189,6 +267,7 @@ class SliceResult:
     probes: list
     rounds: int
     timings: dict = field(default_factory=dict)
+    owners: np.ndarray = None       # probe that produced each returned eigenpair
 
 
 class SliceSolver:
@@ -213,6 +292,12 @@ class SliceSolver:
         while self.count_below([lam_min])[0] > 0:
             lam_min -= 0.1 * span
         guess = model.root(n_e + 0.5, lo_t, hi_t)
+        return lam_min, self.bound_at_count(guess, n_e, lam_min, span)
+
+    def bound_at_count(self, guess: float, n_e: int, lam_min: float, span: float) -> float:
+        """A point lambda with nu(lambda) = n_e (mid-gap within 1e-3 span), bracketed from
+        `guess` and refined by bisection on inertia counts."""
+        hi_t = guess + span
         c = self.count_below([guess])[0]
         lo, hi = (lam_min, guess) if c > n_e else (guess, guess)
         step = 0.01 * span
@@ -232,10 +317,11 @@ class SliceSolver:
                 lo, clo = mid, cm
             else:
                 hi, c = mid, cm
-        return lam_min, lo
+        return lo
 
     def run(self, shifts, lam_min, lam_max, model: DosModel = None, k=None, V0=None, max_rounds=30,
-            block=64, seed=0, driver="subspace", iters_per_round=3, first_iters=80, splits=None, ks=None):
+            block=64, seed=0, driver="subspace", iters_per_round=3, first_iters=80, splits=None, ks=None,
+            warm=False):
         """Factor the shifts and the two region bounds in one batched call, build every
         probe, validate every slice, and refine the probes next to any slice that does
         not validate yet (fewer converged candidates than its exact count).
@@ -317,7 +403,7 @@ class SliceSolver:
                     # round and once at the end of a restart round: the iterated subspace
                     # does not depend on it
                     pr = fj.slice_solve(jj, lo, hi, v0, tol=self.tol, max_iter=mi, refine=self.refine,
-                                        n_expect=ne, allow_noconv=True, refine_from_start=Xs[j] is not None,
+                                        n_expect=ne, allow_noconv=True, refine_from_start=Xs[j] is not None or (warm and V0 is not None),
                                         check_every=2 if Xs[j] is None else mi)
                 probes[j] = pr
                 Xs[j] = pr.X
@@ -357,7 +443,8 @@ class SliceSolver:
         return SliceResult(list(shifts), lam_min, lam_max, lam[order], X, res[order], info, probes, rounds,
                            dict(factor_s=t_factor, solve_s=t_solve, total_s=time.perf_counter() - t0,
                                 iterations=iters, n_below_max=nneg_max, n_below_min=nneg_min,
-                                converged=not active, fp64_refactors=sorted(f64), quality=quality))
+                                converged=not active, fp64_refactors=sorted(f64), quality=quality),
+                           owners=np.array([sel[q][0] for q in order], dtype=np.int64))
 
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,
@@ -438,3 +525,59 @@ def default_basis_width(n_e: int, n_s: int) -> int:
     """k = 2 ceil(n_e / n_s) + 16 rounded up to a multiple of 16."""
     k = 2 * (-(-n_e // n_s)) + 16
     return -(-k // 16) * 16
+
+
+def _ceil16(x: float) -> int:
+    return int(-(-x // 16) * 16)
+
+
+def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precision: str = "mixed",
+                   tol: float = 1e-10, lanczos_steps: int = 100, n_vec: int = 4, seed: int = 0,
+                   start=None, uniforms=None):
+    """Lowest n_e eigenpairs of a sequence of pencils (A_i, B) on one pattern, as the SCF
+    loop of Alg. 1 produces them (Section 3.2).  Step 0 places the shifts from a Lanczos
+    DOS estimate.  Every later step migrates the probes: k-means of the previous step's
+    validated eigenvalues (k-means++ seeds after the DOS placement, the previous shifts
+    afterwards), then migrate_probes; each probe starts from the Ritz vectors of its
+    cluster, padded with random columns to 1.3x their number + 16.  The region keeps
+    nu(lambda_max) = n_e at every step (bisection on inertia from the previous bound).
+    start: N x n_vec device block of DOS start vectors (seeded N(0,1) if None);
+    uniforms: the n_s k-means++ uniforms (seeded if None).  Returns one SliceResult per
+    pencil; timings["migration"] records the shifts and cluster sizes chosen."""
+    n = sym.n
+    rng = np.random.default_rng(seed)
+    if uniforms is None:
+        uniforms = rng.random(n_s)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    results = []
+    for i, a_vals in enumerate(a_list):
+        solver = SliceSolver(sym, a_vals, b_vals, precision=precision, tol=tol)
+        if i == 0:
+            st = start if start is not None else torch.randn(n, n_vec, generator=g, device="cuda",
+                                                             dtype=torch.float64)
+            model = DosModel(n, sym.dos_estimate(a_vals, b_vals, lanczos_steps, st))
+            lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
+            lam_max = solver.bound_at_count(lam_max, n_e, lam_min, lam_max - lam_min)
+            res = solver.run(shifts, lam_min, lam_max, model, splits=splits, ks=ks, seed=seed)
+            res.timings["migration"] = None
+        else:
+            prev = results[-1]
+            init = kmeans_pp_seeds(prev.eigenvalues, n_s, uniforms) if i == 1 else np.asarray(prev.shifts)
+            groups = migrate_probes(prev.eigenvalues, prev.owners, prev.shifts, init)
+            shifts = [s_ for s_, _ in groups]
+            span = float(prev.lam_max - prev.lam_min)
+            lam_min = prev.lam_min
+            while solver.count_below([lam_min])[0] > 0:
+                lam_min -= 0.1 * span
+            lam_max = solver.bound_at_count(prev.lam_max, n_e, lam_min, span)
+            V0, ks = [], []
+            for _, m in groups:
+                kk = min(n, _ceil16(1.3 * len(m) + 16))
+                fill = torch.randn(n, kk - len(m), generator=g, device="cuda", dtype=torch.float64)
+                V0.append(torch.cat([prev.eigenvectors[:, m], fill], dim=1).contiguous())
+                ks.append(kk)
+            res = solver.run(shifts, lam_min, lam_max, None, V0=V0, ks=ks, seed=seed + i, warm=True)
+            res.timings["migration"] = dict(shifts=shifts, sizes=[len(m) for _, m in groups],
+                                            init="kmeans++" if i == 1 else "previous shifts")
+        results.append(res)
+    return results

@@ -80,3 +80,24 @@ def test_kmeans_matches_oracle():
     x = np.sort(np.concatenate([rng.normal(0, 0.1, 50), rng.normal(3, 0.2, 80), rng.normal(7, 0.1, 40)]))
     u = rng.random(3)
     assert np.allclose(kmeans_shifts(x, 3, u), opart.kmeans_shifts(x, 3, u), atol=1e-14)
+
+
+def test_migrate_probes_matches_oracle():
+    from oracle import partition
+    from paper_1908_06043_gb300.driver import kmeans_pp_seeds, migrate_probes
+    rng = np.random.default_rng(11)
+    for trial in range(40):
+        n_s = int(rng.integers(2, 9))
+        v = np.sort(np.concatenate([rng.normal(c, 0.2, int(rng.integers(1, 30)))
+                                    for c in rng.uniform(-5, 5, int(rng.integers(2, 8)))]))
+        old = np.sort(rng.uniform(v.min() - 2, v.max() + 2, n_s))
+        owner = np.searchsorted(0.5 * (old[1:] + old[:-1]), v)
+        u = rng.random(n_s)
+        seeds = kmeans_pp_seeds(v, n_s, u)
+        assert np.array_equal(seeds, partition.kmeans_pp_init(v, n_s, u))
+        for init in (old, seeds):
+            got = migrate_probes(v, owner, old, init)
+            ref = partition.migrate(v, owner, old, init)
+            assert len(got) == len(ref)
+            for (s1, m1), (s2, m2) in zip(got, ref):
+                assert m1 == m2 and abs(s1 - s2) <= 1e-12 * max(1.0, abs(s2))

@@ -1,0 +1,67 @@
+"""GPU parity of the whole slicing driver against the dense oracle: DOS shift placement,
+batched factorisation, probes and validation for the lowest n_e eigenpairs of one pencil,
+and the SCF-like pencil sequence with k-means probe migration (Section 3.2)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dense, partition, spectral
+from tests.gpu_util import setup
+from workloads.pencils import config_pencil, normal_block, scf_pencil, scf_sequence_perturbation
+
+pytestmark = pytest.mark.gpu
+
+
+def _check_lowest(p, res, n_e, tol=1e-10):
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    assert spectral.count_below(lam, res.lam_max) == n_e
+    assert spectral.count_below(lam, res.lam_min) == 0
+    assert res.eigenvalues.size == n_e
+    ref = lam[:n_e]
+    assert np.all(np.abs(res.eigenvalues - ref) <= 1e-10 * np.maximum(np.abs(ref), 1.0))
+    X = res.eigenvectors.cpu().numpy()
+    assert spectral.residual_norms(p, res.eigenvalues, X).max() <= tol
+    assert spectral.b_orthonormality_error(p, X) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config1_lowest_eigenpairs(gpu_lib, precision):
+    from paper_1908_06043_gb300.driver import DosModel, SliceSolver
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    start = torch.tensor(normal_block(p.n, 4, 1000), device="cuda")
+    model = DosModel(p.n, sym.dos_estimate(a, b, 100, start))
+    solver = SliceSolver(sym, a, b, precision=precision)
+    lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, 86, 4)
+    res = solver.run(shifts, lam_min, lam_max, model, splits=splits, ks=ks)
+    assert res.timings["converged"]
+    # the region holds n_e = 86 eigenvalues up to the DOS margin
+    _check_lowest(p, res, res.timings["n_below_max"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_scf_sequence_with_probe_migration(gpu_lib, precision):
+    # A_i = A_0 + 0.1 2^-i R, R seeded U(-1, 1) on A's pattern; the shifts of step i > 0
+    # come from k-means of step i-1's validated eigenvalues and must equal the oracle's
+    # migration of the same data; every step must reproduce the dense eigenvalues
+    from paper_1908_06043_gb300.driver import solve_sequence
+    p0 = config_pencil(1)
+    r = scf_sequence_perturbation(p0, seed=33)
+    pencils = [scf_pencil(p0, r, i) for i in range(3)]
+    ctx, sym, _, b = setup(gpu_lib, pencils[0])
+    a_list = [torch.tensor(q.a, device="cuda") for q in pencils]
+    uniforms = np.random.default_rng(7).random(4)
+    res = solve_sequence(sym, a_list, b, 86, 4, precision=precision, uniforms=uniforms,
+                         start=torch.tensor(normal_block(p0.n, 4, 1000), device="cuda"))
+    for i, (q, rs) in enumerate(zip(pencils, res)):
+        assert rs.timings["converged"], i
+        _check_lowest(q, rs, 86)
+        if i == 0:
+            continue
+        prev = res[i - 1]
+        init = partition.kmeans_pp_init(prev.eigenvalues, 4, uniforms) if i == 1 else np.asarray(prev.shifts)
+        ref = partition.migrate(prev.eigenvalues, prev.owners, prev.shifts, init)
+        got = rs.timings["migration"]["shifts"]
+        assert len(got) == len(ref)
+        assert np.allclose(got, [s for s, _ in ref], rtol=1e-12, atol=1e-12)
+        assert rs.timings["migration"]["sizes"] == [len(m) for _, m in ref]
