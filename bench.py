@@ -34,9 +34,9 @@ WORKLOADS = {
 }
 METRIC = "slice solves/s at N=110,592 (mixed vs FP64, resid<=1e-10); factor TFLOP/s"
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-FP64_ALU_PEAK_TFLOPS = 1.25                               # GB300 FP64 (nominal; no tensor-core FP64 path used)
-FLOP_CLASSES = {"schur", "panel", "fwd_update", "bwd_gather", "spmm", "gram", "gemm",
-                "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32"}
+FP64_ALU_PEAK_TFLOPS = 1.25                               # GB300 FP64 nominal: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz
+FLOP_CLASSES = {"schur", "panel", "fwd_update", "bwd_gather", "spmm", "gram", "gemm", "solve",
+                "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32", "solve_f32"}
 
 
 def parse():
@@ -210,6 +210,12 @@ def main():
         lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
         t1 = time.perf_counter()
         res = solver.run(shifts, lam_min, lam_max, model, seed=seed, splits=splits, ks=ks)
+        # band-energy gradient of the delivered eigenpairs (SDDMM on the stored pattern)
+        tg = time.perf_counter()
+        lam_d = torch.tensor(res.eigenvalues, device="cuda")
+        ga, gb = sym.band_energy_grad(res.eigenvectors, lam_d)
+        res.timings["grad"] = (ga, gb)
+        res.timings["grad_s"] = time.perf_counter() - tg
         if args.verbose:
             print(f"[step {precision} seed={seed}] dos+place {t1 - t0:.3f}s factor {res.timings['factor_s']:.3f}s "
                   f"probes {res.timings['solve_s']:.3f}s total {time.perf_counter() - t0:.3f}s rounds {res.rounds} "
@@ -319,7 +325,8 @@ def main():
         peak = FP32_ALU_PEAK_TFLOPS if f32 else FP64_ALU_PEAK_TFLOPS
         bound, unit = "alu", "TFLOP/s"
         peak_src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops/FMA x 2.07 GHz" if f32 else
-                    "nominal GB300 FP64 rate 1.25 TFLOP/s (CUDA-core FP64; not in MEASURED_PEAKS.json)")
+                    "nominal GB300 FP64 rate 1.25 TFLOP/s = 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz "
+                    "(CUDA-core FP64; MEASURED_PEAKS.json has no FP64 figure)")
     else:
         achieved, bound, unit, peak, peak_src = None, "unknown", None, None, None
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,

@@ -18,7 +18,7 @@ struct ss_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
-    int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
+    int solve_mode = SS_SOLVE_PER_STEP;       // how the triangular sweeps are launched
     GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
     int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)
     // per-class launch timing (ss_profile): event pairs recorded around launches
