@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--verbose", action="store_true")
+    ap.add_argument("--sequence", type=int, default=0,
+                    help="instead of the benchmark: solve this many pencils A_i = A_0 + 0.1 2^-i R of the "
+                         "workload with probe migration and print one JSON line per pencil")
     ap.add_argument("--only-probe", action="store_true",
                     help="profiling case: factor one shift of the workload and run its probe for 6 iterations")
     return ap.parse_args()
@@ -229,6 +232,33 @@ def main():
         ok = bool(res.timings["converged"]) and len(res.residuals) > 0 and float(res.residuals.max()) <= 1e-10
         ok = ok and all(n_conv >= n_exact for n_exact, _, n_conv, _ in res.slices)
         return ok
+
+    if args.sequence:
+        # SCF-like pencil sequence: DOS placement for the first pencil, k-means probe
+        # migration with warm starts afterwards; per-pencil wall time and iterations
+        from paper_1908_06043_gb300.driver import solve_sequence
+        from workloads.pencils import scf_pencil, scf_sequence_perturbation
+        r = scf_sequence_perturbation(p, seed=33)
+        a_list = [torch.tensor(scf_pencil(p, r, i).a, device="cuda") for i in range(args.sequence)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = solve_sequence(sym, a_list, b, n_e, n_s, precision=args.precision,
+                             start=torch.tensor(normal_block(p.n, n_vec, 1000), device="cuda"),
+                             uniforms=np.random.default_rng(7).random(n_s))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for i, rs in enumerate(res):
+            mig = rs.timings["migration"]
+            print(json.dumps({"sequence_step": i, "workload": wl["name"], "precision": args.precision,
+                              "seconds": rs.timings["total_s"], "factor_s": rs.timings["factor_s"],
+                              "rounds": rs.rounds, "probe_iterations": rs.timings["iterations"],
+                              "validated": check(rs), "eigenpairs": int(len(rs.eigenvalues)),
+                              "max_resid": float(rs.residuals.max()),
+                              "shifts": [float(x) for x in rs.shifts],
+                              "migration_init": mig["init"] if mig else "DOS placement",
+                              "cluster_sizes": mig["sizes"] if mig else None}), flush=True)
+        print(json.dumps({"sequence_total_s": t1 - t0, "pencils": len(res)}), flush=True)
+        return
 
     if args.only_probe:
         # one representative probe of the workload (shift 8 of the placement), for ncu; a

@@ -531,6 +531,36 @@ def _ceil16(x: float) -> int:
     return int(-(-x // 16) * 16)
 
 
+def migrated_windows(values, groups, lam_min: float, lam_max: float):
+    """Slice boundaries and basis widths for migrated probes (groups from
+    migrate_probes, sorted by shift), using the previous step's eigenvalues as the
+    spectrum estimate.  The boundary between two probes lies midway between the last
+    member of the lower probe and the first of the upper one (the midpoint of the shifts
+    if the member sets interleave); each basis covers the eigenvalues within the probe's
+    ball -- the largest distance from its shift to its window ends -- as in ball_partition.
+    Above lambda_max the count is extrapolated from the same distance below it."""
+    x = np.sort(np.asarray(values, dtype=np.float64))
+    sh = [s_ for s_, _ in groups]
+    ns = len(groups)
+    splits = [None]
+    for j in range(1, ns):
+        lo_m = float(np.max(np.asarray(values)[groups[j - 1][1]]))
+        hi_m = float(np.min(np.asarray(values)[groups[j][1]]))
+        t = 0.5 * (lo_m + hi_m)
+        splits.append(t if sh[j - 1] < t < sh[j] and lo_m < hi_m else 0.5 * (sh[j - 1] + sh[j]))
+    ks = []
+    for j in range(ns):
+        lo = lam_min if j == 0 else splits[j]
+        hi = lam_max if j == ns - 1 else splits[j + 1]
+        r = max(sh[j] - lo, hi - sh[j])
+        a, b = sh[j] - r, sh[j] + r
+        c = int(np.count_nonzero((x >= a) & (x <= b)))
+        if b > lam_max:
+            c += int(np.count_nonzero((x >= 2 * lam_max - b) & (x <= lam_max)))
+        ks.append(_ceil16(1.15 * c + 16))
+    return splits, ks
+
+
 def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precision: str = "mixed",
                    tol: float = 1e-10, lanczos_steps: int = 100, n_vec: int = 4, seed: int = 0,
                    start=None, uniforms=None):
@@ -539,7 +569,7 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
     DOS estimate.  Every later step migrates the probes: k-means of the previous step's
     validated eigenvalues (k-means++ seeds after the DOS placement, the previous shifts
     afterwards), then migrate_probes; each probe starts from the Ritz vectors of its
-    cluster, padded with random columns to 1.3x their number + 16.  The region keeps
+    cluster, padded with random columns to the basis width of migrated_windows.  The region keeps
     nu(lambda_max) = n_e at every step (bisection on inertia from the previous bound).
     start: N x n_vec device block of DOS start vectors (seeded N(0,1) if None);
     uniforms: the n_s k-means++ uniforms (seeded if None).  Returns one SliceResult per
@@ -570,13 +600,14 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
             while solver.count_below([lam_min])[0] > 0:
                 lam_min -= 0.1 * span
             lam_max = solver.bound_at_count(prev.lam_max, n_e, lam_min, span)
-            V0, ks = [], []
-            for _, m in groups:
-                kk = min(n, _ceil16(1.3 * len(m) + 16))
+            splits, ks = migrated_windows(prev.eigenvalues, groups, lam_min, lam_max)
+            V0 = []
+            for (_, m), kk in zip(groups, ks):
+                kk = min(n, max(kk, len(m) + 16))
                 fill = torch.randn(n, kk - len(m), generator=g, device="cuda", dtype=torch.float64)
                 V0.append(torch.cat([prev.eigenvectors[:, m], fill], dim=1).contiguous())
-                ks.append(kk)
-            res = solver.run(shifts, lam_min, lam_max, None, V0=V0, ks=ks, seed=seed + i, warm=True)
+            res = solver.run(shifts, lam_min, lam_max, None, V0=V0, ks=ks, splits=splits, seed=seed + i,
+                             warm=True)
             res.timings["migration"] = dict(shifts=shifts, sizes=[len(m) for _, m in groups],
                                             init="kmeans++" if i == 1 else "previous shifts")
         results.append(res)
