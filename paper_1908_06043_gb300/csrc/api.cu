@@ -517,7 +517,9 @@ static int solve_sweeps(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     const int cls = std::is_same<T, float>::value ? SS_K_SOLVE_F32 : SS_K_SOLVE;
-    if (!ctx->d_bar) SS_CUDA_TRY(ctx, cudaMalloc((void **)&ctx->d_bar, sizeof(GridBar)));
+    constexpr int kSmSlots = 1024;
+    if (!ctx->d_bar) SS_CUDA_TRY(ctx, cudaMalloc((void **)&ctx->d_bar, sizeof(GridBar) + sizeof(int32_t) * kSmSlots));
+    int32_t *sm_slots = reinterpret_cast<int32_t *>(ctx->d_bar + 1);
     int &per_sm = ctx->sweep_blocks_per_sm[std::is_same<T, float>::value ? 1 : 0];
     if (per_sm == 0) {
         SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_sweeps<T>, 256,
@@ -538,7 +540,7 @@ static int solve_sweeps(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
         SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&zall, sizeof(T) * zn, st));
         SS_CUDA_TRY(ctx, cudaMemsetAsync(zall, 0, sizeof(T) * zn, st));
     }
-    SS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBar), st));
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBar) + sizeof(int32_t) * kSmSlots, st));
     SweepArgs a{};
     a.lev = (const SweepLevel *)s->d_sweep_lev;
     a.nlev = (int32_t)s->solve_levels.size();
@@ -555,6 +557,8 @@ static int solve_sweeps(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     a.dinv = dinv;
     a.bar = ctx->d_bar;
     a.limit = 20000000;        // polls of about 64 ns: ~1 s per barrier
+    a.sm_slots = sm_slots;
+    a.nsm_slots = kSmSlots;
     void *args[] = {(void *)&a, (void *)&arena, (void *)&b, (void *)&zall};
     g_ss_launches.fetch_add(1, std::memory_order_relaxed);
     size_t slot = 0;

@@ -427,10 +427,37 @@ struct SweepArgs {
     const double *linv;
     const double *dblk;
     const int32_t *piv;
-    int32_t forward, backward, dinv, pad;
+    int32_t forward, backward, dinv, nsm_slots;
     GridBar *bar;
     long long limit;
+    int32_t *sm_slots;     // nsm_slots zeroed counters (blocks seen per SM id), or null
 };
+
+// Position of this block in the order (rank on its SM, SM id), so that the first items
+// of a step land on distinct SMs: a cooperative launch may place consecutive blocks on
+// the same SM, where small steps would then share one SM's FP64 units.  Falls back to
+// blockIdx.x when the SM ids exceed the counter array (the same for every block).
+__device__ __forceinline__ int spread_block_id(const SweepArgs &a, bool *ok) {
+    __shared__ int s_r, s_vb;
+    unsigned smid, nsmid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    const bool use = a.sm_slots != nullptr && (int)nsmid <= a.nsm_slots;
+    if (use && threadIdx.x == 0) s_r = atomicAdd(&a.sm_slots[smid], 1);
+    *ok = grid_barrier(a.bar, gridDim.x, a.limit);
+    if (!use || !*ok) return blockIdx.x;
+    if (threadIdx.x == 0) {
+        const int r = s_r;
+        int v = 0;
+        for (int q = 0; q < (int)nsmid; ++q) {
+            const int c = ((volatile int *)a.sm_slots)[q];
+            v += min(c, r) + ((q < (int)smid && c > r) ? 1 : 0);
+        }
+        s_vb = v;
+    }
+    __syncthreads();
+    return s_vb;
+}
 
 // Forward and/or backward sweep over every level in one cooperative launch.  The work
 // items of a step are spread over the resident blocks; a grid barrier separates
@@ -443,16 +470,19 @@ __global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__re
     const int k = a.k;
     const int nchunk = (k + KC - 1) / KC, ndchunk = (k + KD - 1) / KD;
     const unsigned nb = gridDim.x;
+    bool ok = true;
+    const int vb = spread_block_id(a, &ok);
+    if (!ok) return;
     if (a.forward) {
         for (int L = 0; L < a.nlev; ++L) {
             const SweepLevel lv = a.lev[L];
             const int32_t *lp = a.solve_panels + lv.panel_off;
-            for (int q = blockIdx.x; q < lv.count * ndchunk; q += nb)
+            for (int q = vb; q < lv.count * ndchunk; q += nb)
                 fwd_diag_item<T>(smem_raw, q % lv.count, q / lv.count, lp, a.panels, a.linv, a.piv, b, k);
             if (!grid_barrier(a.bar, nb, a.limit)) return;
             if (lv.row_tiles == 0) continue;
             const int32_t *tp = a.tile_pre + lv.panel_off;
-            for (int q = blockIdx.x; q < lv.row_tiles * nchunk; q += nb) {
+            for (int q = vb; q < lv.row_tiles * nchunk; q += nb) {
                 if constexpr (std::is_same<T, float>::value)
                     fwd_update_f32_item(smem_raw, q % lv.row_tiles, q / lv.row_tiles, lp, tp, lv.count, a.panels,
                                         a.idx, arena, b, k);
@@ -470,7 +500,7 @@ __global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__re
         T *z = zall + (int64_t)lv.panel_off * NB * k;
         if (lv.row_tiles > 0) {
             const int32_t *tp = a.tile_pre + lv.panel_off;
-            for (int q = blockIdx.x; q < lv.row_tiles * nchunk; q += nb) {
+            for (int q = vb; q < lv.row_tiles * nchunk; q += nb) {
                 if constexpr (std::is_same<T, float>::value)
                     bwd_gather_f32_item(smem_raw, q % lv.row_tiles, q / lv.row_tiles, lp, tp, lv.count, a.panels,
                                         a.idx, arena, b, k, z);
@@ -480,7 +510,7 @@ __global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__re
             }
             if (!grid_barrier(a.bar, nb, a.limit)) return;
         }
-        for (int q = blockIdx.x; q < lv.count * ndchunk; q += nb)
+        for (int q = vb; q < lv.count * ndchunk; q += nb)
             bwd_diag_item<T>(smem_raw, q % lv.count, q / lv.count, lp, a.panels, a.linv, a.dblk, a.piv, z,
                              lv.row_tiles > 0 ? 1 : 0, b, k, a.dinv);
         if (L > 0 && !grid_barrier(a.bar, nb, a.limit)) return;

@@ -365,6 +365,8 @@ class SliceSolver:
         Xs = [None] * ns
         f64 = {}                  # FP64 refactors of mixed shifts whose probes stalled
         stall = [0] * ns
+        restarts = [0] * ns
+        grown = [0] * ns
         best = [np.inf] * ns
         active = list(range(ns))
         rounds = 0
@@ -419,6 +421,16 @@ class SliceSolver:
                     if s_ < ns:
                         bad.add(s_)
             active = sorted(bad)
+            # a probe whose slice is still short after every 4th restart round gets a
+            # wider basis (+50 %, at least 16 random columns): its window holds more
+            # eigenvalues near sigma than the estimate it was sized from
+            for j in active:
+                restarts[j] += 1
+                if driver != "lanczos" and restarts[j] % 4 == 0 and Xs[j] is not None and Xs[j].shape[1] < n:
+                    extra = min(n - Xs[j].shape[1], max(16, Xs[j].shape[1] // 2))
+                    Xs[j] = torch.cat([Xs[j], torch.randn(n, extra, generator=g, device="cuda",
+                                                          dtype=torch.float64)], dim=1).contiguous()
+                    grown[j] += 1
             # a mixed-precision probe whose window residuals stop improving is moved to an
             # FP64 factor of its shift (the FP32 factor limits its accuracy)
             for j in active:
@@ -443,7 +455,8 @@ class SliceSolver:
         return SliceResult(list(shifts), lam_min, lam_max, lam[order], X, res[order], info, probes, rounds,
                            dict(factor_s=t_factor, solve_s=t_solve, total_s=time.perf_counter() - t0,
                                 iterations=iters, n_below_max=nneg_max, n_below_min=nneg_min,
-                                converged=not active, fp64_refactors=sorted(f64), quality=quality),
+                                converged=not active, fp64_refactors=sorted(f64), quality=quality,
+                                basis_growth=grown),
                            owners=np.array([sel[q][0] for q in order], dtype=np.int64))
 
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):

@@ -54,7 +54,8 @@ def test_scf_sequence_with_probe_migration(gpu_lib, precision):
     res = solve_sequence(sym, a_list, b, 86, 4, precision=precision, uniforms=uniforms,
                          start=torch.tensor(normal_block(p0.n, 4, 1000), device="cuda"))
     for i, (q, rs) in enumerate(zip(pencils, res)):
-        assert rs.timings["converged"], i
+        assert rs.timings["converged"], (i, rs.slices, rs.shifts, rs.timings["iterations"],
+                                         rs.timings["basis_growth"], rs.timings["migration"])
         _check_lowest(q, rs, 86)
         if i == 0:
             continue
