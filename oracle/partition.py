@@ -9,6 +9,19 @@ Test infrastructure only.  Readings where the paper is silent or garbled:
   (residual, probe index, Ritz index).
 * k-means++ draws its uniforms from an input array (one per centroid) so that both
   sides see the same random numbers.
+* DOSCluster (Alg. 3, Section 3.1): a grid point is a local maximiser of phi if it is
+  larger than its left neighbour and not smaller than its right one; an end point must
+  be larger than its single neighbour (a flat tail is no maximum); no maximiser counts
+  as one.  Between two maximisers
+  the minimiser is taken over the grid points strictly between them (the midpoint of
+  the two if there are none).  The refinement merges an interval with
+  gamma < merge_tol into the adjacent interval (sharing an end) with the fewer
+  estimated eigenvalues and reruns Alg. 3 on intervals with gamma > refine_tol at
+  n_omega' = ceil(2 C(l,u) / C(a,b) n_omega) points, at most `max_rounds` times.  The
+  safeguards split the interval with the most estimated eigenvalues at its CDOS median
+  and merge the interval with the fewest into its adjacent neighbour with fewer
+  (skipping intervals with no adjacent one).  Gaps left by removed intervals are
+  closed at their midpoints so that the intervals tile [a, b].
 * Probe update after clustering (Section 3.2): a cluster maps to the probe that
   produced most of its values (ties: the probe whose old shift is nearest the cluster
   centroid, then the lower index).  The 2-means split of the largest cluster starts
@@ -21,7 +34,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .dos import cdos_Phi
+from .dos import cdos_Phi, dos_phi, expectation_shift
 
 
 def bisect_root(f, lo, hi, target, rel=1e-12, maxit=200):
@@ -219,3 +232,115 @@ def migrate(values, owner, old_shifts, init_centroids):
     out = [(float(x[np.array(m)].mean()), m) for _, m in probes]
     out.sort(key=lambda t: t[0])
     return out
+
+
+def dos_cluster(n, runs, a, b, n_omega):
+    """Alg. 3: intervals of [a, b] around the local maxima of phi on n_omega grid points,
+    split at the minima between them; intervals without a Ritz value are dropped."""
+    S = a + (b - a) / (n_omega - 1) * np.arange(n_omega)
+    ph = dos_phi(S, n, runs)
+    maxi = []
+    for i in range(n_omega):
+        if i == 0:
+            is_max = ph[0] > ph[1]
+        else:
+            is_max = ph[i] > ph[i - 1] and (i == n_omega - 1 or ph[i] >= ph[i + 1])
+        if is_max:
+            maxi.append(i)
+    if len(maxi) <= 1:
+        return [(a, b)]
+    mu = [a]
+    for j in range(len(maxi) - 1):
+        lo_i, hi_i = maxi[j], maxi[j + 1]
+        if hi_i - lo_i >= 2:
+            inner = np.arange(lo_i + 1, hi_i)
+            mu.append(float(S[inner[np.argmin(ph[inner])]]))
+        else:
+            mu.append(0.5 * float(S[lo_i] + S[hi_i]))
+    mu.append(b)
+    theta = np.concatenate([th for th, _, _ in runs])
+    out = []
+    for j in range(len(mu) - 1):
+        l, u = mu[j], mu[j + 1]
+        if np.any((theta > l) & (theta <= u)) or (j == 0 and np.any(theta == l)):
+            out.append((l, u))
+    return out if out else [(a, b)]
+
+
+def _gamma(n, runs, l, u):
+    return float(cdos_Phi(u, n, runs)[0] - cdos_Phi(l, n, runs)[0])
+
+
+def _merge_small(n, runs, I, merge_tol):
+    """Refinement step 2: merge intervals holding fewer than merge_tol eigenvalues into
+    the adjacent interval with fewer eigenvalues (intervals without one stay)."""
+    changed = True
+    while changed:
+        changed = False
+        for j, (l, u) in enumerate(I):
+            if _gamma(n, runs, l, u) >= merge_tol:
+                continue
+            nb = []
+            if j > 0 and I[j - 1][1] == l:
+                nb.append(j - 1)
+            if j + 1 < len(I) and I[j + 1][0] == u:
+                nb.append(j + 1)
+            if not nb:
+                continue
+            t = min(nb, key=lambda q: (_gamma(n, runs, *I[q]), q))
+            lo, hi = min(I[t][0], l), max(I[t][1], u)
+            I = [iv for q, iv in enumerate(I) if q not in (j, t)]
+            I.append((lo, hi))
+            I.sort()
+            changed = True
+            break
+    return I
+
+
+def dos_cluster_partition(n, runs, a, b, n_s, n_omega, merge_tol=2.0, refine_tol=50.0, max_rounds=20):
+    """Cluster intervals of Alg. 3 with the refinement strategy and the safeguards that
+    give exactly n_s intervals (Section 3.1); returns (intervals, expectation shifts)."""
+    C_ab = _gamma(n, runs, a, b)
+    I = dos_cluster(n, runs, a, b, n_omega)
+    done = set()
+    for _ in range(max_rounds):
+        I = _merge_small(n, runs, I, merge_tol)
+        new = []
+        grew = False
+        for (l, u) in I:
+            g = _gamma(n, runs, l, u)
+            if g > refine_tol and (l, u) not in done:
+                done.add((l, u))
+                m = max(3, int(np.ceil(2.0 * g / C_ab * n_omega)))
+                sub = dos_cluster(n, runs, l, u, m)
+                if len(sub) >= 2:
+                    new.extend(sub)
+                    grew = True
+                    continue
+            new.append((l, u))
+        I = sorted(new)
+        if not grew:
+            break
+    # close the gaps left by dropped intervals at their midpoints
+    tiled = []
+    for j, (l, u) in enumerate(I):
+        lo = a if j == 0 else 0.5 * (I[j - 1][1] + l)
+        hi = b if j == len(I) - 1 else 0.5 * (u + I[j + 1][0])
+        tiled.append((lo, hi))
+    I = tiled
+    while len(I) < n_s:
+        j = max(range(len(I)), key=lambda q: (_gamma(n, runs, *I[q]), -q))
+        l, u = I[j]
+        target = 0.5 * (float(cdos_Phi(l, n, runs)[0]) + float(cdos_Phi(u, n, runs)[0]))
+        m = bisect_root(lambda w: float(cdos_Phi(w, n, runs)[0]), l, u, target)
+        I[j:j + 1] = [(l, m), (m, u)]
+    while len(I) > n_s:
+        order = sorted(range(len(I)), key=lambda q: (_gamma(n, runs, *I[q]), q))
+        j = order[0]
+        nb = [q for q in (j - 1, j + 1) if 0 <= q < len(I)]
+        t = min(nb, key=lambda q: (_gamma(n, runs, *I[q]), q))
+        lo, hi = min(I[t][0], I[j][0]), max(I[t][1], I[j][1])
+        I = [iv for q, iv in enumerate(I) if q not in (j, t)] + [(lo, hi)]
+        I.sort()
+    shifts = [expectation_shift(l, u, n, runs) for l, u in I]
+    return I, shifts

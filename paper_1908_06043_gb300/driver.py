@@ -109,6 +109,94 @@ def cdos_partition(model: DosModel, a: float, b: float, n_s: int):
     return iv, shifts
 
 
+def dos_clusters(model: DosModel, a: float, b: float, n_omega: int):
+    """Alg. 3 (DOSCluster): cut [a, b] at the DOS minima between its local maxima on an
+    n_omega-point grid and keep the pieces that hold a Lanczos Ritz value."""
+    grid = np.linspace(a, b, n_omega)
+    grid[0], grid[-1] = a, b
+    f = model.phi(grid)
+    up = np.empty(n_omega, dtype=bool)
+    up[0] = f[0] > f[1]
+    up[1:] = f[1:] > f[:-1]
+    down = np.ones(n_omega, dtype=bool)
+    down[1:-1] = f[1:-1] >= f[2:]
+    peaks = np.flatnonzero(up & down)
+    if peaks.size <= 1:
+        return [(a, b)]
+    cuts = [a]
+    for p0, p1 in zip(peaks[:-1], peaks[1:]):
+        if p1 - p0 >= 2:
+            cuts.append(float(grid[p0 + 1 + int(np.argmin(f[p0 + 1:p1]))]))
+        else:
+            cuts.append(0.5 * float(grid[p0] + grid[p1]))
+    cuts.append(b)
+    ritz = np.concatenate([th for th, _, _ in model.runs])
+    keep = [(cuts[j], cuts[j + 1]) for j in range(len(cuts) - 1)
+            if np.any((ritz > cuts[j]) & (ritz <= cuts[j + 1])) or (j == 0 and np.any(ritz == cuts[0]))]
+    return keep or [(a, b)]
+
+
+def dos_cluster_partition(model: DosModel, a: float, b: float, n_s: int, n_omega: int,
+                          merge_tol: float = 2.0, refine_tol: float = 50.0, max_rounds: int = 20):
+    """Shift placement for clustered spectra (Section 3.1): Alg. 3 on a coarse grid;
+    intervals holding fewer than merge_tol estimated eigenvalues join their adjacent
+    neighbour with fewer; intervals holding more than refine_tol are searched again at
+    2 C(l,u)/C(a,b) times the resolution until nothing splits; then gaps are closed at
+    their midpoints and intervals are split at their CDOS median (largest first) or
+    merged (smallest first, into the adjacent neighbour with fewer) until there are
+    exactly n_s.  Returns (intervals, expectation shifts of Eq. 7)."""
+    def count(iv):
+        return float(model.Phi(iv[1])[0] - model.Phi(iv[0])[0])
+
+    total = count((a, b))
+    ivs = dos_clusters(model, a, b, n_omega)
+    searched = set()
+    for _ in range(max_rounds):
+        merged = True
+        while merged:                       # step 2
+            merged = False
+            for j, iv in enumerate(ivs):
+                if count(iv) >= merge_tol:
+                    continue
+                adj = [q for q in (j - 1, j + 1) if 0 <= q < len(ivs)
+                       and (ivs[q][1] == iv[0] if q < j else ivs[q][0] == iv[1])]
+                if not adj:
+                    continue
+                t = min(adj, key=lambda q: (count(ivs[q]), q))
+                joined = (min(ivs[t][0], iv[0]), max(ivs[t][1], iv[1]))
+                ivs = sorted([x for q, x in enumerate(ivs) if q not in (j, t)] + [joined])
+                merged = True
+                break
+        out, split = [], False              # steps 3 and 4
+        for iv in ivs:
+            c = count(iv)
+            if c > refine_tol and iv not in searched:
+                searched.add(iv)
+                sub = dos_clusters(model, iv[0], iv[1], max(3, int(math.ceil(2.0 * c / total * n_omega))))
+                if len(sub) >= 2:
+                    out += sub
+                    split = True
+                    continue
+            out.append(iv)
+        ivs = sorted(out)
+        if not split:
+            break
+    m = len(ivs)
+    ivs = [((a if j == 0 else 0.5 * (ivs[j - 1][1] + ivs[j][0])),
+            (b if j == m - 1 else 0.5 * (ivs[j][1] + ivs[j + 1][0]))) for j in range(m)]
+    while len(ivs) < n_s:
+        j = max(range(len(ivs)), key=lambda q: (count(ivs[q]), -q))
+        lo, hi = ivs[j]
+        mid = model.root(0.5 * float(model.Phi(lo)[0] + model.Phi(hi)[0]), lo, hi)
+        ivs[j:j + 1] = [(lo, mid), (mid, hi)]
+    while len(ivs) > n_s:
+        j = min(range(len(ivs)), key=lambda q: (count(ivs[q]), q))
+        t = min([q for q in (j - 1, j + 1) if 0 <= q < len(ivs)], key=lambda q: (count(ivs[q]), q))
+        joined = (min(ivs[t][0], ivs[j][0]), max(ivs[t][1], ivs[j][1]))
+        ivs = sorted([x for q, x in enumerate(ivs) if q not in (j, t)] + [joined])
+    return ivs, [model.expectation(l, u) for l, u in ivs]
+
+
 # ----------------------------------------------------------------- validation
 def validate(shifts, lam_min, lam_max, probes, nneg_shift, nneg_min, nneg_max, tol, taus=None):
     """Section 2.2.  probes[j] = (theta, resid); taus[s] (optional) is the point that
@@ -462,8 +550,8 @@ class SliceSolver:
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,
         lambda_max at Phi = (1 + margin) n_e + 1, and n_s intervals between them, by the
-        CDOS roots of Eq. 6 with expectation shifts (mode "cdos") or by ball_partition
-        (mode "ball").  Returns (lambda_min, lambda_max, shifts, splits, basis sizes):
+        CDOS roots of Eq. 6 with expectation shifts (mode "cdos"), by DOSCluster (Alg. 3,
+        mode "cluster") or by ball_partition (mode "ball").  Returns (lambda_min, lambda_max, shifts, splits, basis sizes):
         splits[s] divides slice s between probes s-1 and s (None: the midpoints)."""
         lo_t, hi_t = model.theta_range()
         lam_min = lo_t
@@ -471,6 +559,16 @@ class SliceSolver:
         if mode == "cdos":
             _, shifts = cdos_partition(model, lam_min, lam_max, n_s)
             return lam_min, lam_max, shifts, None, None
+        if mode == "cluster":
+            # DOSCluster intervals (Alg. 3 with refinement), expectation shifts; each basis
+            # covers the estimated eigenvalues within its shift's distance to the far end
+            n_om = 10 * max(len(th) for th, _, _ in model.runs)
+            iv, shifts = dos_cluster_partition(model, lam_min, lam_max, n_s, n_om)
+            ks = []
+            for s_, (l, u) in zip(shifts, iv):
+                r = max(s_ - l, u - s_)
+                ks.append(int(-(-(1.15 * float(model.Phi(s_ + r)[0] - model.Phi(s_ - r)[0]) + 16) // 16) * 16))
+            return lam_min, lam_max, shifts, [None] + [iv[j][0] for j in range(1, n_s)], ks
         iv, shifts, balls = ball_partition(model, lam_min, lam_max, n_s)
         splits = [None] + [iv[j][0] for j in range(1, n_s)]
         ks = [int(-(-(1.15 * bc + 16) // 16) * 16) for bc in balls]

@@ -101,3 +101,28 @@ def test_migrate_probes_matches_oracle():
             assert len(got) == len(ref)
             for (s1, m1), (s2, m2) in zip(got, ref):
                 assert m1 == m2 and abs(s1 - s2) <= 1e-12 * max(1.0, abs(s2))
+
+
+def test_dos_cluster_partition_matches_oracle():
+    from oracle import partition
+    from oracle.dos import gaussian_widths
+    from paper_1908_06043_gb300.driver import DosModel, dos_cluster_partition, dos_clusters
+    rng = np.random.default_rng(12)
+    for trial in range(12):
+        centres = np.sort(rng.uniform(-10, 10, int(rng.integers(1, 6))))
+        theta = np.sort(np.concatenate([c + rng.uniform(0.02, 0.5) * rng.standard_normal(int(rng.integers(3, 25)))
+                                        for c in centres]))
+        z2 = rng.random(theta.size)
+        z2 /= z2.sum()
+        n = int(rng.integers(200, 5000))
+        model = DosModel(n, [(theta, z2)])
+        runs = [(theta, z2, gaussian_widths(theta))]
+        a, b = theta[0] - 1.0, theta[-1] + 1.0
+        n_om = 10 * theta.size
+        assert dos_clusters(model, a, b, n_om) == partition.dos_cluster(n, runs, a, b, n_om)
+        for n_s in (1, 3, 8):
+            I1, s1 = dos_cluster_partition(model, a, b, n_s, n_om)
+            I2, s2 = partition.dos_cluster_partition(n, runs, a, b, n_s, n_om)
+            assert len(I1) == len(I2) == n_s
+            assert np.allclose(np.array(I1), np.array(I2), rtol=1e-9, atol=1e-9)
+            assert np.allclose(s1, s2, rtol=1e-9, atol=1e-9)

@@ -66,3 +66,18 @@ def test_scf_sequence_with_probe_migration(gpu_lib, precision):
         assert len(got) == len(ref)
         assert np.allclose(got, [s for s, _ in ref], rtol=1e-12, atol=1e-12)
         assert rs.timings["migration"]["sizes"] == [len(m) for _, m in ref]
+
+
+def test_config1_dos_cluster_placement(gpu_lib):
+    # Alg. 3 placement (clusters of the DOS, expectation shifts) through the whole driver
+    from paper_1908_06043_gb300.driver import DosModel, SliceSolver
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    start = torch.tensor(normal_block(p.n, 4, 1000), device="cuda")
+    model = DosModel(p.n, sym.dos_estimate(a, b, 100, start))
+    solver = SliceSolver(sym, a, b, precision="fp64")
+    lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, 86, 4, mode="cluster")
+    assert len(shifts) == 4 and all(lam_min < s_ < lam_max for s_ in shifts)
+    res = solver.run(shifts, lam_min, lam_max, model, splits=splits, ks=ks)
+    assert res.timings["converged"]
+    _check_lowest(p, res, res.timings["n_below_max"])

@@ -118,3 +118,70 @@ def test_migration_invariants_random():
         assert sorted(i for _, m in out for i in m) == list(range(v.size))
         for s, m in out:
             assert len(m) > 0 and abs(s - v[m].mean()) < 1e-12
+
+
+def _runs(theta, weights):
+    from oracle.dos import gaussian_widths
+    theta = np.asarray(theta, dtype=np.float64)
+    z2 = np.asarray(weights, dtype=np.float64)
+    return [(theta, z2 / z2.sum(), gaussian_widths(theta))]
+
+
+def test_dos_cluster_finds_separated_clusters():
+    # three groups of Ritz values far apart: Alg. 3 returns one interval per group,
+    # split at the DOS minima between them
+    centres = [-10.0, 0.0, 10.0]
+    theta = np.concatenate([c + 0.1 * np.arange(5) for c in centres])
+    runs = _runs(theta, np.ones(theta.size))
+    I = partition.dos_cluster(1500, runs, -12.0, 12.0, 10 * theta.size)
+    assert len(I) == 3
+    for (l, u), c in zip(I, centres):
+        assert l < c and c + 0.4 < u
+    assert I[0][1] < -2.0 and 2.0 < I[1][1] < 8.0
+
+
+def test_dos_cluster_single_maximum_returns_whole_interval():
+    theta = np.linspace(-1.0, 1.0, 9)
+    w = np.exp(-theta ** 2)                     # one smooth bump
+    runs = [(theta, w / w.sum(), np.full(theta.size, 1.0))]
+    assert partition.dos_cluster(100, runs, -3.0, 3.0, 50) == [(-3.0, 3.0)]
+
+
+def test_dos_cluster_drops_intervals_without_ritz_values():
+    # two narrow peaks inside [a, b] and a third maximum created only by a Ritz value
+    # outside [a, b]: the interval holding no Ritz value is removed
+    theta = np.array([-5.0, -4.9, 5.0, 5.1, 30.0])
+    runs = [(theta, np.full(5, 0.2), np.array([0.05, 0.05, 0.05, 0.05, 12.0]))]
+    I = partition.dos_cluster(100, runs, -8.0, 20.0, 281)
+    theta_in = theta[theta <= 20.0]
+    for l, u in I:
+        assert np.any((theta_in > l) & (theta_in <= u))
+    assert len(I) == 2
+
+
+def test_dos_cluster_partition_exact_count_and_tiling():
+    rng = np.random.default_rng(8)
+    centres = [-8.0, -3.0, 0.0, 6.0]
+    theta = np.sort(np.concatenate([c + 0.2 * rng.standard_normal(20) for c in centres]))
+    runs = _runs(theta, np.ones(theta.size))
+    for n_s in (2, 4, 7, 12):
+        I, sh = partition.dos_cluster_partition(4000, runs, -10.0, 8.0, n_s, 10 * theta.size)
+        assert len(I) == n_s and len(sh) == n_s
+        assert I[0][0] == -10.0 and I[-1][1] == 8.0
+        for j in range(n_s - 1):
+            assert I[j][1] == I[j + 1][0]
+        for (l, u), s in zip(I, sh):
+            assert l < s < u
+
+
+def test_dos_cluster_refinement_separates_close_clusters():
+    # two dense clusters 0.3 apart hold ~1000 eigenvalues each; a 12-point grid sees one
+    # bump, the refined search on the over-full interval separates them
+    theta = np.concatenate([0.01 * np.arange(10), 0.3 + 0.01 * np.arange(10), [5.0]])
+    w = np.concatenate([np.ones(20), [0.05]])
+    runs = [(theta, w / w.sum(), np.full(theta.size, 0.02))]
+    coarse = partition.dos_cluster(2000, runs, -1.0, 6.0, 12)
+    assert len(coarse) <= 2 and coarse[0][0] == -1.0 and coarse[0][1] > 0.4
+    I, _ = partition.dos_cluster_partition(2000, runs, -1.0, 6.0, 3, 12)
+    cuts = [u for _, u in I[:-1]]
+    assert any(0.09 < c < 0.3 for c in cuts)        # between the two clusters
