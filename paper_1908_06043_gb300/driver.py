@@ -468,7 +468,7 @@ class SliceSolver:
                 lo, hi = windows[j]
                 if driver == "lanczos":
                     if Xs[j] is None:
-                        v0 = V0[j] if V0 is not None else torch.randn(n, min(block, n), generator=g, device="cuda",
+                        v0 = V0[j] if V0 is not None and V0[j] is not None else torch.randn(n, min(block, n), generator=g, device="cuda",
                                                                      dtype=torch.float64)
                         mb = min(m1[j], max(1, n // v0.shape[1]))
                     else:
@@ -480,7 +480,7 @@ class SliceSolver:
                     kk = k or (ks[j] if ks is not None else min(n, -(-(2 * cnt[j] + 16) // 16) * 16))
                     kk = min(n, max(kk, -(-(cnt[j] + 16) // 16) * 16))
                     if Xs[j] is None:
-                        v0 = V0[j] if V0 is not None else torch.randn(n, kk, generator=g, device="cuda",
+                        v0 = V0[j] if V0 is not None and V0[j] is not None else torch.randn(n, kk, generator=g, device="cuda",
                                                                      dtype=torch.float64)
                         # stop the first round at 80% of the window's estimated count;
                         # validation then tops up with short rounds
@@ -493,7 +493,7 @@ class SliceSolver:
                     # round and once at the end of a restart round: the iterated subspace
                     # does not depend on it
                     pr = fj.slice_solve(jj, lo, hi, v0, tol=self.tol, max_iter=mi, refine=self.refine,
-                                        n_expect=ne, allow_noconv=True, refine_from_start=Xs[j] is not None or (warm and V0 is not None),
+                                        n_expect=ne, allow_noconv=True, refine_from_start=Xs[j] is not None or (warm and V0 is not None and V0[j] is not None),
                                         check_every=2 if Xs[j] is None else mi)
                 probes[j] = pr
                 Xs[j] = pr.X
@@ -546,6 +546,40 @@ class SliceSolver:
                                 converged=not active, fp64_refactors=sorted(f64), quality=quality,
                                 basis_growth=grown),
                            owners=np.array([sel[q][0] for q in order], dtype=np.int64))
+
+    def run_with_recovery(self, shifts, lam_min, lam_max, model: DosModel = None, max_inserts: int = 2,
+                          **kw):
+        """run(), then recovery of missing eigenvalues (Section 3.3): while some slice
+        holds fewer converged eigenpairs than its inertia count, new probes are inserted
+        in each such slice (two placed in it by ball_partition on the DOS, else one at its
+        midpoint) and the probes run again, the old ones restarted from their Ritz
+        vectors.  Returns
+        the last SliceResult; timings["inserted"] lists the shifts added per attempt."""
+        res = self.run(shifts, lam_min, lam_max, model, **kw)
+        inserted = []
+        shifts = list(shifts)
+        while not res.timings["converged"] and len(inserted) < max_inserts:
+            ns = len(shifts)
+            add = []
+            for s_, (n_exact, _, n_conv, _) in enumerate(res.slices):
+                if n_conv >= n_exact:
+                    continue
+                lo = lam_min if s_ == 0 else shifts[s_ - 1]
+                hi = lam_max if s_ == ns else shifts[s_]
+                if model is not None:               # two probes placed in the slice by the DOS
+                    add += [x for x in ball_partition(model, lo, hi, 2)[1] if lo < x < hi]
+                else:
+                    add.append(0.5 * (lo + hi))
+            inserted.append(add)
+            old = {sh: pr.X for sh, pr in zip(shifts, res.probes)}
+            shifts = sorted(shifts + add)
+            V0 = [old.get(sh) for sh in shifts]
+            kw2 = dict(kw)
+            kw2.pop("splits", None)
+            kw2.pop("ks", None)
+            res = self.run(shifts, lam_min, lam_max, model, V0=V0, warm=True, **kw2)
+        res.timings["inserted"] = inserted
+        return res
 
     def place_shifts(self, model: DosModel, n_e: int, n_s: int, margin: float = 0.01, mode: str = "ball"):
         """Region and shifts from the DOS alone: lambda_min below every Ritz value,
@@ -674,7 +708,7 @@ def migrated_windows(values, groups, lam_min: float, lam_max: float):
 
 def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precision: str = "mixed",
                    tol: float = 1e-10, lanczos_steps: int = 100, n_vec: int = 4, seed: int = 0,
-                   start=None, uniforms=None):
+                   start=None, uniforms=None, eta_tol: float = np.inf):
     """Lowest n_e eigenpairs of a sequence of pencils (A_i, B) on one pattern, as the SCF
     loop of Alg. 1 produces them (Section 3.2).  Step 0 places the shifts from a Lanczos
     DOS estimate.  Every later step migrates the probes: k-means of the previous step's
@@ -683,27 +717,44 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
     cluster, padded with random columns to the basis width of migrated_windows.  The region keeps
     nu(lambda_max) = n_e at every step (bisection on inertia from the previous bound).
     start: N x n_vec device block of DOS start vectors (seeded N(0,1) if None);
-    uniforms: the n_s k-means++ uniforms (seeded if None).  Returns one SliceResult per
-    pencil; timings["migration"] records the shifts and cluster sizes chosen."""
+    uniforms: the n_s k-means++ uniforms (seeded if None).  Every step recovers missing
+    eigenvalues by probe insertion (Section 3.3).  eta_tol: relative change of
+    Tr(X^T A X) over the previous eigenvectors (Eq. 9) above which a step is placed from a
+    new DOS estimate instead of by migration (inf: never).  Returns one SliceResult per
+    pencil; timings["migration"] records the shifts and cluster sizes chosen and
+    timings["eta"] the monitor's (old, new, changed)."""
     n = sym.n
     rng = np.random.default_rng(seed)
+    etas = []
     if uniforms is None:
         uniforms = rng.random(n_s)
     g = torch.Generator(device="cuda").manual_seed(seed)
     results = []
     for i, a_vals in enumerate(a_list):
         solver = SliceSolver(sym, a_vals, b_vals, precision=precision, tol=tol)
-        if i == 0:
+        redo_dos = i == 0
+        if i > 0:
+            # eta monitor (Eq. 9): Tr(X^T A X) over the previous eigenvectors under the old
+            # and the new A; a relative change above eta_tol sends this step back to a DOS
+            # placement instead of migration
+            prev = results[-1]
+            eta_old = float(np.sum(prev.eigenvalues))
+            eta_new = trace_form(sym, a_vals, prev.eigenvectors)
+            changed = abs(eta_new - eta_old) > eta_tol * max(1.0, abs(eta_old))
+            etas.append((eta_old, eta_new, changed))
+            redo_dos = changed
+        if redo_dos:
             st = start if start is not None else torch.randn(n, n_vec, generator=g, device="cuda",
                                                              dtype=torch.float64)
             model = DosModel(n, sym.dos_estimate(a_vals, b_vals, lanczos_steps, st))
             lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
             lam_max = solver.bound_at_count(lam_max, n_e, lam_min, lam_max - lam_min)
-            res = solver.run(shifts, lam_min, lam_max, model, splits=splits, ks=ks, seed=seed)
+            res = solver.run_with_recovery(shifts, lam_min, lam_max, model, splits=splits, ks=ks, seed=seed)
             res.timings["migration"] = None
         else:
             prev = results[-1]
-            init = kmeans_pp_seeds(prev.eigenvalues, n_s, uniforms) if i == 1 else np.asarray(prev.shifts)
+            after_dos = prev.timings["migration"] is None
+            init = kmeans_pp_seeds(prev.eigenvalues, n_s, uniforms) if after_dos else np.asarray(prev.shifts)
             groups = migrate_probes(prev.eigenvalues, prev.owners, prev.shifts, init)
             shifts = [s_ for s_, _ in groups]
             span = float(prev.lam_max - prev.lam_min)
@@ -717,9 +768,16 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
                 kk = min(n, max(kk, len(m) + 16))
                 fill = torch.randn(n, kk - len(m), generator=g, device="cuda", dtype=torch.float64)
                 V0.append(torch.cat([prev.eigenvectors[:, m], fill], dim=1).contiguous())
-            res = solver.run(shifts, lam_min, lam_max, None, V0=V0, ks=ks, splits=splits, seed=seed + i,
-                             warm=True)
+            res = solver.run_with_recovery(shifts, lam_min, lam_max, None, V0=V0, ks=ks, splits=splits,
+                                           seed=seed + i, warm=True)
             res.timings["migration"] = dict(shifts=shifts, sizes=[len(m) for _, m in groups],
-                                            init="kmeans++" if i == 1 else "previous shifts")
+                                            init="kmeans++" if after_dos else "previous shifts")
+        res.timings["eta"] = etas[-1] if i > 0 else None
         results.append(res)
     return results
+
+
+def trace_form(sym: api.Symbolic, a_vals, X) -> float:
+    """eta(X, A) = Tr(X^T A X) (Eq. 9), A X by the library's SpMM."""
+    AX = sym.spmm(a_vals, None, X)
+    return float((X * AX).sum().item())

@@ -60,7 +60,8 @@ def test_scf_sequence_with_probe_migration(gpu_lib, precision):
         if i == 0:
             continue
         prev = res[i - 1]
-        init = partition.kmeans_pp_init(prev.eigenvalues, 4, uniforms) if i == 1 else np.asarray(prev.shifts)
+        after_dos = prev.timings["migration"] is None
+        init = partition.kmeans_pp_init(prev.eigenvalues, 4, uniforms) if after_dos else np.asarray(prev.shifts)
         ref = partition.migrate(prev.eigenvalues, prev.owners, prev.shifts, init)
         got = rs.timings["migration"]["shifts"]
         assert len(got) == len(ref)
@@ -81,3 +82,36 @@ def test_config1_dos_cluster_placement(gpu_lib):
     res = solver.run(shifts, lam_min, lam_max, model, splits=splits, ks=ks)
     assert res.timings["converged"]
     _check_lowest(p, res, res.timings["n_below_max"])
+
+
+def test_missing_eigenvalues_recovered_by_probe_insertion(gpu_lib):
+    # host-side fault injection (Section 3.3): all four shifts misplaced at the top of the
+    # region and too few rounds for the low slices; validation reports missing
+    # eigenvalues and the inserted probes recover them
+    from paper_1908_06043_gb300.driver import DosModel, SliceSolver
+    p = config_pencil(1)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    start = torch.tensor(normal_block(p.n, 4, 1000), device="cuda")
+    model = DosModel(p.n, sym.dos_estimate(a, b, 100, start))
+    solver = SliceSolver(sym, a, b, precision="fp64")
+    lam_min = float(lam[0]) - 1.0
+    lam_max = 0.5 * float(lam[85] + lam[86])
+    shifts = list(0.5 * (lam[[80, 82, 83]] + lam[[81, 83, 84]])) + [0.5 * float(lam[84] + lam[85])]
+    res = solver.run_with_recovery(shifts, lam_min, lam_max, model, max_inserts=4, max_rounds=8)
+    assert res.timings["inserted"] and len(res.shifts) > 4     # the first attempt missed some
+    assert res.timings["converged"], (res.slices, res.timings["inserted"])
+    _check_lowest(p, res, 86)
+
+
+def test_eta_monitor_trace_form(gpu_lib):
+    # Eq. 9: Tr(X^T A X) of the library's SpMM against the dense form, and for
+    # B-orthonormal eigenvectors equal to the sum of their eigenvalues
+    from paper_1908_06043_gb300.driver import trace_form
+    p = config_pencil(1)
+    lam, X = dense.gen_eig(p.dense("a"), p.dense("b"))
+    ctx, sym, a, b = setup(gpu_lib, p)
+    Xd = torch.tensor(np.ascontiguousarray(X[:, :86]), device="cuda")
+    eta = trace_form(sym, a, Xd)
+    assert abs(eta - float(np.trace(X[:, :86].T @ p.dense("a") @ X[:, :86]))) <= 1e-10 * abs(eta)
+    assert abs(eta - float(lam[:86].sum())) <= 1e-9 * max(1.0, abs(eta))
