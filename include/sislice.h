@@ -120,11 +120,11 @@ const char *ss_last_error(const ss_ctx *ctx);
 
 /* How the level-scheduled triangular sweeps of every solve (ss_solve, the probes of
  * ss_slice_solve, the DOS Lanczos) are launched -- an implementation choice with no
- * paper counterpart.  SS_SOLVE_PER_STEP (default): one launch per level and step;
- * SS_SOLVE_SWEEP_KERNEL: one cooperative launch per solve that walks all levels with a
- * bounded grid barrier between steps (a barrier that waits about 1 s makes the solve
- * return SS_ERR_TIMEOUT).  Both compute the same sums; the atomics make the rounding
- * order differ.  ss_solve_noalloc always launches per step.  Errors: SS_ERR_ARG. */
+ * paper counterpart.  SS_SOLVE_SWEEP_KERNEL (default): one cooperative launch per solve
+ * that walks all levels with a bounded grid barrier between steps (a barrier that waits
+ * about 1 s makes the solve return SS_ERR_TIMEOUT); SS_SOLVE_PER_STEP: one launch per
+ * level and step.  Both compute the same sums; the atomics make the rounding order
+ * differ.  ss_solve_noalloc always launches per step.  Errors: SS_ERR_ARG. */
 enum { SS_SOLVE_SWEEP_KERNEL = 0, SS_SOLVE_PER_STEP = 1 };
 ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
 

@@ -72,8 +72,8 @@ class Context:
         return analyze(self, rowptr, colind, nd_leaf)
 
     def set_solve_mode(self, mode: str):
-        """"per_step": one launch per solve level and step (default); "sweep": one
-        cooperative launch per solve."""
+        """"sweep": one cooperative launch per solve (default); "per_step": one launch per
+        solve level and step."""
         m = {"sweep": L.SS_SOLVE_SWEEP_KERNEL, "per_step": L.SS_SOLVE_PER_STEP}[mode]
         self.check(self.lib.ss_set_solve_mode(self.h, m), "ss_set_solve_mode")
 

@@ -766,7 +766,7 @@ static int shifted_values(ss_numeric *f, int j, const double **out) {
 }
 
 // X = (A - sigma B)^-1 R in the original order; FP64 R, X (may alias).
-int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done) {
+int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done, double target) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
@@ -810,11 +810,16 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
         SS_CUDA_TRY(ctx, cudaGetLastError());
         return SS_OK;
     }
-    // mixed: FP32 solves inside FP64 iterative refinement, X_0 = 0; a requested
-    // refinement gets at least the number of steps the shift's contraction factor needs
-    // to reach 1e-13
-    if (refine > 0 && f->rho[j] > 0.0 && f->rho[j] < 1.0)
+    // mixed: FP32 solves inside FP64 iterative refinement, X_0 = 0.  With a target the
+    // residual decides when to stop; otherwise a requested refinement gets at least the
+    // number of steps the shift's contraction factor needs to reach 1e-13
+    if (target > 0.0) {
+        refine = std::max(refine, 12);
+    } else if (refine > 0 && f->rho[j] > 0.0 && f->rho[j] < 1.0) {
         refine = std::max(refine, std::min(8, (int)std::ceil(std::log(1e-13) / std::log(f->rho[j])) - 1));
+    }
+    unsigned long long *mx = nullptr;
+    if (target > 0.0) SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mx, sizeof(unsigned long long) * 2, st));
     float *wf = nullptr;
     double *r = nullptr, *y = nullptr, *x = nullptr;
     SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wf, sizeof(float) * tot, st));
@@ -828,6 +833,17 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
             const double *mv = nullptr;
             if ((rc = shifted_values(f, j, &mv)) != SS_OK) return rc;
             if ((rc = spmm_launch(s, mv, mv, nullptr, nullptr, x, k, y)) != SS_OK) return rc;
+            if (mx) {
+                SS_CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 2, st));
+                ss_launch(ctx, SS_K_MISC, k_absmax_diff, g, 256, 0, st, tot, R, (const double *)y, mx);
+                unsigned long long h[2];
+                SS_CUDA_TRY(ctx, cudaMemcpyAsync(h, mx, sizeof(h), cudaMemcpyDeviceToHost, st));
+                SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+                double d, m;
+                std::memcpy(&d, &h[0], sizeof(d));
+                std::memcpy(&m, &h[1], sizeof(m));
+                if (d <= target * m) break;
+            }
             ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, y, r);
             rhs = r;
         }
@@ -841,6 +857,7 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     cudaFreeAsync(r, st);
     cudaFreeAsync(y, st);
     cudaFreeAsync(x, st);
+    if (mx) cudaFreeAsync(mx, st);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }

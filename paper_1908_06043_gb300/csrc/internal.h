@@ -18,7 +18,7 @@ struct ss_ctx {
     cudaStream_t stream = nullptr;
     int sm_count = 0;
     std::string err;
-    int solve_mode = SS_SOLVE_PER_STEP;       // how the triangular sweeps are launched
+    int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
     GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
     int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)
     // per-class launch timing (ss_profile): event pairs recorded around launches
@@ -214,7 +214,10 @@ int solve_contraction(ss_numeric *f, int j, double *rho);
 // in-place solve (A - sigma_j B) x = b of a permuted-order N x k block
 template <typename T> int solve_permuted(ss_numeric *f, int j, T *b, int k);
 // X = (A - sigma_j B)^-1 R in the original order (FP64 in/out, refinement for mixed)
-int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done);
+// target > 0 (FP32 solves only): refine until max|R - M X| <= target max|R|, at most
+// max(refine, 12) steps
+int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done,
+                double target = 0.0);
 int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
                 const double *X, int k, double *Y);
 int spmm_launch_ld(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,

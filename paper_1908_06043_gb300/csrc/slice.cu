@@ -117,14 +117,13 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
                   (int *)nullptr);
     } else if (k > 96) {
         // cooperative grid: every block resident, rounds separated by a bounded barrier
+        // (H double-buffered in H2)
         const int np = (k + (k & 1)) / 2, max_sweeps = 40;
-        int2 *pairs;
-        double2 *cs;
+        double *H2;
         double *acc;
         ssd::GridBar *bar;
         int *status;
-        TRY_ALLOC(ctx, buf.get(&pairs, (size_t)np));
-        TRY_ALLOC(ctx, buf.get(&cs, (size_t)np));
+        TRY_ALLOC(ctx, buf.get(&H2, (size_t)k * k));
         TRY_ALLOC(ctx, buf.get(&acc, (size_t)2 * max_sweeps));
         TRY_ALLOC(ctx, buf.get(&bar, 1));
         TRY_ALLOC(ctx, buf.get(&status, 1));
@@ -137,8 +136,8 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
         const double thr = 1e-18, tol = 1e-14;
         const long long limit = 20000000;      // polls of about 64 ns: ~1 s
         int *sw = status;
-        void *args[] = {(void *)&H, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol, (void *)&max_sweeps,
-                        (void *)&pairs, (void *)&cs, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
+        void *args[] = {(void *)&H, (void *)&H2, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol,
+                        (void *)&max_sweeps, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
         g_ss_launches.fetch_add(1, std::memory_order_relaxed);
         size_t slot = 0;
         const bool prof = ctx->prof_mask & (1u << SS_K_JACOBI);
@@ -295,7 +294,12 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // while the window's residuals are above 1e-6 and FP64 refinement afterwards
         int done_ref = 0;
         const int ref_now = near_conv ? (ss_solves_f32(f, j) ? refine : 1) : 0;
-        if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref)) != SS_OK) return rc;
+        // FP32 solves refine until their residual is 1e-3 of the window's current residual
+        // (1e-13 before the first Rayleigh-Ritz of this call, at most 1e-8)
+        double ref_target = 0.0;
+        if (near_conv && ss_solves_f32(f, j))
+            ref_target = hist.empty() ? 1e-13 : std::max(1e-14, std::min(1e-8, 1e-3 * hist.back()));
+        if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref, ref_target)) != SS_OK) return rc;
         refine_total += done_ref;
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;
         // Alg. 2 step 4; one Cholesky-QR pass when no Rayleigh-Ritz follows (the next
