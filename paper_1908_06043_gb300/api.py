@@ -68,8 +68,8 @@ class Context:
     def sync(self):
         self.check(self.lib.ss_sync(self.h), "ss_sync")
 
-    def analyze(self, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0) -> "Symbolic":
-        return analyze(self, rowptr, colind, nd_leaf)
+    def analyze(self, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0, dense: bool = False) -> "Symbolic":
+        return analyze(self, rowptr, colind, nd_leaf, dense)
 
     def set_solve_mode(self, mode: str):
         """"sweep": one cooperative launch per solve (default); "per_step": one launch per
@@ -108,13 +108,17 @@ class Context:
             pass
 
 
-def analyze(ctx: Context, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0) -> "Symbolic":
-    """Symbolic analysis of the full symmetric CSR pattern (host arrays)."""
+def analyze(ctx: Context, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0,
+            dense: bool = False) -> "Symbolic":
+    """Symbolic analysis of the full symmetric CSR pattern (host arrays).  dense=True is
+    the dense-pencil path: no dissection, one front holding the whole (connected) matrix,
+    factored by the same blocked LDL^T kernels (for pencils too dense to gain from
+    sparsity)."""
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     colind = np.ascontiguousarray(colind, dtype=np.int32)
     n = rowptr.size - 1
     opt = L.ss_options()
-    opt.nd_leaf = nd_leaf
+    opt.nd_leaf = max(1, n) if dense else nd_leaf
     h = C.c_void_p()
     ctx.check(ctx.lib.ss_analyze(ctx.h, n, _ptr(rowptr), _ptr(colind), C.byref(opt), C.byref(h)), "ss_analyze")
     return Symbolic(ctx, h, n, int(rowptr[-1]))

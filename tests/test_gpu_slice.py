@@ -123,3 +123,25 @@ def test_gauss16_probe_matches_dense_golden(gpu_lib, precision):
     assert np.all(np.abs(pr.theta[inside] - ref) <= 1e-10 * np.maximum(np.abs(ref), 1.0))
     X = pr.X.cpu().numpy()[:, inside]
     assert spectral.residual_norms(p, pr.theta[inside], X).max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config1_dense_pencil_path(gpu_lib, precision):
+    # dense-pencil path: one front holding the whole N = 864 matrix (no dissection);
+    # inertia and a probe against the dense oracle
+    p = config_pencil(1)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    ctx = gpu_lib.Context(0)
+    sym = ctx.analyze(p.rowptr, p.colind, dense=True)
+    assert sym.info["n_supernodes"] == 1 and sym.info["max_front"] == p.n
+    a = torch.tensor(p.a, device="cuda")
+    b = torch.tensor(p.b, device="cuda")
+    sig = [0.5 * (lam[i] + lam[i + 1]) for i in (5, 40, 85, 431)]
+    f = sym.factor(a, b, sig, precision)
+    for j, i in enumerate((5, 40, 85, 431)):
+        assert f.inertia(j)[0] == i + 1
+    lo, hi = 0.5 * (lam[30] + lam[31]), 0.5 * (lam[50] + lam[51])
+    pr = f.slice_solve(1, lo, hi, torch.tensor(normal_block(p.n, 48, 11), device="cuda"), max_iter=300,
+                       n_expect=20)
+    assert pr.converged and pr.n_found == 20
+    _check_probe(p, lam, lo, hi, pr)
