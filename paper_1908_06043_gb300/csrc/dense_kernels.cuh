@@ -18,8 +18,11 @@ namespace ssd {
 // block = 32 x 32 tile of G over one chunk of rows; 256 threads, 2 x 2 outputs each
 __global__ void __launch_bounds__(256) k_gram(int64_t n, const double *__restrict__ X, int64_t ldx, int k1,
                                               const double *__restrict__ Y, int64_t ldy, int k2,
-                                              int64_t rows_per, double *G) {
+                                              int64_t rows_per, int sym, double *G) {
     __shared__ double Xs[32][33], Ys[32][33];
+    // sym: G is symmetric (X^T M X-type products): tiles above the diagonal only, each
+    // written to both triangles
+    if (sym && blockIdx.x > blockIdx.y) return;
     const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int64_t r_begin = blockIdx.z * rows_per;
     const int64_t r_end = min(n, r_begin + rows_per);
@@ -47,23 +50,29 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, const double *__restric
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
             int i = i0 + tx + 16 * a, j = j0 + ty + 16 * b;
-            if (i < k1 && j < k2) atomicAdd(&G[(int64_t)i * k2 + j], acc[a][b]);
+            if (i < k1 && j < k2) {
+                atomicAdd(&G[(int64_t)i * k2 + j], acc[a][b]);
+                if (sym && blockIdx.x != blockIdx.y) atomicAdd(&G[(int64_t)j * k2 + i], acc[a][b]);
+            }
         }
 }
 
 // ---------------------------------------------------------------- Y = beta Y + alpha X Q  (or X Q^T)
 // block = 64 rows x 32 columns of Y; k1 chunks of 32 through shared memory.  Q is k1 x k2
-// (ldq = k2) or, transposed, k2 x k1 (ldq = k1).  beta = 0 does not read Y.
+// (ldq = k2) or, transposed, k2 x k1 (ldq = k1).  beta = 0 does not read Y.  tri: the
+// effective Q (k1 x k2) is upper triangular (a lower-triangular Q used transposed), so
+// chunks below column block j0's diagonal are skipped.
 __global__ void __launch_bounds__(256) k_gemm_tall(int64_t n, const double *__restrict__ X, int64_t ldx, int k1,
                                                    const double *__restrict__ Q, int k2, int transq,
                                                    double alpha, double beta, double *__restrict__ Y,
-                                                   int64_t ldy) {
+                                                   int64_t ldy, int tri) {
     __shared__ double Xs[64][33], Qs[32][33];
     const int64_t r0 = blockIdx.x * 64ll;
     const int j0 = blockIdx.y * 32;
     const int tid = threadIdx.x, tc = tid & 31, tr = tid >> 5;   // column tc, rows tr + 8 a
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int t0 = 0; t0 < k1; t0 += 32) {
+    const int t_end = tri ? min(k1, j0 + 32) : k1;
+    for (int t0 = 0; t0 < t_end; t0 += 32) {
         for (int q = tid; q < 64 * 32; q += 256) {
             int rr = q >> 5, c = q & 31;
             int64_t r = r0 + rr;

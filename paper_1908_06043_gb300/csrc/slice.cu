@@ -46,7 +46,7 @@ inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b);
 
 // G = X^T Y (k1 x k2, contiguous); X, Y n x k with leading dimensions ldx, ldy
 int gram_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Y, int64_t ldy, int k2,
-            double *G) {
+            double *G, int sym = 0) {
     cudaStream_t st = ctx->stream;
     SS_CUDA_TRY(ctx, cudaMemsetAsync(G, 0, sizeof(double) * k1 * k2, st));
     const int64_t bxy = (int64_t)cdiv(k1, 32) * cdiv(k2, 32);
@@ -55,28 +55,29 @@ int gram_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const 
     int64_t per = ((n + nz - 1) / nz + 31) / 32 * 32;
     nz = (n + per - 1) / per;
     ss_launch(ctx, SS_K_GRAM, ssd::k_gram, dim3(cdiv(k1, 32), cdiv(k2, 32), (unsigned)std::max<int64_t>(1, nz)), 256,
-              0, st, n, X, ldx, k1, Y, ldy, k2, per, G);
-    ctx->add_flops(SS_K_GRAM, 2.0 * (double)n * k1 * k2);
+              0, st, n, X, ldx, k1, Y, ldy, k2, per, sym, G);
+    ctx->add_flops(SS_K_GRAM, sym ? (double)n * k1 * (k2 + 1) : 2.0 * (double)n * k1 * k2);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }
 
-int gram(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Y, int k2, double *G) {
-    return gram_ld(ctx, X, k1, n, k1, Y, k2, k2, G);
+int gram(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Y, int k2, double *G, int sym = 0) {
+    return gram_ld(ctx, X, k1, n, k1, Y, k2, k2, G, sym);
 }
 
 // Y = beta Y + alpha X Q (Q k1 x k2) or X Q^T (Q k2 x k1)
 int gemm_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Q, int k2, int transq,
-            double alpha, double beta, double *Y, int64_t ldy) {
+            double alpha, double beta, double *Y, int64_t ldy, int tri = 0) {
     ss_launch(ctx, SS_K_GEMM, ssd::k_gemm_tall, dim3(cdiv(n, 64), cdiv(k2, 32)), 256, 0, ctx->stream, n, X, ldx, k1,
-              Q, k2, transq, alpha, beta, Y, ldy);
-    ctx->add_flops(SS_K_GEMM, 2.0 * (double)n * k1 * k2);
+              Q, k2, transq, alpha, beta, Y, ldy, tri);
+    ctx->add_flops(SS_K_GEMM, tri ? (double)n * k2 * (k2 + 1) : 2.0 * (double)n * k1 * k2);
     SS_CUDA_TRY(ctx, cudaGetLastError());
     return SS_OK;
 }
 
-int gemm_tall(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Q, int k2, int transq, double *Y) {
-    return gemm_ld(ctx, X, k1, n, k1, Q, k2, transq, 1.0, 0.0, Y, k2);
+int gemm_tall(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Q, int k2, int transq, double *Y,
+              int tri = 0) {
+    return gemm_ld(ctx, X, k1, n, k1, Q, k2, transq, 1.0, 0.0, Y, k2, tri);
 }
 
 __global__ void k_symmetrize(double *H, int k) {
@@ -185,13 +186,13 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
     int rc;
     for (int pass = 0; pass < 2; ++pass) {
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, Wk)) != SS_OK) return rc;
-        if ((rc = gram(ctx, V, s->n, k, Wk, k, G)) != SS_OK) return rc;
+        if ((rc = gram(ctx, V, s->n, k, Wk, k, G, 1)) != SS_OK) return rc;
         ss_launch(ctx, SS_K_SMALL_DENSE, k_symmetrize, cdiv((int64_t)k * k, 256), 256, 0, st, G, k);
         int hinfo = 0;
         for (int attempt = 0; attempt < 3; ++attempt) {
             if (attempt > 0) {
                 // restore G from Wk (still B V) and shift it
-                if ((rc = gram(ctx, V, s->n, k, Wk, k, G)) != SS_OK) return rc;
+                if ((rc = gram(ctx, V, s->n, k, Wk, k, G, 1)) != SS_OK) return rc;
                 ss_launch(ctx, SS_K_SMALL_DENSE, k_symmetrize, cdiv((int64_t)k * k, 256), 256, 0, st, G, k);
                 const double rel = 11.0 * ((double)s->n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 *
                                    (attempt == 1 ? 1.0 : 1e4);
@@ -205,7 +206,7 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
         if (hinfo != 0)
             return ctx->set_error(SS_ERR_NOCONV, "Cholesky-QR: basis is numerically rank deficient");
         ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 32), 256, 0, st, (const double *)G, k, Rinv);
-        if ((rc = gemm_tall(ctx, V, s->n, k, Rinv, k, 1, Wk)) != SS_OK) return rc;
+        if ((rc = gemm_tall(ctx, V, s->n, k, Rinv, k, 1, Wk, 1)) != SS_OK) return rc;
         std::swap(V, Wk);
     }
     (void)buf;
@@ -224,7 +225,7 @@ int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&B
     for (int pass = 0; pass < passes; ++pass) {
         int hinfo = 0;
         for (int attempt = 0; attempt < 3; ++attempt) {
-            if ((rc = gram(ctx, W, s->n, k, BW, k, G)) != SS_OK) return rc;
+            if ((rc = gram(ctx, W, s->n, k, BW, k, G, 1)) != SS_OK) return rc;
             ss_launch(ctx, SS_K_SMALL_DENSE, k_symmetrize, cdiv((int64_t)k * k, 256), 256, 0, st, G, k);
             if (attempt > 0) {
                 const double rel = 11.0 * ((double)s->n * k + (double)k * (k + 1)) * 1.1102230246251565e-16 *
@@ -238,8 +239,8 @@ int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&B
         }
         if (hinfo != 0) return ctx->set_error(SS_ERR_NOCONV, "Cholesky-QR: basis is numerically rank deficient");
         ss_launch(ctx, SS_K_SMALL_DENSE, ssd::k_trinv_lower, cdiv(k, 32), 256, 0, st, (const double *)G, k, Rinv);
-        if ((rc = gemm_tall(ctx, W, s->n, k, Rinv, k, 1, Wt)) != SS_OK) return rc;
-        if ((rc = gemm_tall(ctx, BW, s->n, k, Rinv, k, 1, BWt)) != SS_OK) return rc;
+        if ((rc = gemm_tall(ctx, W, s->n, k, Rinv, k, 1, Wt, 1)) != SS_OK) return rc;
+        if ((rc = gemm_tall(ctx, BW, s->n, k, Rinv, k, 1, BWt, 1)) != SS_OK) return rc;
         std::swap(W, Wt);
         std::swap(BW, BWt);
     }
@@ -314,7 +315,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // Rayleigh-Ritz: H = W^T A W; the dead V / BV buffers take A W and A X
         double *AW = V, *AX = BV;
         if ((rc = spmm_launch(s, f->a_vals, f->a_vals, nullptr, nullptr, W, k, AW)) != SS_OK) return rc;
-        if ((rc = gram(ctx, W, n, k, AW, k, G)) != SS_OK) return rc;
+        if ((rc = gram(ctx, W, n, k, AW, k, G, 1)) != SS_OK) return rc;
         if ((rc = sym_eig(ctx, G, k, theta_d, Q, buf)) != SS_OK) return rc;
         if ((rc = gemm_tall(ctx, W, n, k, Q, k, 0, T1)) != SS_OK) return rc;      // X
         if ((rc = gemm_tall(ctx, BW, n, k, Q, k, 0, T2)) != SS_OK) return rc;     // B X
@@ -455,7 +456,7 @@ int block_lanczos_impl(ss_numeric *f, int j, double lo, double hi, const ss_solv
     // Rayleigh-Ritz on the basis: H = V^T A V
     const int d = (int)cur;
     if ((rc = spmm_launch_ld(s, f->a_vals, f->a_vals, nullptr, nullptr, Vb, dmax, d, AV, dmax)) != SS_OK) return rc;
-    if ((rc = gram_ld(ctx, Vb, dmax, n, d, AV, dmax, d, H)) != SS_OK) return rc;
+    if ((rc = gram_ld(ctx, Vb, dmax, n, d, AV, dmax, d, H, 1)) != SS_OK) return rc;
     if ((rc = sym_eig(ctx, H, d, theta_d, Q, buf)) != SS_OK) return rc;
     std::vector<double> th(d), hq((size_t)d * d);
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(th.data(), theta_d, sizeof(double) * d, cudaMemcpyDeviceToHost, st));
