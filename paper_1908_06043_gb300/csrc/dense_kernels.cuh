@@ -341,47 +341,24 @@ __global__ void __launch_bounds__(1024) k_jacobi_block(double *H, double *V, int
 using ::GridBar;
 using ::grid_barrier;
 
-// The same parallel-ordered Jacobi as k_jacobi_block, spread over a cooperative grid.
-// H is double-buffered (H -> H2 -> H ...): within a round every thread derives the two
-// rotations its 2 x 2 block needs from the round's input buffer and writes the rotated
-// block to the other buffer, so one grid barrier per round suffices.  The result ends
-// in H.  acc: 2 * max_sweeps doubles (zeroed) for the per-sweep off-diagonal / total
-// norms.
-__device__ __forceinline__ void jac_rotation(const double *__restrict__ H, int k, int kp, int r, int t,
-                                             double thr, int *p, int *q, double *c, double *sn) {
-    const int i = (t == 0) ? kp - 1 : (r + t) % (kp - 1);
-    const int y = jac_partner(i, r, kp);
-    *p = min(i, y);
-    *q = max(i, y);
-    *c = 1.0;
-    *sn = 0.0;
-    if (*q < k) {
-        const double hpq = H[(int64_t)*p * k + *q];
-        const double hpp = H[(int64_t)*p * k + *p], hqq = H[(int64_t)*q * k + *q];
-        if (hpq != 0.0 && fabs(hpq) > thr * sqrt(fabs(hpp * hqq))) {
-            const double th = (hqq - hpp) / (2.0 * hpq);
-            const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            *c = 1.0 / sqrt(tt * tt + 1.0);
-            *sn = tt * *c;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *H2, double *V, int k, double thr,
-                                                     double tol, int max_sweeps, double *acc, GridBar *bar,
-                                                     long long limit, int *sweeps_done) {
+// The same parallel-ordered Jacobi as k_jacobi_block, spread over a cooperative grid:
+// per round the rotations go to global scratch (pairs / cs), a grid barrier, the 2 x 2
+// block and row-pair updates over all threads, a grid barrier.  acc: 2 * max_sweeps
+// doubles (zeroed) for the per-sweep off-diagonal / total norms.
+__global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *V, int k, double thr, double tol,
+                                                     int max_sweeps, int2 *pairs, double2 *cs, double *acc,
+                                                     GridBar *bar, long long limit, int *sweeps_done) {
     const int kp = k + (k & 1);
     const int np = kp / 2;
     const unsigned int nb = gridDim.x;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)nb * blockDim.x;
     __shared__ double red_off[8], red_all[8];
-    double *cur = H, *nxt = H2;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         double off = 0.0, all = 0.0;
         for (int64_t q = gtid; q < (int64_t)k * k; q += gthreads) {
-            double v = cur[q] * cur[q];
+            double v = H[q] * H[q];
             all += v;
             if (q / k != q % k) off += v;
         }
@@ -401,46 +378,60 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *H2, doub
         const double o2 = *(volatile double *)&acc[2 * sweep], a2 = *(volatile double *)&acc[2 * sweep + 1];
         if (o2 <= tol * tol * a2) break;
         for (int r = 0; r < kp - 1; ++r) {
+            for (int64_t t = gtid; t < np; t += gthreads) {
+                int i = (t == 0) ? kp - 1 : (int)((r + t) % (kp - 1));
+                int y = jac_partner(i, r, kp);
+                int p = min(i, y), q = max(i, y);
+                double c = 1.0, sn = 0.0;
+                if (q < k) {
+                    const double hpq = H[(int64_t)p * k + q];
+                    const double hpp = H[(int64_t)p * k + p], hqq = H[(int64_t)q * k + q];
+                    if (hpq != 0.0 && fabs(hpq) > thr * sqrt(fabs(hpp * hqq))) {
+                        const double th = (hqq - hpp) / (2.0 * hpq);
+                        const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                        c = 1.0 / sqrt(tt * tt + 1.0);
+                        sn = tt * c;
+                    }
+                }
+                pairs[t] = make_int2(p, q);
+                cs[t] = make_double2(c, sn);
+            }
+            if (!grid_barrier(bar, nb, limit)) return;
             for (int64_t e = gtid; e < (int64_t)np * np; e += gthreads) {
                 const int ta = (int)(e / np), tb = (int)(e % np);
-                int p1, q1, p2, q2;
-                double c1, s1, c2, s2;
-                jac_rotation(cur, k, kp, r, ta, thr, &p1, &q1, &c1, &s1);
-                jac_rotation(cur, k, kp, r, tb, thr, &p2, &q2, &c2, &s2);
+                const double2 r1 = cs[ta], r2 = cs[tb];
+                const double c1 = r1.x, s1 = r1.y, c2 = r2.x, s2 = r2.y;
+                if (s1 == 0.0 && s2 == 0.0) continue;
+                const int2 a1 = pairs[ta], a2p = pairs[tb];
+                const int p1 = a1.x, q1 = a1.y, p2 = a2p.x, q2 = a2p.y;
                 const bool rq = q1 < k, cq = q2 < k;
-                const double h11 = cur[(int64_t)p1 * k + p2];
-                const double h12 = cq ? cur[(int64_t)p1 * k + q2] : 0.0;
-                const double h21 = rq ? cur[(int64_t)q1 * k + p2] : 0.0;
-                const double h22 = (rq && cq) ? cur[(int64_t)q1 * k + q2] : 0.0;
-                const double x11 = c2 * h11 - s2 * h12, x12 = s2 * h11 + c2 * h12;
-                const double x21 = c2 * h21 - s2 * h22, x22 = s2 * h21 + c2 * h22;
+                double h11 = H[(int64_t)p1 * k + p2];
+                double h12 = cq ? H[(int64_t)p1 * k + q2] : 0.0;
+                double h21 = rq ? H[(int64_t)q1 * k + p2] : 0.0;
+                double h22 = (rq && cq) ? H[(int64_t)q1 * k + q2] : 0.0;
+                double x11 = c2 * h11 - s2 * h12, x12 = s2 * h11 + c2 * h12;
+                double x21 = c2 * h21 - s2 * h22, x22 = s2 * h21 + c2 * h22;
                 double b11 = c1 * x11 - s1 * x21, b21 = s1 * x11 + c1 * x21;
                 double b12 = c1 * x12 - s1 * x22, b22 = s1 * x12 + c1 * x22;
                 if (ta == tb && s1 != 0.0) { b12 = 0.0; b21 = 0.0; }
-                nxt[(int64_t)p1 * k + p2] = b11;
-                if (cq) nxt[(int64_t)p1 * k + q2] = b12;
-                if (rq) nxt[(int64_t)q1 * k + p2] = b21;
-                if (rq && cq) nxt[(int64_t)q1 * k + q2] = b22;
+                H[(int64_t)p1 * k + p2] = b11;
+                if (cq) H[(int64_t)p1 * k + q2] = b12;
+                if (rq) H[(int64_t)q1 * k + p2] = b21;
+                if (rq && cq) H[(int64_t)q1 * k + q2] = b22;
             }
             for (int64_t e = gtid; e < (int64_t)k * np; e += gthreads) {
                 const int row = (int)(e / np), tb = (int)(e % np);
-                int p2, q2;
-                double c2, s2;
-                jac_rotation(cur, k, kp, r, tb, thr, &p2, &q2, &c2, &s2);
-                if (s2 == 0.0) continue;
+                const double2 r2 = cs[tb];
+                if (r2.y == 0.0) continue;
+                const int2 a2p = pairs[tb];
                 double *vr = V + (int64_t)row * k;
-                const double vp = vr[p2], vq = vr[q2];
-                vr[p2] = c2 * vp - s2 * vq;
-                vr[q2] = s2 * vp + c2 * vq;
+                const double vp = vr[a2p.x], vq = vr[a2p.y];
+                vr[a2p.x] = r2.x * vp - r2.y * vq;
+                vr[a2p.y] = r2.y * vp + r2.x * vq;
             }
             if (!grid_barrier(bar, nb, limit)) return;
-            double *t = cur;
-            cur = nxt;
-            nxt = t;
         }
     }
-    if (cur != H)
-        for (int64_t q = gtid; q < (int64_t)k * k; q += gthreads) H[q] = cur[q];
     if (gtid == 0 && sweeps_done) *sweeps_done = sweep;
 }
 

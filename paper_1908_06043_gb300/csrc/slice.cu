@@ -118,13 +118,14 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
                   (int *)nullptr);
     } else if (k > 96) {
         // cooperative grid: every block resident, rounds separated by a bounded barrier
-        // (H double-buffered in H2)
         const int np = (k + (k & 1)) / 2, max_sweeps = 40;
-        double *H2;
+        int2 *pairs;
+        double2 *cs;
         double *acc;
         ssd::GridBar *bar;
         int *status;
-        TRY_ALLOC(ctx, buf.get(&H2, (size_t)k * k));
+        TRY_ALLOC(ctx, buf.get(&pairs, (size_t)np));
+        TRY_ALLOC(ctx, buf.get(&cs, (size_t)np));
         TRY_ALLOC(ctx, buf.get(&acc, (size_t)2 * max_sweeps));
         TRY_ALLOC(ctx, buf.get(&bar, 1));
         TRY_ALLOC(ctx, buf.get(&status, 1));
@@ -137,8 +138,8 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
         const double thr = 1e-18, tol = 1e-14;
         const long long limit = 20000000;      // polls of about 64 ns: ~1 s
         int *sw = status;
-        void *args[] = {(void *)&H, (void *)&H2, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol,
-                        (void *)&max_sweeps, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
+        void *args[] = {(void *)&H, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol, (void *)&max_sweeps,
+                        (void *)&pairs, (void *)&cs, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
         g_ss_launches.fetch_add(1, std::memory_order_relaxed);
         size_t slot = 0;
         const bool prof = ctx->prof_mask & (1u << SS_K_JACOBI);
