@@ -49,7 +49,8 @@ int gram_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const 
             double *G, int sym = 0) {
     cudaStream_t st = ctx->stream;
     SS_CUDA_TRY(ctx, cudaMemsetAsync(G, 0, sizeof(double) * k1 * k2, st));
-    const int64_t bxy = (int64_t)cdiv(k1, 32) * cdiv(k2, 32);
+    const int64_t t1 = cdiv(k1, 32), t2 = cdiv(k2, 32);
+    const int64_t bxy = sym ? t1 * (t1 + 1) / 2 : t1 * t2;     // tiles that do work
     int64_t nz = std::max<int64_t>(1, (4 * (int64_t)ctx->sm_count + bxy - 1) / bxy);
     nz = std::min<int64_t>(nz, std::max<int64_t>(1, n / 256));
     int64_t per = ((n + nz - 1) / nz + 31) / 32 * 32;
