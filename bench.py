@@ -374,7 +374,7 @@ def main():
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": wl["name"], "precision": args.precision,
-                      "probe_driver": "shift-invert subspace iteration (Alg. 2), Rayleigh-Ritz every 2nd iteration in the first round, once per later round",
+                      "probe_driver": "shift-invert subspace iteration (Alg. 2), Rayleigh-Ritz every 3rd iteration in the first round, once per later round",
                       "shift_placement": "DOS ball partition (radius 2h ball <= basis)",
                       "lanczos_steps": steps_dos, "lanczos_vectors": n_vec, "parallelism": f"replicas x{ws}",
                       "l2": "inputs larger than L2 (factor arena > 129 MB)",

@@ -489,12 +489,12 @@ class SliceSolver:
                     else:
                         v0, mi, ne = Xs[j], iters_per_round, v0_never(Xs[j])
                     fj, jj = (f64[j], 0) if j in f64 else (f, j)
-                    # Rayleigh-Ritz (the convergence check) every 2nd iteration in a first
+                    # Rayleigh-Ritz (the convergence check) every 3rd iteration in a first
                     # round and once at the end of a restart round: the iterated subspace
                     # does not depend on it
                     pr = fj.slice_solve(jj, lo, hi, v0, tol=self.tol, max_iter=mi, refine=self.refine,
                                         n_expect=ne, allow_noconv=True, refine_from_start=Xs[j] is not None or (warm and V0 is not None and V0[j] is not None),
-                                        check_every=2 if Xs[j] is None else mi)
+                                        check_every=3 if Xs[j] is None else mi)
                 probes[j] = pr
                 Xs[j] = pr.X
                 iters[j] += pr.iterations
