@@ -128,6 +128,14 @@ const char *ss_last_error(const ss_ctx *ctx);
 enum { SS_SOLVE_SWEEP_KERNEL = 0, SS_SOLVE_PER_STEP = 1 };
 ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
 
+/* Self-test of the bounded grid barrier used by the cooperative kernels (no paper
+ * counterpart): one block per SM waits at a barrier that expects extra_arrivals (0 or 1)
+ * more blocks than are launched, polling at most `limit` times (1 .. 1e8; a poll takes
+ * about 64-100 ns).  extra_arrivals = 0 returns SS_OK; 1 makes every wait run out and
+ * returns SS_ERR_TIMEOUT with the context still usable.  Errors: SS_ERR_ARG, SS_ERR_CUDA,
+ * SS_ERR_TIMEOUT. */
+ss_status ss_selftest_barrier(ss_ctx *ctx, int32_t extra_arrivals, int64_t limit);
+
 /* ---- ss_analyze (Section 2.1: the sparse LDL^T of A - sigma B is the major cost;
  * Section 5: the paper's solver orders with nested dissection) --------------------
  * Host CSR pattern in, symbolic analysis out: nested-dissection ordering, supernodes

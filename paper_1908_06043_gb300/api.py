@@ -77,6 +77,10 @@ class Context:
         m = {"sweep": L.SS_SOLVE_SWEEP_KERNEL, "per_step": L.SS_SOLVE_PER_STEP}[mode]
         self.check(self.lib.ss_set_solve_mode(self.h, m), "ss_set_solve_mode")
 
+    def selftest_barrier(self, extra_arrivals: int = 0, limit: int = 200000):
+        """Run the bounded grid-barrier self-test (raises SisliceError on a timeout)."""
+        self.check(self.lib.ss_selftest_barrier(self.h, extra_arrivals, limit), "ss_selftest_barrier")
+
     def launch_count(self) -> int:
         """Kernels launched by the library since it was loaded."""
         return int(self.lib.ss_launch_count())

@@ -103,6 +103,34 @@ extern "C" ss_status ss_destroy(ss_ctx *ctx) {
 
 extern "C" const char *ss_last_error(const ss_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+// every block waits at one grid barrier that expects `expected` arrivals
+__global__ void k_barrier_selftest(GridBar *bar, unsigned int expected, long long limit) {
+    grid_barrier(bar, expected, limit);
+}
+
+extern "C" ss_status ss_selftest_barrier(ss_ctx *ctx, int32_t extra_arrivals, int64_t limit) {
+    if (!ctx) return SS_ERR_ARG;
+    if (ctx->device < 0 || extra_arrivals < 0 || extra_arrivals > 1 || limit <= 0 || limit > 100000000)
+        return ctx->set_error(SS_ERR_ARG, "ss_selftest_barrier: bad argument or host-only context");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    GridBar *bar = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&bar, sizeof(GridBar), st));
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, sizeof(GridBar), st));
+    const unsigned int nb = (unsigned int)ctx->sm_count;          // one block per SM: resident
+    unsigned int expected = nb + (unsigned int)extra_arrivals;
+    long long lim = limit;
+    void *args[] = {(void *)&bar, (void *)&expected, (void *)&lim};
+    g_ss_launches.fetch_add(1, std::memory_order_relaxed);
+    SS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)k_barrier_selftest, dim3(nb), dim3(256), args, 0, st));
+    int herr = 0;
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaFreeAsync(bar, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (herr) return ctx->set_error(SS_ERR_TIMEOUT, "ss_selftest_barrier: grid barrier timed out");
+    return SS_OK;
+}
+
 extern "C" ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode) {
     if (!ctx) return SS_ERR_ARG;
     if (mode != SS_SOLVE_SWEEP_KERNEL && mode != SS_SOLVE_PER_STEP)

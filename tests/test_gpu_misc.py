@@ -122,3 +122,19 @@ def test_gauss16_gradient_sampled_and_finite_difference(gpu_lib):
     g_single, _ = sym.band_energy_grad(X[:, q:q + 1].contiguous(), torch.tensor(th[q:q + 1], device="cuda"))
     g_sym = g_single[ent].item() + g_single[mirror].item()
     assert abs(fd - g_sym) <= 1e-5 * max(abs(g_sym), 1e-3), (fd, g_sym)
+
+
+def test_grid_barrier_wait_is_bounded(gpu_lib):
+    # failure detection without a GPU fault: a barrier that expects one block more than
+    # was launched runs out of polls, every block leaves, the host reads SS_ERR_TIMEOUT and
+    # the context keeps working
+    ctx = gpu_lib.Context(0)
+    ctx.selftest_barrier(0, 200000)
+    with pytest.raises(gpu_lib.SisliceError) as e:
+        ctx.selftest_barrier(1, 200000)
+    assert e.value.status == gpu_lib.L.SS_ERR_TIMEOUT
+    ctx.selftest_barrier(0, 200000)
+    p = config_pencil(1)
+    ctx2, sym, a, b = setup(gpu_lib, p)
+    f = sym.factor(a, b, [0.1], "fp64")
+    assert f.inertia(0)[0] + f.inertia(0)[2] == p.n
