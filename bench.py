@@ -254,7 +254,7 @@ def main():
                               "rounds": rs.rounds, "probe_iterations": rs.timings["iterations"],
                               "validated": check(rs), "eigenpairs": int(len(rs.eigenvalues)),
                               "max_resid": float(rs.residuals.max()),
-                              "shifts": [float(x) for x in rs.shifts],
+                              "shifts": [float(x) for x in rs.shifts], "n_probes": len(rs.shifts),
                               "migration_init": mig["init"] if mig else "DOS placement",
                               "cluster_sizes": mig["sizes"] if mig else None}), flush=True)
         print(json.dumps({"sequence_total_s": t1 - t0, "pencils": len(res)}), flush=True)

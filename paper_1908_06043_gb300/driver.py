@@ -478,7 +478,7 @@ class SliceSolver:
                                        driver="lanczos", k_out=ko, allow_noconv=True)
                 else:
                     kk = k or (ks[j] if ks is not None else min(n, -(-(2 * cnt[j] + 16) // 16) * 16))
-                    kk = min(n, max(kk, -(-(cnt[j] + 16) // 16) * 16))
+                    kk = min(n, 4096, max(kk, -(-(cnt[j] + 16) // 16) * 16))
                     if Xs[j] is None:
                         v0 = V0[j] if V0 is not None and V0[j] is not None else torch.randn(n, kk, generator=g, device="cuda",
                                                                      dtype=torch.float64)
@@ -514,8 +514,9 @@ class SliceSolver:
             # eigenvalues near sigma than the estimate it was sized from
             for j in active:
                 restarts[j] += 1
-                if driver != "lanczos" and restarts[j] % 4 == 0 and Xs[j] is not None and Xs[j].shape[1] < n:
-                    extra = min(n - Xs[j].shape[1], max(16, Xs[j].shape[1] // 2))
+                cap = min(n, 4096)
+                if driver != "lanczos" and restarts[j] % 4 == 0 and Xs[j] is not None and Xs[j].shape[1] < cap:
+                    extra = min(cap - Xs[j].shape[1], max(16, Xs[j].shape[1] // 2))
                     Xs[j] = torch.cat([Xs[j], torch.randn(n, extra, generator=g, device="cuda",
                                                           dtype=torch.float64)], dim=1).contiguous()
                     grown[j] += 1
@@ -676,6 +677,21 @@ def _ceil16(x: float) -> int:
     return int(-(-x // 16) * 16)
 
 
+def _inside_region(groups, lam_min: float, lam_max: float):
+    """Probes whose migrated shift left the new region [lambda_min, lambda_max] hand their
+    members to the nearest probe inside it (a region bound moves with the pencil)."""
+    inside = [g for g in groups if lam_min < g[0] < lam_max]
+    if not inside:
+        return [(0.5 * (lam_min + lam_max), sorted(i for _, m in groups for i in m))]
+    out = [(s_, list(m)) for s_, m in inside]
+    for s_, m in groups:
+        if lam_min < s_ < lam_max:
+            continue
+        q = min(range(len(out)), key=lambda t: abs(out[t][0] - s_))
+        out[q] = (out[q][0], sorted(out[q][1] + list(m)))
+    return out
+
+
 def migrated_windows(values, groups, lam_min: float, lam_max: float):
     """Slice boundaries and basis widths for migrated probes (groups from
     migrate_probes, sorted by shift), using the previous step's eigenvalues as the
@@ -702,7 +718,9 @@ def migrated_windows(values, groups, lam_min: float, lam_max: float):
         c = int(np.count_nonzero((x >= a) & (x <= b)))
         if b > lam_max:
             c += int(np.count_nonzero((x >= 2 * lam_max - b) & (x <= lam_max)))
-        ks.append(_ceil16(1.15 * c + 16))
+        # the ball can reach far into the spectrum for a centroid shift of a wide cluster;
+        # the basis stays within 4x its members + 16 (validation widens it if needed)
+        ks.append(min(_ceil16(1.15 * c + 16), _ceil16(4 * (len(groups[j][1]) + 16)), 4096))
     return splits, ks
 
 
@@ -755,13 +773,14 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
             prev = results[-1]
             after_dos = prev.timings["migration"] is None
             init = kmeans_pp_seeds(prev.eigenvalues, n_s, uniforms) if after_dos else np.asarray(prev.shifts)
-            groups = migrate_probes(prev.eigenvalues, prev.owners, prev.shifts, init)
-            shifts = [s_ for s_, _ in groups]
+            migrated = migrate_probes(prev.eigenvalues, prev.owners, prev.shifts, init)
             span = float(prev.lam_max - prev.lam_min)
             lam_min = prev.lam_min
             while solver.count_below([lam_min])[0] > 0:
                 lam_min -= 0.1 * span
             lam_max = solver.bound_at_count(prev.lam_max, n_e, lam_min, span)
+            groups = _inside_region(migrated, lam_min, lam_max)
+            shifts = [s_ for s_, _ in groups]
             splits, ks = migrated_windows(prev.eigenvalues, groups, lam_min, lam_max)
             V0 = []
             for (_, m), kk in zip(groups, ks):
@@ -770,8 +789,9 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
                 V0.append(torch.cat([prev.eigenvectors[:, m], fill], dim=1).contiguous())
             res = solver.run_with_recovery(shifts, lam_min, lam_max, None, V0=V0, ks=ks, splits=splits,
                                            seed=seed + i, warm=True)
-            res.timings["migration"] = dict(shifts=shifts, sizes=[len(m) for _, m in groups],
-                                            init="kmeans++" if after_dos else "previous shifts")
+            res.timings["migration"] = dict(shifts=[s_ for s_, _ in migrated], sizes=[len(m) for _, m in migrated],
+                                            init="kmeans++" if after_dos else "previous shifts",
+                                            shifts_used=shifts)
         res.timings["eta"] = etas[-1] if i > 0 else None
         results.append(res)
     return results
