@@ -180,7 +180,7 @@ def lloyd_assign(x, cent, maxit=1000):
     return cent, a
 
 
-def migrate(values, owner, old_shifts, init_centroids):
+def migrate(values, owner, old_shifts, init_centroids, balance=None):
     """Shift migration between two SCF steps (Section 3.2).
 
     values: validated eigenvalues of the previous step; owner[i]: the probe that
@@ -191,7 +191,10 @@ def migrate(values, owner, old_shifts, init_centroids):
     the merged values); probes with no cluster deleted; for each deletion the largest
     cluster split by 2-means, one part kept by its probe and the other given to an
     inserted probe.  Returns a list of (shift, member indices into values), sorted by
-    shift; an inserted probe's start vectors are the Ritz vectors of its members."""
+    shift; an inserted probe's start vectors are the Ritz vectors of its members.
+    balance: if given, a probe holding more than balance * len(values) / n_s values is
+    split the same way (the paper's probe insertion for load balance), up to 2 n_s
+    probes."""
     x = np.asarray(values, dtype=np.float64)
     owner = np.asarray(owner)
     old = np.asarray(old_shifts, dtype=np.float64)
@@ -212,7 +215,10 @@ def migrate(values, owner, old_shifts, init_centroids):
         if members[p]:
             probes.append([p, sorted(members[p])])
     deleted = n_s - len(probes)
-    for _ in range(deleted):
+    limit = float(balance) * x.size / n_s if balance else np.inf
+    splits_done = 0
+    while splits_done < deleted or (len(probes) < 2 * n_s and max(len(m) for _, m in probes) > limit):
+        splits_done += 1
         big = max(range(len(probes)), key=lambda q: (len(probes[q][1]), -q))
         p, idx = probes[big]
         idx = np.array(idx)

@@ -298,7 +298,7 @@ def kmeans_pp_seeds(values, n_s, uniforms):
     return np.asarray(seeds)
 
 
-def migrate_probes(values, owner, old_shifts, init):
+def migrate_probes(values, owner, old_shifts, init, balance=None):
     """Move the probes of one SCF step to the next (Section 3.2).
 
     The validated eigenvalues `values` (owner[i] = probe that produced values[i]) are
@@ -308,6 +308,8 @@ def migrate_probes(values, owner, old_shifts, init):
     a cluster is dropped and replaced: the largest cluster is split in two by 2-means
     (started from its extreme values), its probe keeps the half with more of its own
     values (ties: the half nearer its old shift) and a new probe takes the other half.
+    With `balance`, a probe holding more than balance x the mean count is split the same
+    way (insertion for load balance), up to twice as many probes as before.
     Returns [(shift, member indices)] sorted by shift, shift = mean of the members."""
     x = np.asarray(values, dtype=np.float64)
     owner = np.asarray(owner)
@@ -322,7 +324,10 @@ def migrate_probes(values, owner, old_shifts, init):
         mu = x[idx].mean()
         owned[min(top, key=lambda q: (abs(old[q] - mu), q))].extend(idx.tolist())
     groups = [(p, np.array(sorted(m))) for p, m in enumerate(owned) if m]
-    for _ in range(n_s - len(groups)):
+    missing = n_s - len(groups)
+    cap = float(balance) * x.size / n_s if balance else np.inf
+    while missing > 0 or (len(groups) < 2 * n_s and max(m.size for _, m in groups) > cap):
+        missing -= 1
         g = max(range(len(groups)), key=lambda q: (groups[q][1].size, -q))
         p, idx = groups[g]
         v = x[idx]
@@ -726,7 +731,7 @@ def migrated_windows(values, groups, lam_min: float, lam_max: float):
 
 def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precision: str = "mixed",
                    tol: float = 1e-10, lanczos_steps: int = 100, n_vec: int = 4, seed: int = 0,
-                   start=None, uniforms=None, eta_tol: float = np.inf):
+                   start=None, uniforms=None, eta_tol: float = np.inf, balance: float = 2.0):
     """Lowest n_e eigenpairs of a sequence of pencils (A_i, B) on one pattern, as the SCF
     loop of Alg. 1 produces them (Section 3.2).  Step 0 places the shifts from a Lanczos
     DOS estimate.  Every later step migrates the probes: k-means of the previous step's
@@ -738,7 +743,9 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
     uniforms: the n_s k-means++ uniforms (seeded if None).  Every step recovers missing
     eigenvalues by probe insertion (Section 3.3).  eta_tol: relative change of
     Tr(X^T A X) over the previous eigenvectors (Eq. 9) above which a step is placed from a
-    new DOS estimate instead of by migration (inf: never).  Returns one SliceResult per
+    new DOS estimate instead of by migration (inf: never).  balance: a migrated probe with
+    more than balance x the mean number of eigenvalues gets an inserted neighbour (None:
+    only deleted probes are replaced).  Returns one SliceResult per
     pencil; timings["migration"] records the shifts and cluster sizes chosen and
     timings["eta"] the monitor's (old, new, changed)."""
     n = sym.n
@@ -773,7 +780,7 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
             prev = results[-1]
             after_dos = prev.timings["migration"] is None
             init = kmeans_pp_seeds(prev.eigenvalues, n_s, uniforms) if after_dos else np.asarray(prev.shifts)
-            migrated = migrate_probes(prev.eigenvalues, prev.owners, prev.shifts, init)
+            migrated = migrate_probes(prev.eigenvalues, prev.owners, prev.shifts, init, balance=balance)
             span = float(prev.lam_max - prev.lam_min)
             lam_min = prev.lam_min
             while solver.count_below([lam_min])[0] > 0:
@@ -791,7 +798,7 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
                                            seed=seed + i, warm=True)
             res.timings["migration"] = dict(shifts=[s_ for s_, _ in migrated], sizes=[len(m) for _, m in migrated],
                                             init="kmeans++" if after_dos else "previous shifts",
-                                            shifts_used=shifts)
+                                            shifts_used=shifts, balance=balance)
         res.timings["eta"] = etas[-1] if i > 0 else None
         results.append(res)
     return results

@@ -95,9 +95,9 @@ def test_migrate_probes_matches_oracle():
         u = rng.random(n_s)
         seeds = kmeans_pp_seeds(v, n_s, u)
         assert np.array_equal(seeds, partition.kmeans_pp_init(v, n_s, u))
-        for init in (old, seeds):
-            got = migrate_probes(v, owner, old, init)
-            ref = partition.migrate(v, owner, old, init)
+        for init, bal in ((old, None), (seeds, None), (old, 1.5), (seeds, 2.0)):
+            got = migrate_probes(v, owner, old, init, balance=bal)
+            ref = partition.migrate(v, owner, old, init, balance=bal)
             assert len(got) == len(ref)
             for (s1, m1), (s2, m2) in zip(got, ref):
                 assert m1 == m2 and abs(s1 - s2) <= 1e-12 * max(1.0, abs(s2))

@@ -73,7 +73,8 @@ def test_scf_sequence_with_probe_migration(gpu_lib, precision):
         prev = res[i - 1]
         after_dos = prev.timings["migration"] is None
         init = partition.kmeans_pp_init(prev.eigenvalues, 4, uniforms) if after_dos else np.asarray(prev.shifts)
-        ref = partition.migrate(prev.eigenvalues, prev.owners, prev.shifts, init)
+        ref = partition.migrate(prev.eigenvalues, prev.owners, prev.shifts, init,
+                                balance=rs.timings["migration"]["balance"])
         got = rs.timings["migration"]["shifts"]
         assert len(got) == len(ref)
         assert np.allclose(got, [s for s, _ in ref], rtol=1e-12, atol=1e-12)

@@ -185,3 +185,21 @@ def test_dos_cluster_refinement_separates_close_clusters():
     I, _ = partition.dos_cluster_partition(2000, runs, -1.0, 6.0, 3, 12)
     cuts = [u for _, u in I[:-1]]
     assert any(0.09 < c < 0.3 for c in cuts)        # between the two clusters
+
+
+def test_migration_load_balance_insertion():
+    # k-means leaves clusters of 93 and 117 values (mean 105): with balance = 1.1 the
+    # larger one is split in two, after which no probe holds more than 1.1x the mean
+    rng = np.random.default_rng(9)
+    v = np.sort(np.concatenate([rng.uniform(0, 1, 10), rng.uniform(2, 10, 200)]))
+    owner = (v > 1.5).astype(int)
+    old = np.array([0.5, 6.0])
+    plain = partition.migrate(v, owner, old, old)
+    assert sorted(len(m) for _, m in plain) == [93, 117]
+    assert partition.migrate(v, owner, old, old, balance=1.2) == plain
+    bal = partition.migrate(v, owner, old, old, balance=1.1)
+    assert len(bal) == 3
+    assert sorted(i for _, m in bal for i in m) == list(range(v.size))
+    assert max(len(m) for _, m in bal) <= 1.1 * v.size / 2
+    for s_, m in bal:
+        assert abs(s_ - v[m].mean()) < 1e-12
