@@ -126,3 +126,52 @@ def test_dos_cluster_partition_matches_oracle():
             assert len(I1) == len(I2) == n_s
             assert np.allclose(np.array(I1), np.array(I2), rtol=1e-9, atol=1e-9)
             assert np.allclose(s1, s2, rtol=1e-9, atol=1e-9)
+
+
+def test_migrated_windows_and_region_filter():
+    from paper_1908_06043_gb300.driver import _inside_region, migrate_probes, migrated_windows
+    rng = np.random.default_rng(21)
+    v = np.sort(np.concatenate([rng.uniform(-40, -10, 12), rng.uniform(-2, 0.3, 150)]))
+    old = np.array([-30.0, -1.5, -0.9, -0.3, 0.1])
+    owner = np.searchsorted(0.5 * (old[1:] + old[:-1]), v)
+    groups = migrate_probes(v, owner, old, old)
+    lam_min, lam_max = -45.0, 0.31
+    splits, ks = migrated_windows(v, groups, lam_min, lam_max)
+    sh = [s_ for s_, _ in groups]
+    assert splits[0] is None and len(splits) == len(sh) == len(ks)
+    for j in range(1, len(sh)):
+        assert sh[j - 1] < splits[j] < sh[j]
+    for (_, m), k in zip(groups, ks):
+        assert k % 16 == 0 and 16 <= k <= min(4096, 4 * (len(m) + 16) + 15)
+    # a region bound that moved below the top shift: its members go to the nearest probe
+    cut = 0.5 * (sh[-2] + sh[-1])
+    kept = _inside_region(groups, lam_min, cut)
+    assert len(kept) == len(groups) - 1
+    assert sorted(i for _, m in kept for i in m) == list(range(v.size))
+    assert all(lam_min < s_ < cut for s_, _ in kept)
+
+
+def test_recovery_inserts_probes_in_deficient_slices():
+    # host logic of Section 3.3 with the probes mocked: slice 1 reports a missing
+    # eigenvalue, so the next run gets a probe inside (sigma_0, sigma_1) and the old probes
+    # restart from their vectors
+    from types import SimpleNamespace
+    from paper_1908_06043_gb300.driver import SliceSolver
+    calls = []
+
+    class Fake(SliceSolver):
+        def __init__(self):
+            pass
+
+        def run(self, shifts, lam_min, lam_max, model=None, **kw):
+            calls.append((list(shifts), kw.get("V0")))
+            ok = len(calls) > 1
+            ns = len(shifts)
+            slices = [(10, 10, 10 if ok or s_ != 1 else 9, "ok") for s_ in range(ns + 1)]
+            probes = [SimpleNamespace(X="X%d" % j) for j in range(ns)]
+            return SimpleNamespace(timings={"converged": ok}, slices=slices, probes=probes, shifts=list(shifts))
+
+    res = Fake().run_with_recovery([0.0, 1.0, 2.0], -1.0, 3.0, None)
+    assert res.timings["converged"] and res.timings["inserted"] == [[0.5]]
+    assert calls[1][0] == [0.0, 0.5, 1.0, 2.0]
+    assert calls[1][1] == ["X0", None, "X1", "X2"]
