@@ -1,4 +1,4 @@
-"""Host-side SISLICE logic over the CUDA library (Alg. 1 with a fixed pencil, Sec. 2-3).
+"""Host-side SISLICE logic over the CUDA library (Alg. 1, Sections 2-3).
 
 The device work -- factorisations, inertia, in-slice iterations, DOS sweeps -- runs in
 the library; this module sequences it and holds the O(n_s k) scalar logic:
@@ -12,10 +12,16 @@ the library; this module sequences it and holds the O(n_s k) scalar logic:
   eigenvalues, from the DOS estimate and exact inertia counts.
 * ``validate``: candidates split at the slice midpoints, exact counts from inertia,
   the three cases of Section 2.2.
-* ``kmeans_shifts``: k-means++ seeding and Lloyd iterations on validated Ritz values
-  (Section 3.2); the uniforms are passed in.
+* ``ball_partition`` and ``dos_cluster_partition``: shift placement for non-uniform and
+  clustered spectra (the latter is Alg. 3, DOSCluster, with its refinement).
+* ``kmeans_shifts``, ``kmeans_pp_seeds``, ``migrate_probes``: k-means++ seeding, Lloyd
+  iterations and the probe migration between SCF steps (Section 3.2); the uniforms are
+  passed in.
 * ``SliceSolver.run``: factor every shift (one batched call), inertia, probes, rounds of
-  subspace iterations until every slice validates.
+  subspace iterations until every slice validates; ``run_with_recovery`` inserts probes
+  where eigenvalues are missing (Section 3.3).
+* ``solve_sequence``: a sequence of pencils on one pattern with migration, warm starts and
+  the trace monitor of Eq. 9.
 """
 from __future__ import annotations
 
