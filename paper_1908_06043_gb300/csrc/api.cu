@@ -230,11 +230,22 @@ int ss_norm1(ss_symbolic *s, const double *vals, double *out) {
 }
 
 // ------------------------------------------------------------------ numeric factorisation
+// Large dynamic shared memory is a per-device function attribute: set once per device
+// (the caller has made that device current).
+static bool first_use_on_device(int device, std::mutex &mu, std::vector<char> &seen) {
+    std::lock_guard<std::mutex> lock(mu);
+    if (device < 0) return false;
+    if ((size_t)device >= seen.size()) seen.resize(device + 1, 0);
+    if (seen[device]) return false;
+    seen[device] = 1;
+    return true;
+}
+
 template <typename T>
-static void set_smem_attrs() {
-    static bool done = false;
-    if (done) return;
-    done = true;
+static void set_smem_attrs(int device) {
+    static std::mutex mu;
+    static std::vector<char> seen;
+    if (!first_use_on_device(device, mu, seen)) return;
     cudaFuncSetAttribute(k_diag_bk<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagSmem);
     cudaFuncSetAttribute(k_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)panel_smem<T>());
     cudaFuncSetAttribute(k_schur<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)schur_smem<T>());
@@ -250,7 +261,7 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
-    set_smem_attrs<T>();
+    set_smem_attrs<T>(ctx->device);
     const int ns = (int)which.size();
     if (ns == 0) return SS_OK;
     const int64_t npan = (int64_t)s->panels.size();
@@ -609,7 +620,7 @@ static int solve_levels(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
-    set_smem_attrs<T>();
+    set_smem_attrs<T>(ctx->device);
     const T *arena = (const T *)f->arena[j];
     if (std::is_same<T, float>::value && f->arena_lo[j]) arena = (const T *)f->arena_lo[j];
     if (ctx->solve_mode == SS_SOLVE_SWEEP_KERNEL) return solve_sweeps<T>(f, j, b, k, forward, backward, dinv, arena);
@@ -918,11 +929,10 @@ extern "C" ss_status ss_band_energy_grad(ss_symbolic *s, const double *X, const 
     const size_t smem = sizeof(double) * 2 * (size_t)n_e;
     if (smem > 220 * 1024) return ctx->set_error(SS_ERR_ARG, "ss_band_energy_grad: n_e too large (max 14080)");
     SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
-    static bool attr = false;
-    if (!attr) {
+    static std::mutex attr_mu;
+    static std::vector<char> attr_seen;
+    if (first_use_on_device(ctx->device, attr_mu, attr_seen))
         cudaFuncSetAttribute(sss::k_sddmm, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr = true;
-    }
     ss_launch(ctx, SS_K_SDDMM, sss::k_sddmm, (unsigned)s->n, 256, smem, ctx->stream, s->n, s->d_rowptr, s->d_colind, X, lambda, n_e,
                                                              grad_a, grad_b);
     SS_CUDA_TRY(ctx, cudaGetLastError());
@@ -987,7 +997,7 @@ extern "C" ss_status ss_solve_noalloc(ss_numeric *f, int32_t j, const double *R,
     if (rc != SS_OK) return rc;
     double *z = w + zoff;
     cudaStream_t st = ctx->stream;
-    set_smem_attrs<double>();
+    set_smem_attrs<double>(ctx->device);
     const unsigned g = (unsigned)((nk + 255) / 256);
     ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, (int)k, s->d_perm, R, w, 0);
     const double *arena = (const double *)f->arena[j];
