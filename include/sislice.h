@@ -206,9 +206,12 @@ ss_status ss_factor_stats(const ss_numeric *f, int32_t shift_idx, double *min_pi
                           double *max_abs_l, int64_t *n_2x2);
 
 /* ---- ss_solve (Alg. 2 step 3 without B: X = (A - sigma_j B)^-1 R) ------------------
- * R and X are DEVICE float64 N x k row-major (may alias).  For a mixed factor, `refine`
- * FP64 refinement corrections are applied (residual by FP64 SpMM with A and B).
- * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM. */
+ * R and X are DEVICE float64 N x k row-major (may alias).  `refine` FP64 iterative
+ * refinement corrections are applied (X += M^-1 (R - (A - sigma_j B) X)); for a shift
+ * solved in FP32 at least as many as its contraction factor needs to reach 1e-13 (at
+ * most 8).  The residual uses the values of A - sigma_j B, formed on the shift's first
+ * refined solve and kept with the factor (nnz doubles per shift).
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_TIMEOUT (sweep kernel barrier). */
 ss_status ss_solve(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k, double *X,
                    int32_t refine);
 
@@ -234,7 +237,9 @@ ss_status ss_solve_noalloc(ss_numeric *f, int32_t shift_idx, const double *R, in
  * the B inner product, Rayleigh-Ritz, residual norms; Section 2.1; or the shift-invert
  * block Lanczos the paper names as its alternative, Section 1) ----------------------
  * Builds the spectral probe of shift sigma_j.  V0 is the DEVICE N x k start block
- * (seeded N(0,1) or a previous probe's X; required).  SS_SUBSPACE iterates on k
+ * (seeded N(0,1) or a previous probe's X; required; k <= min(N, 4096)).  Solves of a
+ * shift solved in FP32 are refined once the window is near convergence, until their
+ * residual is 1e-3 of the window's current residual (1e-13 .. 1e-8).  SS_SUBSPACE iterates on k
  * vectors and returns k Ritz pairs.  SS_BLOCK_LANCZOS builds max_iter blocks of width k
  * (O = (A - sigma B)^-1 B, full B-re-orthogonalisation), does one Rayleigh-Ritz on the
  * whole basis and returns the k_out Ritz pairs nearest sigma.
