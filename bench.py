@@ -366,8 +366,20 @@ def main():
                     "(CUDA-core FP64; MEASURED_PEAKS.json has no FP64 figure)")
     else:
         achieved, bound, unit, peak, peak_src = None, "unknown", None, None, None
+    traffic, traffic_src = None, None
+    if dom == "solve" and dom_n > 0 and info["l_offdiag_entries"] > 0:
+        # DRAM bytes per launch of the FP64 sweep solve, scaled from one ncu capture
+        # (k = 304 probe solve on this pencil: 832.3 MB read + 91.1 MB written) by the
+        # launch's width: L is read once per sweep, the N x k right-hand sides four times
+        k_avg = dom_flops / dom_n / (4.0 * info["l_offdiag_entries"])
+        def model(k):
+            return 2 * 8.0 * info["l_offdiag_entries"] + 4 * 8.0 * p.n * k
+        traffic = (832.3e6 + 91.1e6) * model(k_avg) / model(304)
+        traffic_src = (f"ncu dram__bytes_read+write of one k=304 launch on the N=16384 pencil, scaled to the "
+                       f"mean launch width k={k_avg:.0f} by the L + 4 N k model")
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": (achieved / peak) if achieved and peak else None, "traffic": None,
+                "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic,
+                "traffic_source": traffic_src,
                 "launches": dom_n, "avg_launch_ms": 1e3 * per_launch,
                 "share_of_profiled_time": prof[dom][1] / tot_prof if tot_prof else None,
                 "peak_source": peak_src}
