@@ -224,7 +224,10 @@ ss_status ss_solve(ss_numeric *f, int32_t shift_idx, const double *R, int32_t k,
  * right-hand sides followed by (widest solve level) x 64 x k doubles of gather buffer.
  * The caller passes R and X (DEVICE float64 N x k row-major, may alias) as for
  * ss_solve.  The first call on a device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every call shares
+ * device current; make that first call before any stream capture.  The address is kept
+ * for the life of the process: a cudaDeviceReset (which destroys the array with the
+ * device's context) leaves it stale, so do not call this entry point on a device after
+ * resetting it.  Every call shares
  * the array and it keeps the last call's contents (the call clears the parts it needs
  * cleared), so calls that overlap on the GPU -- on two streams, or two contexts of the
  * same device -- race: serialise them.

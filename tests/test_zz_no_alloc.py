@@ -42,12 +42,41 @@ def test_noalloc_solve_matches_ss_solve_twice(gpu_lib):
             assert (res.norm() / R.norm()).item() <= 1e-8
 
 
+def test_noalloc_in_place(gpu_lib):
+    """R and X may be the same buffer: the right-hand sides are copied into the scratch
+    array before anything is written to X."""
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    f = sym.factor(a, b, [0.2], "fp64")
+    R = torch.tensor(normal_block(p.n, 12, 5), device="cuda")
+    ref = f.solve(0, R, refine=0)
+    RX = R.clone()
+    rc = f.ctx.lib.ss_solve_noalloc(f.h, 0, C.c_void_p(RX.data_ptr()), RX.shape[1], C.c_void_p(RX.data_ptr()))
+    f.ctx.check(rc, "ss_solve_noalloc")
+    torch.cuda.synchronize()
+    assert ((RX - ref).norm() / ref.norm()).item() <= 1e-9
+
+
 def test_noalloc_rejects_oversized(gpu_lib):
     p = config_pencil(1)
     ctx, sym, a, b = setup(gpu_lib, p)
     f = sym.factor(a, b, [0.2], "fp64")
+    # N k alone beyond the array
     too_many = 4_194_304 // p.n + 1
     R = torch.zeros((p.n, too_many), dtype=torch.float64, device="cuda")
     with pytest.raises(gpu_lib.SisliceError) as ei:
         _noalloc(f, 0, R)
     assert "exceeds" in str(ei.value)
+    # N k fits, but the backward sweep's gather buffer (64 k per panel of the widest
+    # solve level) does not
+    fits = 4_194_304 // p.n
+    R = torch.zeros((p.n, fits), dtype=torch.float64, device="cuda")
+    with pytest.raises(gpu_lib.SisliceError) as ei:
+        _noalloc(f, 0, R)
+    assert "exceeds" in str(ei.value)
+    # the context stays usable after a rejected call
+    R = torch.tensor(normal_block(p.n, 4, 9), device="cuda")
+    X = _noalloc(f, 0, R)
+    torch.cuda.synchronize()
+    ref = f.solve(0, R, refine=0)
+    assert ((X - ref).norm() / ref.norm()).item() <= 1e-9
