@@ -17,6 +17,7 @@ def lib():
         P = C.c_void_p
         i64 = C.c_int64
         _lib.or_gen_eig.argtypes = [i64, P, P, P, P]
+        _lib.or_gen_eig_lowest.argtypes = [i64, P, P, i64, P, P]
         _lib.or_tridiag_eig.argtypes = [i64, P, P, P, P]
         _lib.or_ldlt_bk.argtypes = [i64, P, P, P, P]
         _lib.or_band_ldlt.argtypes = [i64, i64, P, P, P]
@@ -46,6 +47,24 @@ def gen_eig(A: np.ndarray, B: np.ndarray, vectors: bool = True):
         raise np.linalg.LinAlgError("B is not positive definite")
     if rc:
         raise RuntimeError(f"or_gen_eig failed ({rc})")
+    return lam, X
+
+
+def gen_eig_lowest(A: np.ndarray, B: np.ndarray, m: int):
+    """The lowest m eigenpairs of A x = lambda B x (Eq. 1) by the same reduction as
+    gen_eig, with the tridiagonal matrix's eigenvectors from inverse iteration and the
+    Householder back-transform (no full set of vectors is formed).  Returns (theta, X):
+    theta the eigenvalues of the reduced matrix, X (n x m) with x^T B x = 1."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    n = A.shape[0]
+    lam = np.empty(m)
+    X = np.empty((n, m))
+    rc = lib().or_gen_eig_lowest(n, _p(A), _p(B), m, _p(lam), _p(X))
+    if rc == 1:
+        raise np.linalg.LinAlgError("B is not positive definite")
+    if rc:
+        raise RuntimeError(f"or_gen_eig_lowest failed ({rc})")
     return lam, X
 
 

@@ -17,9 +17,16 @@
  *                   inertia by Sylvester's law when every pivot is well away from 0.
  *  or_csr_mm        Y = M X for a CSR matrix and a row-major block X (residuals).
  *  or_tridiag_eig   eigenpairs of a symmetric tridiagonal matrix (Lanczos DOS, Eq. 5).
+ *  or_gen_eig_lowest the lowest m eigenpairs of the pencil by the same reduction, with
+ *                   the eigenvectors of the tridiagonal matrix from inverse iteration
+ *                   (Gaussian elimination with partial pivoting on T - theta I) and the
+ *                   Householder back-transform; the caller takes the Rayleigh quotient
+ *                   x^T A x / x^T B x of each x on the original pencil, which removes the
+ *                   first-order error that forming L^-1 A L^-T leaves in theta when B is
+ *                   ill-conditioned.
  *
  * Return codes: 0 ok, 1 not SPD (Cholesky hit a non-positive pivot), 2 QL did not
- * converge, 3 a band pivot fell below the reliability threshold.
+ * converge, 3 a band pivot fell below the reliability threshold, 4 bad size.
  */
 #include <math.h>
 #include <stdint.h>
@@ -285,6 +292,158 @@ int or_gen_eig(int64_t n, const double *A, const double *B, double *lam, double 
     }
 done:
     free(L); free(W); free(C); free(e);
+    return rc;
+}
+
+/* ---- one eigenvector of the tridiagonal T (diagonal d, off-diagonal e[i] coupling i and
+ * i+1) for an eigenvalue estimate theta: inverse iteration y <- (T - theta I)^-1 y with
+ * Gaussian elimination with partial pivoting (the row-interchange LU of a tridiagonal
+ * matrix: U has a diagonal and two super-diagonals).  Each iterate is orthogonalised
+ * against the vectors in prev[0..nprev) (eigenvectors already found for estimates in the
+ * same cluster), then normalised.  A zero pivot is replaced by eps * ||T||_1. */
+static void tridiag_inverse_iteration(int64_t n, const double *d, const double *e, double theta,
+                                      double tnorm, int iters, const double *const *prev, int nprev,
+                                      double *y, double *u0, double *u1, double *u2, double *mult,
+                                      unsigned char *piv) {
+    const double tiny = 2.220446049250313e-16 * (tnorm > 0.0 ? tnorm : 1.0);
+    /* factor T - theta I */
+    for (int64_t i = 0; i < n; ++i) { u0[i] = d[i] - theta; u1[i] = (i + 1 < n) ? e[i] : 0.0; u2[i] = 0.0; }
+    for (int64_t i = 0; i + 1 < n; ++i) {
+        const double sub = e[i];                 /* M[i+1][i] */
+        if (fabs(sub) > fabs(u0[i])) {           /* swap rows i and i+1 */
+            const double m = u0[i] / sub;
+            const double r1 = u1[i], r2 = u2[i];     /* old row i at columns i+1, i+2 */
+            const double a1 = u0[i + 1], b1 = u1[i + 1];  /* old row i+1 at columns i+1, i+2 */
+            u0[i] = sub; u1[i] = a1; u2[i] = b1;
+            u0[i + 1] = r1 - m * a1;
+            u1[i + 1] = r2 - m * b1;
+            mult[i] = m;
+            piv[i] = 1;
+        } else {
+            if (u0[i] == 0.0) u0[i] = tiny;
+            const double m = sub / u0[i];
+            u0[i + 1] -= m * u1[i];
+            u1[i + 1] -= m * u2[i];
+            mult[i] = m;
+            piv[i] = 0;
+        }
+    }
+    if (u0[n - 1] == 0.0) u0[n - 1] = tiny;
+    /* start vector: all ones */
+    for (int64_t i = 0; i < n; ++i) y[i] = 1.0;
+    for (int it = 0; it < iters; ++it) {
+        /* forward: apply the row operations to y */
+        for (int64_t i = 0; i + 1 < n; ++i) {
+            if (piv[i]) { double t = y[i]; y[i] = y[i + 1]; y[i + 1] = t - mult[i] * y[i]; }
+            else y[i + 1] -= mult[i] * y[i];
+        }
+        /* back substitution with U */
+        for (int64_t i = n - 1; i >= 0; --i) {
+            double s = y[i];
+            if (i + 1 < n) s -= u1[i] * y[i + 1];
+            if (i + 2 < n) s -= u2[i] * y[i + 2];
+            y[i] = s / u0[i];
+        }
+        for (int q = 0; q < nprev; ++q) {
+            double dot = 0.0;
+            for (int64_t i = 0; i < n; ++i) dot += prev[q][i] * y[i];
+            for (int64_t i = 0; i < n; ++i) y[i] -= dot * prev[q][i];
+        }
+        double nrm = 0.0;
+        for (int64_t i = 0; i < n; ++i) nrm += y[i] * y[i];
+        nrm = sqrt(nrm);
+        for (int64_t i = 0; i < n; ++i) y[i] /= nrm;
+    }
+}
+
+/* The lowest m eigenpairs of A x = lambda B x (dense row-major, symmetric A, SPD B):
+ * Cholesky B = L L^T, C = L^-1 A L^-T, Householder tridiagonalisation C = Q T Q^T,
+ * eigenvalues of T by implicit QL (ascending), the eigenvector of T for each of the m
+ * lowest by inverse iteration (three steps; estimates closer than 1e-3 max(1, |theta|)
+ * to the previous one form a cluster whose vectors are orthogonalised), then z = Q y
+ * (the reflectors applied in reverse order) and x = L^-T z, so x^T B x = 1.
+ * lam[m] (eigenvalues of T, ascending), X (n x m row-major, column j = vector j). */
+int or_gen_eig_lowest(int64_t n, const double *A, const double *B, int64_t m, double *lam, double *X) {
+    if (m < 1 || m > n) return 4;
+    size_t nn = (size_t)n * (size_t)n;
+    double *L = (double *)malloc(sizeof(double) * nn);
+    double *W = (double *)malloc(sizeof(double) * nn);
+    double *C = (double *)malloc(sizeof(double) * nn);
+    double *d = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *e = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *th = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *ee = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *Y = NULL;
+    int rc = cholesky_lower(n, B, L);
+    if (rc) goto done;
+    forward_subst(n, n, L, A, W);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) C[IDX(i, j, n)] = W[IDX(j, i, n)];
+    forward_subst(n, n, L, C, W);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) C[IDX(i, j, n)] = 0.5 * (W[IDX(i, j, n)] + W[IDX(j, i, n)]);
+    householder_tridiag(n, C, d, e, W);           /* W now holds the reflectors */
+    memcpy(th, d, sizeof(double) * (size_t)n);
+    memcpy(ee, e, sizeof(double) * (size_t)n);
+    rc = tridiag_ql(n, th, ee, NULL);
+    if (rc) goto done;
+    sort_eig(n, th, NULL, NULL);
+    {
+        double tnorm = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double r = fabs(d[i]) + (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+            if (r > tnorm) tnorm = r;
+        }
+        /* eigenvectors of T: vector j stored contiguously in C (free now), row j */
+        double *u0 = (double *)malloc(sizeof(double) * (size_t)n);
+        double *u1 = (double *)malloc(sizeof(double) * (size_t)n);
+        double *u2 = (double *)malloc(sizeof(double) * (size_t)n);
+        double *mu = (double *)malloc(sizeof(double) * (size_t)n);
+        unsigned char *pv = (unsigned char *)malloc((size_t)n);
+        const double **prev = (const double **)malloc(sizeof(double *) * (size_t)m);
+        int64_t c0 = 0;                          /* first index of the current cluster */
+        for (int64_t j = 0; j < m; ++j) {
+            if (j > 0 && !(th[j] - th[j - 1] <= 1e-3 * (fabs(th[j]) > 1.0 ? fabs(th[j]) : 1.0))) c0 = j;
+            int np = 0;
+            for (int64_t q = c0; q < j; ++q) prev[np++] = C + IDX(q, 0, n);
+            tridiag_inverse_iteration(n, d, e, th[j], tnorm, 3, prev, np, C + IDX(j, 0, n), u0, u1, u2, mu, pv);
+            lam[j] = th[j];
+        }
+        free(u0); free(u1); free(u2); free(mu); free(pv); free(prev);
+        /* Y (n x m row-major) = the vectors of T as columns, then Y <- Q Y with
+         * Q = H_0 H_1 ... H_{n-3}: H_{n-3} first */
+        Y = (double *)malloc(sizeof(double) * (size_t)n * (size_t)m);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t j = 0; j < m; ++j) Y[IDX(i, j, m)] = C[IDX(j, i, n)];
+        const int64_t cb = 64;
+#pragma omp parallel for schedule(dynamic)
+        for (int64_t q0 = 0; q0 < m; q0 += cb) {
+            const int64_t q1 = q0 + cb < m ? q0 + cb : m;
+            double s[64];
+            for (int64_t k = n - 3; k >= 0; --k) {
+                const double *v = W + IDX(k, 0, n);
+                for (int64_t q = q0; q < q1; ++q) s[q - q0] = 0.0;
+                for (int64_t r = k + 1; r < n; ++r) {
+                    const double vr = v[r];
+                    if (vr == 0.0) continue;
+                    const double *yr = Y + IDX(r, 0, m);
+                    for (int64_t q = q0; q < q1; ++q) s[q - q0] += vr * yr[q];
+                }
+                for (int64_t r = k + 1; r < n; ++r) {
+                    const double vr2 = 2.0 * v[r];
+                    if (vr2 == 0.0) continue;
+                    double *yr = Y + IDX(r, 0, m);
+                    for (int64_t q = q0; q < q1; ++q) yr[q] -= vr2 * s[q - q0];
+                }
+            }
+        }
+        backward_subst_t(n, m, L, Y, X);
+    }
+done:
+    free(L); free(W); free(C); free(d); free(e); free(th); free(ee); free(Y);
     return rc;
 }
 

@@ -126,3 +126,75 @@ def test_csr_mm_matches_dense():
     p = gaussian_pencil((3, 2, 2), seed=3)
     X = np.random.default_rng(0).standard_normal((p.n, 5))
     assert np.allclose(dense.csr_mm(p.rowptr, p.colind, p.a, X), p.dense("a") @ X, atol=1e-13)
+
+
+# ---- lowest eigenpairs: inverse iteration + back-transform + Rayleigh quotient (Eq. 1)
+@pytest.mark.parametrize("mass", [False, True])
+def test_lowest_eigenpairs_laplacian_closed_form(mass):
+    n = 80
+    p = laplacian_1d(n, mass=mass)
+    lam, X = spectral.lowest_eigenpairs(p, 20)
+    k = np.arange(1, 21)
+    th = k * np.pi / (n + 1)
+    ref = 2 - 2 * np.cos(th)
+    if mass:
+        ref = ref / ((4 + 2 * np.cos(th)) / 6)
+    assert np.abs(lam - ref).max() <= 1e-13
+    # eigenvectors are the sines, B-normalised (up to sign)
+    j = np.arange(1, n + 1)
+    B = p.dense("b")
+    for c in range(20):
+        s = np.sin(j * (c + 1) * np.pi / (n + 1))
+        s /= np.sqrt(s @ B @ s)
+        assert min(np.abs(X[:, c] - s).max(), np.abs(X[:, c] + s).max()) <= 1e-10
+
+
+def test_lowest_eigenpairs_gaussian_vs_lapack():
+    p = gaussian_pencil((3, 3, 3), seed=5)
+    A, B = p.dense("a"), p.dense("b")
+    lam, X = spectral.lowest_eigenpairs(p, 40)
+    w = sla.eigh(A, B, eigvals_only=True)[:40]
+    assert np.abs(lam - w).max() <= 1e-12 * max(1.0, np.abs(w).max())
+    assert np.abs(X.T @ B @ X - np.eye(40)).max() <= 1e-10
+    assert spectral.residual_norms(p, lam, X).max() <= 1e-12
+
+
+def _ill_conditioned_pencil(n, seed, bmin):
+    """B = Q diag(b) Q^T with b log-spaced in [bmin, 1], A = Q diag(lambda b) Q^T plus a
+    small symmetric perturbation, lambda ~ U(-50, 10): the low eigenvectors are
+    B-normalised with ||x||_2 up to about bmin^-1/2, as on the low tail of the Gaussian
+    pencils."""
+    from workloads.pencils import Pencil
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    b = np.logspace(np.log10(bmin), 0, n)
+    a = rng.uniform(-50, 10, n) * b
+    B = (Q * b) @ Q.T
+    B = 0.5 * (B + B.T)
+    E = 1e-3 * rng.standard_normal((n, n))
+    A = (Q * a) @ Q.T + E + E.T
+    A = 0.5 * (A + A.T)
+    rows, cols = np.nonzero(np.ones((n, n)))
+    rowptr = np.arange(0, n * n + 1, n, dtype=np.int64)
+    return Pencil(n, rowptr, cols.astype(np.int32), A[rows, cols].copy(), B[rows, cols].copy())
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_lowest_eigenpairs_extended_precision_on_ill_conditioned_b(seed):
+    """Against eigenvalues computed in 40-digit arithmetic (Cholesky reduction and a
+    symmetric eigensolver in mpmath) on a pencil whose low eigenvectors have ||x||_2 of a
+    few hundred at ||x||_B = 1."""
+    mp = pytest.importorskip("mpmath")
+    n, m = 32, 8
+    p = _ill_conditioned_pencil(n, seed, 1e-6)
+    mp.mp.dps = 40
+    A = mp.matrix(p.dense("a").tolist())
+    B = mp.matrix(p.dense("b").tolist())
+    Li = mp.inverse(mp.cholesky(B))
+    C = Li * A * Li.T
+    C = (C + C.T) / 2
+    ref = np.array(sorted(float(v) for v in mp.eigsy(C, eigvals_only=True)))[:m]
+    lam, X = spectral.lowest_eigenpairs(p, m)
+    assert np.abs(X).max() > 100.0
+    rel = np.abs(lam - ref) / np.maximum(np.abs(ref), 1.0)
+    assert rel.max() <= 1e-10, rel
