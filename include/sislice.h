@@ -44,6 +44,8 @@ enum {
 };
 
 enum { SS_FP64 = 0, SS_MIXED = 1 };      /* factor precision                     */
+enum { SS_INERTIA_ONLY = 4 };              /* or-ed into the precision of ss_factor: FP64
+                                              fronts, only the inertia is kept          */
 enum { SS_FP64_SOLVE32 = 2 };              /* reported only: FP64 factor, FP32 solves */
 enum { SS_SUBSPACE = 0, SS_BLOCK_LANCZOS = 1 };  /* in-slice driver             */
 
@@ -76,6 +78,12 @@ typedef struct ss_symbolic_info {
                                    diagonal blocks (read once per triangular sweep)  */
     int64_t l_diag_entries;     /* sum over panels of w^2                            */
     double analyze_seconds;
+    /* memory plan of one shift's factorisation (entries of the factor's type):         */
+    int64_t l_storage_entries;  /* L kept for the solves: sum of m * ncol, 256-byte
+                                   aligned blocks                                   */
+    int64_t workspace_entries;  /* the fronts of the widest level (reused per level) */
+    int64_t cb_pool_entries;    /* peak of the contribution blocks awaiting their
+                                   parent's extend-add                              */
 } ss_symbolic_info;
 
 /* Per-probe statistics of one slice solve. */
@@ -128,6 +136,25 @@ const char *ss_last_error(const ss_ctx *ctx);
 enum { SS_SOLVE_SWEEP_KERNEL = 0, SS_SOLVE_PER_STEP = 1 };
 ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
 
+/* Where the FP64 Schur-complement updates of ss_factor run (Alg. 2 step 2; an
+ * implementation choice with no paper counterpart).  SS_SCHUR_TENSOR (default): a factor
+ * step whose Schur update has at least min_flops algorithmic flops [2e7] runs on the FP16
+ * tensor cores (tcgen05.mma, operands staged by bulk copies into shared memory, FP32
+ * accumulators in tensor memory) with the operands cut into 7 exactly representable
+ * 8-bit slices per row, so that the update is as accurate as an FP64 product (the
+ * error-free splitting of Ozaki, Ogita, Oishi and Rump); smaller steps, and every FP32
+ * factor, run on the CUDA cores.  SS_SCHUR_SIMT: every update on the CUDA cores.
+ * Errors: SS_ERR_ARG. */
+enum { SS_SCHUR_TENSOR = 0, SS_SCHUR_SIMT = 1 };
+ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops);
+
+/* Self-test of the tensor-core path (no paper counterpart): one 128 x 64 x 64 FP16 MMA tile
+ * with seeded integer operands in [-128, 128], staged and read back exactly as the Schur
+ * update does; *max_abs_err (HOST) is the largest deviation from the exact product (0 when
+ * the operand layout and descriptors are right).  Errors: SS_ERR_ARG, SS_ERR_CUDA,
+ * SS_ERR_TIMEOUT (a bounded wait ran out; the context stays usable). */
+ss_status ss_selftest_tc(ss_ctx *ctx, uint64_t seed, double *max_abs_err);
+
 /* Self-test of the bounded grid barrier used by the cooperative kernels (no paper
  * counterpart): one block per SM waits at a barrier that expects extra_arrivals (0 or 1)
  * more blocks than are launched, polling at most `limit` times (1 .. 1e8; a poll takes
@@ -172,7 +199,13 @@ ss_status ss_symbolic_validate(const ss_symbolic *sym);
  * shift is refactored in FP64.  The FP64 factor of such a shift is then rounded once to
  * FP32; if one FP32 solve from the rounded copy contracts by rho <= 0.25, the shift's
  * solves run in FP32 inside FP64 refinement, else in FP64 (ss_factor_quality reports
- * which).
+ * which).  precision | SS_INERTIA_ONLY factors in FP64 and keeps no L (inertia,
+ * ss_factor_stats only; solves on such a factor return SS_ERR_ARG): the counts at many
+ * shifts at a fraction of the memory.
+ * Memory: each shift keeps its L storage (info.l_storage_entries); while it is factored
+ * it also holds a level workspace and a contribution-block pool (workspace_entries +
+ * cb_pool_entries), so shifts are factored in waves of as many as the free device memory
+ * holds.
  * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_SINGULAR (a pivot fell below
  * 64 u ||A - sigma B||_1 for some shift; the factor is still returned and
  * ss_inertia reports which shift). */
@@ -301,6 +334,15 @@ ss_status ss_spmm(ss_symbolic *sym, const double *a_vals, const double *b_vals,
                   const double *alpha, const double *beta, const double *X, int32_t k,
                   double *Y);
 
+/* Measured arithmetic peak of the context's GPU (no paper counterpart; the roofline
+ * denominator of the CUDA-core kernels): one launch of kIlp = 8 independent fused
+ * multiply-add chains per thread, 4 blocks of 256 threads per SM, its length grown until
+ * the launch takes about `seconds` (0 < seconds <= 10).  *tflops (HOST) = 2 flops per FMA
+ * over the launch's CUDA-event time.  kind: SS_PEAK_FP64_FMA or SS_PEAK_FP32_FMA.
+ * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM. */
+enum { SS_PEAK_FP64_FMA = 0, SS_PEAK_FP32_FMA = 1 };
+ss_status ss_measure_peak(ss_ctx *ctx, int32_t kind, double seconds, double *tflops);
+
 /* Device synchronisation of the context's stream (convenience for bindings). */
 ss_status ss_sync(ss_ctx *ctx);
 
@@ -319,13 +361,14 @@ enum {
     SS_K_GEMM, SS_K_SMALL_DENSE, SS_K_JACOBI, SS_K_LANCZOS, SS_K_SDDMM, SS_K_MISC,
     SS_K_PANEL_F32, SS_K_SCHUR_F32, SS_K_FWD_UPDATE_F32, SS_K_BWD_GATHER_F32,
     SS_K_SOLVE, SS_K_SOLVE_F32,   /* whole-solve sweep kernel (SS_SOLVE_SWEEP_KERNEL) */
+    SS_K_SCHUR_TC,                /* tensor-core Schur update (slicing + MMA tiles)    */
     SS_K_COUNT
 };
 int64_t ss_launch_count(void);
 ss_status ss_profile(ss_ctx *ctx, uint32_t mask);
 /* *flops (may be NULL): algorithmic flops of the timed launches of the classes that
- * count them (panel, Schur, solve sweeps, SpMM, Gram, GEMM; 2 per multiply-add, lower
- * triangle only for the Schur update); 0 for the others.  Classes ending in _F32 are the
+ * count them (panel, Schur (both paths), solve sweeps, SpMM, Gram, GEMM; 2 per multiply-add,
+ * lower triangle only for the Schur update); 0 for the others.  Classes ending in _F32 are the
  * FP32 instantiations of the mixed-precision factor and solves. */
 ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds, double *flops);
 

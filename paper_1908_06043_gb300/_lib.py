@@ -14,8 +14,11 @@ LIB_PATH = os.path.join(HERE, "_build", "libsislice.so")
 SS_OK, SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_SINGULAR, SS_ERR_NOT_SPD, SS_ERR_NOCONV, \
     SS_ERR_TIMEOUT, SS_ERR_INTERNAL = range(9)
 SS_FP64, SS_MIXED, SS_FP64_SOLVE32 = 0, 1, 2
+SS_INERTIA_ONLY = 4
 SS_SOLVE_SWEEP_KERNEL, SS_SOLVE_PER_STEP = 0, 1
 SS_SUBSPACE, SS_BLOCK_LANCZOS = 0, 1
+SS_PEAK_FP64_FMA, SS_PEAK_FP32_FMA = 0, 1
+SS_SCHUR_TENSOR, SS_SCHUR_SIMT = 0, 1
 STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_SINGULAR",
                 5: "SS_ERR_NOT_SPD", 6: "SS_ERR_NOCONV", 7: "SS_ERR_TIMEOUT", 8: "SS_ERR_INTERNAL"}
 
@@ -29,7 +32,8 @@ class ss_symbolic_info(C.Structure):
                 ("n_levels", C.c_int64), ("n_panels", C.c_int64), ("n_panel_levels", C.c_int64),
                 ("max_front", C.c_int64), ("factor_entries", C.c_int64), ("front_entries", C.c_int64),
                 ("factor_flops", C.c_double), ("schur_flops", C.c_double), ("panel_flops", C.c_double),
-                ("l_offdiag_entries", C.c_int64), ("l_diag_entries", C.c_int64), ("analyze_seconds", C.c_double)]
+                ("l_offdiag_entries", C.c_int64), ("l_diag_entries", C.c_int64), ("analyze_seconds", C.c_double),
+                ("l_storage_entries", C.c_int64), ("workspace_entries", C.c_int64), ("cb_pool_entries", C.c_int64)]
 
 
 class ss_probe_stats(C.Structure):
@@ -45,10 +49,11 @@ class ss_solve_opts(C.Structure):
 
 EXPORTS = ["ss_create", "ss_destroy", "ss_last_error", "ss_analyze", "ss_symbolic_info_get",
            "ss_symbolic_perm", "ss_symbolic_destroy", "ss_symbolic_validate", "ss_factor", "ss_factor_destroy", "ss_inertia", "ss_factor_stats", "ss_factor_quality",
-           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode", "ss_selftest_barrier"]
+           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode", "ss_selftest_barrier", "ss_measure_peak", "ss_set_schur_mode", "ss_selftest_tc"]
 KERNEL_CLASSES = ["assemble", "extend_add", "diag_bk", "panel", "schur", "fwd_diag", "fwd_update", "bwd_gather",
                   "bwd_diag", "permute", "spmm", "gram", "gemm", "small_dense", "jacobi", "lanczos", "sddmm", "misc",
-                  "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32", "solve", "solve_f32"]
+                  "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32", "solve", "solve_f32",
+                  "schur_tc"]
 
 _lib = None
 
@@ -69,6 +74,9 @@ def load():
         "ss_last_error": ([P], C.c_char_p),
         "ss_set_solve_mode": ([P, i32], i32),
         "ss_selftest_barrier": ([P, i32, C.c_int64], i32),
+        "ss_measure_peak": ([P, i32, dbl, C.POINTER(dbl)], i32),
+        "ss_set_schur_mode": ([P, i32, dbl], i32),
+        "ss_selftest_tc": ([P, C.c_uint64, C.POINTER(dbl)], i32),
         "ss_analyze": ([P, i64, P, P, C.POINTER(ss_options), PP], i32),
         "ss_symbolic_info_get": ([P, C.POINTER(ss_symbolic_info)], i32),
         "ss_symbolic_perm": ([P, P], i32),

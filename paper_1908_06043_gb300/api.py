@@ -81,6 +81,25 @@ class Context:
         """Run the bounded grid-barrier self-test (raises SisliceError on a timeout)."""
         self.check(self.lib.ss_selftest_barrier(self.h, extra_arrivals, limit), "ss_selftest_barrier")
 
+    def set_schur_mode(self, mode: str, min_flops: float = 2e7):
+        """"tensor": FP64 Schur updates of factor steps with >= min_flops flops on the
+        tensor cores (sliced FP16 operands, FP64-accurate); "simt": all on CUDA cores."""
+        m = {"tensor": L.SS_SCHUR_TENSOR, "simt": L.SS_SCHUR_SIMT}[mode]
+        self.check(self.lib.ss_set_schur_mode(self.h, m, float(min_flops)), "ss_set_schur_mode")
+
+    def selftest_tc(self, seed: int = 1) -> float:
+        """Largest error of one FP16 tensor-core MMA tile against the exact product."""
+        out = C.c_double()
+        self.check(self.lib.ss_selftest_tc(self.h, seed, C.byref(out)), "ss_selftest_tc")
+        return out.value
+
+    def measure_peak(self, kind: str = "fp64", seconds: float = 0.5) -> float:
+        """Measured FMA throughput of this GPU in TFLOP/s ("fp64" or "fp32")."""
+        k = {"fp64": L.SS_PEAK_FP64_FMA, "fp32": L.SS_PEAK_FP32_FMA}[kind]
+        out = C.c_double()
+        self.check(self.lib.ss_measure_peak(self.h, k, seconds, C.byref(out)), "ss_measure_peak")
+        return out.value
+
     def launch_count(self) -> int:
         """Kernels launched by the library since it was loaded."""
         return int(self.lib.ss_launch_count())
@@ -173,14 +192,15 @@ class Symbolic:
 
 def factor(sym: Symbolic, a_vals, b_vals, sigma, precision: str = "fp64",
            allow_singular: bool = False) -> "Factor":
-    """LDL^T of A - sigma_j B for every shift (one factor per shift)."""
+    """LDL^T of A - sigma_j B for every shift (one factor per shift).  precision "fp64",
+    "mixed", or "inertia" (FP64 fronts, only the inertia kept: no solves)."""
     ctx = sym.ctx
     _dev(a_vals, "a_vals")
     _dev(b_vals, "b_vals")
     if a_vals.numel() != sym.nnz or b_vals.numel() != sym.nnz:
         raise ValueError("value arrays must match the analysed pattern")
     sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
-    prec = {"fp64": L.SS_FP64, "mixed": L.SS_MIXED}[precision]
+    prec = {"fp64": L.SS_FP64, "mixed": L.SS_MIXED, "inertia": L.SS_FP64 | L.SS_INERTIA_ONLY}[precision]
     h = C.c_void_p()
     rc = ctx.lib.ss_factor(sym.h, _ptr(a_vals), _ptr(b_vals), _ptr(sig), sig.size, prec, C.byref(h))
     ctx.check(rc, "ss_factor", allow=(L.SS_ERR_SINGULAR,) if allow_singular else ())

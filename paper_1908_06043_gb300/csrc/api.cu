@@ -14,6 +14,7 @@
 #include "internal.h"
 #include "solve_kernels.cuh"
 #include "sparse_kernels.cuh"
+#include "tc_kernels.cuh"
 
 using namespace ssk;
 
@@ -139,6 +140,73 @@ extern "C" ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode) {
     return SS_OK;
 }
 
+template <typename T>
+static void set_smem_attrs(int device);
+
+extern "C" ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops) {
+    if (!ctx) return SS_ERR_ARG;
+    if ((mode != SS_SCHUR_TENSOR && mode != SS_SCHUR_SIMT) || !(min_flops >= 0.0))
+        return ctx->set_error(SS_ERR_ARG, "ss_set_schur_mode: bad argument");
+    ctx->schur_mode = mode;
+    ctx->tc_min_flops = min_flops;
+    return SS_OK;
+}
+
+// One 128 x 64 x 64 FP16 MMA tile on the tensor cores against the exact product: the
+// operands are small integers, so every product and sum is exact in FP32.
+extern "C" ss_status ss_selftest_tc(ss_ctx *ctx, uint64_t seed, double *max_abs_err) {
+    if (!ctx || !max_abs_err) return SS_ERR_ARG;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "ss_selftest_tc: host-only context");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    set_smem_attrs<double>(ctx->device);
+    const int M = sstc::kTileM, N = sstc::kTileN, K = sstc::kTileK;
+    std::vector<float> a((size_t)M * K), b((size_t)N * K);
+    uint64_t x = seed * 6364136223846793005ull + 1442695040888963407ull;
+    auto next = [&]() {                       // integers in [-128, 128]
+        x = x * 6364136223846793005ull + 1442695040888963407ull;
+        return (float)((int)((x >> 33) % 257) - 128);
+    };
+    for (float &v : a) v = next();
+    for (float &v : b) v = next();
+    std::vector<__half> ha(sstc::kSliceBytes / 2), hb(sstc::kHalfSliceBytes / 2);
+    for (int r = 0; r < M; ++r)
+        for (int k = 0; k < K; ++k) ha[sstc::core_offset(r, k) / 2] = __float2half(a[(size_t)r * K + k]);
+    for (int r = 0; r < N; ++r)
+        for (int k = 0; k < K; ++k) hb[sstc::core_offset(r, k) / 2] = __float2half(b[(size_t)r * K + k]);
+    unsigned char *dA = nullptr, *dB = nullptr;
+    float *dD = nullptr;
+    int *dst = nullptr;
+    cudaStream_t st = ctx->stream;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dA, sstc::kSliceBytes, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dB, sstc::kHalfSliceBytes, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dD, sizeof(float) * M * N, st));
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dst, sizeof(int), st));
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(dA, ha.data(), sstc::kSliceBytes, cudaMemcpyHostToDevice, st));
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(dB, hb.data(), sstc::kHalfSliceBytes, cudaMemcpyHostToDevice, st));
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(dD, 0, sizeof(float) * M * N, st));
+    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_selftest, 1, 128, sstc::kSliceBytes + sstc::kHalfSliceBytes, st,
+              (const unsigned char *)dA, (const unsigned char *)dB, dD, dst);
+    std::vector<float> D((size_t)M * N);
+    int status = -1;
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(D.data(), dD, sizeof(float) * M * N, cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(&status, dst, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    cudaFreeAsync(dA, st);
+    cudaFreeAsync(dB, st);
+    cudaFreeAsync(dD, st);
+    cudaFreeAsync(dst, st);
+    if (status != 0) return ctx->set_error(SS_ERR_TIMEOUT, "ss_selftest_tc: a bounded wait ran out");
+    double err = 0.0;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < N; ++j) {
+            double ref = 0.0;
+            for (int k = 0; k < K; ++k) ref += (double)a[(size_t)i * K + k] * b[(size_t)j * K + k];
+            err = std::max(err, std::fabs(ref - (double)D[(size_t)i * N + j]));
+        }
+    *max_abs_err = err;
+    return SS_OK;
+}
+
 extern "C" ss_status ss_sync(ss_ctx *ctx) {
     if (!ctx) return SS_ERR_ARG;
     if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "host-only context");
@@ -172,6 +240,7 @@ int ss_symbolic_upload(ss_symbolic *s) {
     UP(s->relmap, s->d_relmap);
     UP(s->ext_tasks, s->d_ext_tasks);
     UP(s->panels, s->d_panels);
+    UP(s->store_tasks, s->d_store_tasks);
     UP(s->tasks, s->d_tasks);
     UP(s->solve_panels, s->d_solve_panels);
     UP(s->solve_tile_pre, s->d_solve_tile_pre);
@@ -192,13 +261,13 @@ int ss_symbolic_upload(ss_symbolic *s) {
 
 void ss_symbolic_free_device(ss_symbolic *s) {
     void *ptrs[] = {s->d_rowptr, s->d_colind, s->d_iperm, s->d_perm, s->d_idx, s->d_asm_e,
-                    s->d_asm_dest, s->d_relmap, s->d_ext_tasks, s->d_panels, s->d_tasks,
+                    s->d_asm_dest, s->d_relmap, s->d_ext_tasks, s->d_panels, s->d_store_tasks, s->d_tasks,
                     s->d_solve_panels, s->d_solve_tile_pre, s->d_col_panel, s->d_sweep_lev};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     s->d_rowptr = nullptr; s->d_colind = nullptr; s->d_iperm = nullptr; s->d_perm = nullptr;
     s->d_idx = nullptr; s->d_asm_e = nullptr; s->d_asm_dest = nullptr; s->d_relmap = nullptr;
-    s->d_ext_tasks = nullptr; s->d_panels = nullptr; s->d_tasks = nullptr;
+    s->d_ext_tasks = nullptr; s->d_panels = nullptr; s->d_store_tasks = nullptr; s->d_tasks = nullptr;
     s->d_solve_panels = nullptr; s->d_solve_tile_pre = nullptr; s->d_col_panel = nullptr;
     s->d_sweep_lev = nullptr;
 }
@@ -254,81 +323,120 @@ static void set_smem_attrs(int device) {
     cudaFuncSetAttribute(k_fwd_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_kernel_smem<T>());
     cudaFuncSetAttribute(k_bwd_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_kernel_smem<T>());
     cudaFuncSetAttribute(k_solve_sweeps<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<T>());
+    if (std::is_same<T, double>::value) {
+        cudaFuncSetAttribute(sstc::k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sstc::kSchurTcSmem);
+        cudaFuncSetAttribute(sstc::k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sstc::kSliceBytes + sstc::kHalfSliceBytes));
+    }
 }
 
+// Factorisation of the shifts in `which`, in waves of as many shifts as the free device
+// memory holds: each shift of a wave has its own level workspace, contribution-block pool
+// and panel scratch for the duration of the wave; the L storage (f->arena) persists.
 template <typename T>
 static int factor_run(ss_numeric *f, const std::vector<int> &which) {
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
     cudaStream_t st = ctx->stream;
     set_smem_attrs<T>(ctx->device);
-    const int ns = (int)which.size();
-    if (ns == 0) return SS_OK;
-    const int64_t npan = (int64_t)s->panels.size();
-    std::vector<ShiftPtrs<T>> hp(ns);
-    T *mt = nullptr, *wb = nullptr;
-    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mt, sizeof(T) * std::max<int64_t>(1, (int64_t)s->mt_max * NB * NB) * ns, st));
-    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wb, sizeof(T) * std::max<int64_t>(1, s->wbuf_max) * ns, st));
-    for (int q = 0; q < ns; ++q) {
-        const int j = which[q];
-        ShiftPtrs<T> &p = hp[q];
-        p.arena = (T *)f->arena[j];
-        p.linv = f->linv[j];
-        p.dblk = f->dblk[j];
-        p.piv = f->piv[j];
-        p.mt = mt + (int64_t)q * s->mt_max * NB * NB;
-        p.wbuf = wb + (int64_t)q * std::max<int64_t>(1, s->wbuf_max);
-        p.counts = f->d_counts + SS_NCOUNT * j;
-        p.sigma = f->sigma[j];
-        p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
-        p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
-    }
-    ShiftPtrs<T> *dp = nullptr;
-    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dp, sizeof(ShiftPtrs<T>) * ns, st));
-    SS_CUDA_TRY(ctx, cudaMemcpyAsync(dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
-    static const unsigned long long init[SS_NCOUNT] = {0, 0, 0, 0, 0x7ff0000000000000ull /* +inf */, 0, 0};
-    for (int q = 0; q < ns; ++q)
+    const int ns_all = (int)which.size();
+    if (ns_all == 0) return SS_OK;
+    const int64_t ws_n = std::max<int64_t>(1, s->ws_total), cb_n = std::max<int64_t>(1, s->cb_total);
+    const int64_t mt_n = std::max<int64_t>(1, (int64_t)s->mt_max * NB * NB), wb_n = std::max<int64_t>(1, s->wbuf_max);
+    // FP64 steps with enough Schur work run the tensor-core update (tc_kernels.cuh)
+    const bool tc = std::is_same<T, double>::value && ctx->schur_mode == SS_SCHUR_TENSOR && s->sl_max > 0;
+    const int64_t sl_n = tc ? s->sl_max : 16, ex_n = tc ? std::max<int64_t>(1, s->ex_max) : 1;
+    const double per_shift = (double)sizeof(T) * (double)(ws_n + cb_n + mt_n + wb_n) + (double)sl_n + 4.0 * ex_n;
+    size_t mem_free = 0, mem_tot = 0;
+    SS_CUDA_TRY(ctx, cudaMemGetInfo(&mem_free, &mem_tot));
+    int wave = (int)std::max(1.0, std::min((double)std::min(ns_all, 65535), std::floor(0.8 * (double)mem_free / per_shift)));
+    static const unsigned long long init[SS_NCOUNT] = {0, 0, 0, 0, 0x7ff0000000000000ull /* +inf */, 0, 0, 0};
+    for (int q = 0; q < ns_all; ++q)
         SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->d_counts + SS_NCOUNT * which[q], init, sizeof(init),
                                          cudaMemcpyHostToDevice, st));
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));    // init is a host array
-    for (int32_t l = 0; l < s->nlev; ++l) {
-        const int64_t b0 = s->lev_arena_begin[l], b1 = s->lev_arena_end[l];
-        for (int q = 0; q < ns; ++q)
-            SS_CUDA_TRY(ctx, cudaMemsetAsync((T *)f->arena[which[q]] + b0, 0, sizeof(T) * (b1 - b0), st));
-        const int64_t a0 = s->asm_lev_off[l], acount = s->asm_lev_off[l + 1] - a0;
-        if (acount > 0) {
-            unsigned gx = (unsigned)std::min<int64_t>((acount + 255) / 256, 8192);
-            ss_launch(ctx, SS_K_ASSEMBLE, k_assemble<T>, dim3(gx, ns), 256, 0, st, acount, s->d_asm_e + a0, s->d_asm_dest + a0,
-                                                         f->a_vals, f->b_vals, dp);
+    for (int w0 = 0; w0 < ns_all; w0 += wave) {
+        const int ns = std::min(wave, ns_all - w0);
+        T *mt = nullptr, *wb = nullptr, *ws = nullptr, *cb = nullptr;
+        unsigned char *sl = nullptr;
+        int32_t *ex = nullptr;
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&sl, (size_t)sl_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&ex, sizeof(int32_t) * ex_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mt, sizeof(T) * mt_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wb, sizeof(T) * wb_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&ws, sizeof(T) * ws_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&cb, sizeof(T) * cb_n * ns, st));
+        std::vector<ShiftPtrs<T>> hp(ns);
+        for (int q = 0; q < ns; ++q) {
+            const int j = which[w0 + q];
+            ShiftPtrs<T> &p = hp[q];
+            p.ws = ws + (int64_t)q * ws_n;
+            p.cb = cb + (int64_t)q * cb_n;
+            p.lst = (T *)f->arena[j];
+            p.linv = f->linv[j];
+            p.dblk = f->dblk[j];
+            p.piv = f->piv[j];
+            p.mt = mt + (int64_t)q * mt_n;
+            p.wbuf = wb + (int64_t)q * wb_n;
+            p.sl = sl + (int64_t)q * sl_n;
+            p.ex = ex + (int64_t)q * ex_n;
+            p.counts = f->d_counts + SS_NCOUNT * j;
+            p.sigma = f->sigma[j];
+            p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
+            p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
         }
-        for (int32_t q = s->lev_ext_pass_off[l]; q < s->lev_ext_pass_off[l + 1]; ++q) {
-            const ExtendPass &ps = s->ext_pass[q];
-            ss_launch(ctx, SS_K_EXTEND_ADD, k_extend_add<T>, dim3(ps.cols, ns), 128, 0, st, s->d_ext_tasks + ps.task_off, ps.count,
-                                                               s->d_relmap, dp);
-        }
-        for (int32_t q = s->lev_step_off[l]; q < s->lev_step_off[l + 1]; ++q) {
-            const StepDesc &sd = s->steps[q];
-            const StepTask *tk = s->d_tasks + sd.task_off;
-            ss_launch(ctx, SS_K_DIAG_BK, k_diag_bk<T>, dim3(sd.count, ns), 256, kDiagSmem, st, tk, dp, 0);
-            if (sd.tiles4 > 0)
-            {
-                const int cls = std::is_same<T, float>::value ? SS_K_PANEL_F32 : SS_K_PANEL;
-                ss_launch(ctx, cls, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count, dp);
-                ctx->add_flops(cls, sd.flops4 * ns);
+        ShiftPtrs<T> *dp = nullptr;
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dp, sizeof(ShiftPtrs<T>) * ns, st));
+        SS_CUDA_TRY(ctx, cudaMemcpyAsync(dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
+        for (int32_t l = 0; l < s->nlev; ++l) {
+            for (int q = 0; q < ns; ++q)
+                SS_CUDA_TRY(ctx, cudaMemsetAsync(hp[q].ws, 0, sizeof(T) * s->lev_ws[l], st));
+            const int64_t a0 = s->asm_lev_off[l], acount = s->asm_lev_off[l + 1] - a0;
+            if (acount > 0) {
+                unsigned gx = (unsigned)std::min<int64_t>((acount + 255) / 256, 8192);
+                ss_launch(ctx, SS_K_ASSEMBLE, k_assemble<T>, dim3(gx, ns), 256, 0, st, acount, s->d_asm_e + a0,
+                          s->d_asm_dest + a0, f->a_vals, f->b_vals, dp);
             }
-            if (sd.tiles3 > 0)
-            {
-                const int cls = std::is_same<T, float>::value ? SS_K_SCHUR_F32 : SS_K_SCHUR;
-                ss_launch(ctx, cls, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count, dp);
-                ctx->add_flops(cls, sd.flops3 * ns);
+            for (int32_t q = s->lev_ext_pass_off[l]; q < s->lev_ext_pass_off[l + 1]; ++q) {
+                const ExtendPass &ps = s->ext_pass[q];
+                ss_launch(ctx, SS_K_EXTEND_ADD, k_extend_add<T>, dim3(ps.cols, ns), 128, 0, st,
+                          s->d_ext_tasks + ps.task_off, ps.count, s->d_relmap, dp);
             }
+            for (int32_t q = s->lev_step_off[l]; q < s->lev_step_off[l + 1]; ++q) {
+                const StepDesc &sd = s->steps[q];
+                const StepTask *tk = s->d_tasks + sd.task_off;
+                ss_launch(ctx, SS_K_DIAG_BK, k_diag_bk<T>, dim3(sd.count, ns), 256, kDiagSmem, st, tk, dp, 0);
+                if (sd.tiles4 > 0) {
+                    const int cls = std::is_same<T, float>::value ? SS_K_PANEL_F32 : SS_K_PANEL;
+                    ss_launch(ctx, cls, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count, dp);
+                    ctx->add_flops(cls, sd.flops4 * ns);
+                }
+                if (sd.tiles3 > 0 && tc && sd.tc_tiles > 0 && sd.flops3 >= ctx->tc_min_flops) {
+                    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_slice, dim3(sd.sl_tiles, ns), 128, 0, st, tk, sd.count,
+                              (const ShiftPtrs<double> *)dp);
+                    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_schur_tc, dim3(sd.tc_tiles, ns), 128, sstc::kSchurTcSmem,
+                              st, tk, sd.count, (const ShiftPtrs<double> *)dp);
+                    ctx->add_flops(SS_K_SCHUR_TC, sd.flops3 * ns);
+                } else if (sd.tiles3 > 0) {
+                    const int cls = std::is_same<T, float>::value ? SS_K_SCHUR_F32 : SS_K_SCHUR;
+                    ss_launch(ctx, cls, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count, dp);
+                    ctx->add_flops(cls, sd.flops3 * ns);
+                }
+            }
+            const int32_t t0 = s->lev_store_off[l], nt = s->lev_store_off[l + 1] - t0;
+            if (nt > 0 && s->lev_store_cols[l] > 0)
+                ss_launch(ctx, SS_K_MISC, k_level_store<T>, dim3(s->lev_store_cols[l], ns), 128, 0, st,
+                          (const StoreTask *)(s->d_store_tasks + t0), nt, dp);
         }
+        SS_CUDA_TRY(ctx, cudaGetLastError());
+        SS_CUDA_TRY(ctx, cudaFreeAsync(dp, st));
+        SS_CUDA_TRY(ctx, cudaFreeAsync(mt, st));
+        SS_CUDA_TRY(ctx, cudaFreeAsync(wb, st));
+        SS_CUDA_TRY(ctx, cudaFreeAsync(ws, st));
+        SS_CUDA_TRY(ctx, cudaFreeAsync(cb, st));
+        SS_CUDA_TRY(ctx, cudaFreeAsync(sl, st));
+        SS_CUDA_TRY(ctx, cudaFreeAsync(ex, st));
     }
-    SS_CUDA_TRY(ctx, cudaGetLastError());
-    SS_CUDA_TRY(ctx, cudaFreeAsync(dp, st));
-    SS_CUDA_TRY(ctx, cudaFreeAsync(mt, st));
-    SS_CUDA_TRY(ctx, cudaFreeAsync(wb, st));
-    (void)npan;
     return SS_OK;
 }
 
@@ -361,6 +469,8 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
     ss_numeric *f = new (std::nothrow) ss_numeric();
     if (!f) return ctx->set_error(SS_ERR_OOM, "ss_factor: host allocation failed");
     f->sym = sym;
+    f->inertia_only = (precision & SS_INERTIA_ONLY) != 0;
+    precision = f->inertia_only ? SS_FP64 : precision;      // exact counts come from FP64 fronts
     f->precision = precision;
     f->n_shift = n_shift;
     f->sigma.assign(sigma, sigma + n_shift);
@@ -380,7 +490,7 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
     f->piv.assign(n_shift, nullptr);
     cudaError_t e = cudaMalloc((void **)&f->d_counts, sizeof(unsigned long long) * SS_NCOUNT * n_shift);
     for (int j = 0; j < n_shift && e == cudaSuccess; ++j) {
-        e = cudaMalloc(&f->arena[j], esz * std::max<int64_t>(1, sym->arena));
+        if (!f->inertia_only) e = cudaMalloc(&f->arena[j], esz * std::max<int64_t>(1, sym->l_total));
         if (e == cudaSuccess) e = cudaMalloc((void **)&f->linv[j], sizeof(double) * NB * NB * npan);
         if (e == cudaSuccess) e = cudaMalloc((void **)&f->dblk[j], sizeof(double) * 2 * NB * npan);
         if (e == cudaSuccess) e = cudaMalloc((void **)&f->piv[j], sizeof(int32_t) * NB * npan);
@@ -411,7 +521,7 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
             if (rc != SS_OK) break;
             f->arena_lo[j] = (float *)f->arena[j];
             f->arena[j] = nullptr;
-            cudaError_t e2 = cudaMalloc(&f->arena[j], sizeof(double) * std::max<int64_t>(1, sym->arena));
+            cudaError_t e2 = cudaMalloc(&f->arena[j], sizeof(double) * std::max<int64_t>(1, sym->l_total));
             if (e2 != cudaSuccess) {
                 cudaGetLastError();
                 rc = ctx->set_error(SS_ERR_OOM, "ss_factor: device allocation for an FP64 refactor failed");
@@ -424,7 +534,7 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
         // solve from it contracts by rho <= kRoundedRhoMax, else solves stay FP64
         for (int j : redo) {
             if (rc != SS_OK) break;
-            const int64_t na = std::max<int64_t>(1, sym->arena);
+            const int64_t na = std::max<int64_t>(1, sym->l_total);
             const unsigned g = (unsigned)std::min<int64_t>((na + 255) / 256, (int64_t)ctx->sm_count * 16);
             ss_launch(ctx, SS_K_MISC, k_round_f32, g, 256, 0, ctx->stream, na, (const double *)f->arena[j],
                       f->arena_lo[j]);
@@ -461,6 +571,10 @@ int ss_factor_fetch_counts(ss_numeric *f) {
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     f->counts_valid = true;
     for (int j = 0; j < f->n_shift; ++j)
+        if (f->h_counts[SS_NCOUNT * j + 7])
+            return ctx->set_error(SS_ERR_TIMEOUT, "ss_factor: a bounded device wait of the tensor-core Schur "
+                                                  "update ran out for shift " + std::to_string(j));
+    for (int j = 0; j < f->n_shift; ++j)
         if (f->h_counts[SS_NCOUNT * j + 3]) {
             return ctx->set_error(SS_ERR_SINGULAR, "ss_factor: a pivot fell below the singularity "
                                                    "threshold for shift " + std::to_string(j));
@@ -473,8 +587,9 @@ extern "C" ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const dou
     if (!sym) return SS_ERR_ARG;
     ss_ctx *ctx = sym->ctx;
     if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "ss_factor: host-only context");
+    const int32_t base_prec = precision & ~SS_INERTIA_ONLY;
     if (!out || !a_vals || !b_vals || !sigma || n_shift <= 0 || n_shift > 65535 ||
-        (precision != SS_FP64 && precision != SS_MIXED))
+        (base_prec != SS_FP64 && base_prec != SS_MIXED))
         return ctx->set_error(SS_ERR_ARG, "ss_factor: bad argument");
     for (int j = 0; j < n_shift; ++j)
         if (!std::isfinite(sigma[j])) return ctx->set_error(SS_ERR_ARG, "ss_factor: non-finite shift");
@@ -904,8 +1019,8 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
 extern "C" ss_status ss_solve(ss_numeric *f, int32_t j, const double *R, int32_t k, double *X, int32_t refine) {
     if (!f) return SS_ERR_ARG;
     ss_ctx *ctx = f->sym->ctx;
-    if (j < 0 || j >= f->n_shift || !R || !X || k <= 0 || refine < 0)
-        return ctx->set_error(SS_ERR_ARG, "ss_solve: bad argument");
+    if (j < 0 || j >= f->n_shift || !R || !X || k <= 0 || refine < 0 || f->inertia_only)
+        return ctx->set_error(SS_ERR_ARG, "ss_solve: bad argument (or an inertia-only factor)");
     SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     return solve_apply(f, j, R, k, X, refine, nullptr);
 }
@@ -978,8 +1093,8 @@ extern "C" ss_status ss_solve_noalloc(ss_numeric *f, int32_t j, const double *R,
     if (!f) return SS_ERR_ARG;
     ss_symbolic *s = f->sym;
     ss_ctx *ctx = s->ctx;
-    if (ctx->device < 0 || j < 0 || j >= f->n_shift || !R || !X || k <= 0)
-        return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: bad argument or host-only context");
+    if (ctx->device < 0 || j < 0 || j >= f->n_shift || !R || !X || k <= 0 || f->inertia_only)
+        return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: bad argument, inertia-only factor or host-only context");
     if (f->shift_prec[j] != SS_FP64)
         return ctx->set_error(SS_ERR_ARG, "ss_solve_noalloc: shift was factored in FP32; use ss_solve");
     int32_t maxc = 0;

@@ -1,6 +1,6 @@
 // Numeric multifrontal LDL^T kernels (Alg. 2 step 2: (L, D) <- LDL^T of A - sigma B).
 //
-// A front is a dense column-major m x m block in the level-ordered arena; only its lower
+// A front is a dense column-major m x m block in the level workspace; only its lower
 // triangle is meaningful.  Its first ncol columns are eliminated in panels of width
 // w <= 64; each panel step is
 //   K2 diag:  FP64 Bunch-Kaufman on the w x w diagonal block, pivots restricted to the
@@ -9,8 +9,10 @@
 //   K4 panel: L21 = F21 Mt (in place) and W = L21 D (scratch), 64-row tiles.
 //   K3 Schur: F22 -= L21 W^T on the lower-triangular 64 x 64 tiles of the trailing front.
 // Before a level's steps its fronts are zeroed, the stored entries of A - sigma B are
-// scattered in (assembly) and the children's contribution blocks are added (extend-add,
-// one pass per child slot so that no two blocks of a pass write the same parent entry).
+// scattered in (assembly) and the children's contribution blocks are added from the pool
+// (extend-add, one pass per child slot so that no two blocks of a pass write the same
+// parent entry).  After them the fronts' panel columns go to L storage and their trailing
+// blocks to the pool (store), so the workspace holds one level at a time.
 // Every kernel is batched over shifts with blockIdx.y.
 #pragma once
 
@@ -29,13 +31,17 @@ template <typename T> constexpr size_t schur_smem() { return 2 * NB * (TR + 1) *
 
 template <typename T>
 struct ShiftPtrs {
-    T *arena;
+    T *ws;                          // level workspace (fronts of the level being factored)
+    T *cb;                          // contribution-block pool
+    T *lst;                         // L storage (null: inertia only, nothing kept)
     double *linv;                   // npanels * NB * NB, row-major L^-1 of each panel
     double *dblk;                   // npanels * 2 * NB: D diagonal then sub-diagonal
     int32_t *piv;                   // npanels * NB
     T *mt;                          // mt_max * NB * NB
     T *wbuf;                        // wbuf_max
-    unsigned long long *counts;     // [neg, zero, pos, tiny, min_pivot_bits, n2x2, max_abs_l_bits]
+    unsigned char *sl;              // operand slices of the tensor-core Schur update
+    int32_t *ex;                    // their row exponents
+    unsigned long long *counts;     // [neg, zero, pos, tiny, min_pivot_bits, n2x2, max_abs_l_bits, timeouts]
     double sigma;
     double tiny_thr;                // pivots below this are flagged
     double norm;                    // ||A - sigma B||_1 bound (for min-pivot ratio)
@@ -50,12 +56,12 @@ __global__ void k_assemble(int64_t count, const int32_t *__restrict__ asm_e,
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
          q += (int64_t)gridDim.x * blockDim.x) {
         int32_t e = asm_e[q];
-        s.arena[asm_dest[q]] = (T)(a[e] - s.sigma * b[e]);
+        s.ws[asm_dest[q]] = (T)(a[e] - s.sigma * b[e]);
     }
 }
 
 // ---------------------------------------------------------------- extend-add
-// One block per contribution column: parent[rel[i], rel[j]] += child[ncol+i, ncol+j], i >= j.
+// One block per contribution column: parent[rel[i], rel[j]] += cb[i, j], i >= j.
 template <typename T>
 __global__ void k_extend_add(const ExtendTask *__restrict__ tasks, int32_t ntask,
                              const int32_t *__restrict__ relmap, const ShiftPtrs<T> *sp) {
@@ -70,9 +76,36 @@ __global__ void k_extend_add(const ExtendTask *__restrict__ tasks, int32_t ntask
     const int32_t j = col - t.col_pre;
     const int32_t nr = t.child_m - t.child_ncol;
     const int32_t *rel = relmap + t.rel_off;
-    const T *cc = s.arena + t.child_off + (int64_t)(t.child_ncol + j) * t.child_m + t.child_ncol;
-    T *pc = s.arena + t.parent_off + (int64_t)rel[j] * t.parent_m;
+    const T *cc = s.cb + t.child_off + (int64_t)(t.child_ncol + j) * t.child_m + t.child_ncol;
+    T *pc = s.ws + t.parent_off + (int64_t)rel[j] * t.parent_m;
     for (int32_t i = j + threadIdx.x; i < nr; i += blockDim.x) pc[rel[i]] += cc[i];
+}
+
+// ---------------------------------------------------------------- store
+// One block per front column of a level: column c < ncol to L storage (all m rows),
+// column ncol + j to the contribution-block pool (rows j .. nr-1, leading dimension nr).
+template <typename T>
+__global__ void k_level_store(const StoreTask *__restrict__ tasks, int32_t ntask, const ShiftPtrs<T> *sp) {
+    const ShiftPtrs<T> s = sp[blockIdx.y];
+    const int32_t col = blockIdx.x;
+    int lo = 0, hi = ntask - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (tasks[mid].col_pre <= col) lo = mid; else hi = mid - 1;
+    }
+    const StoreTask t = tasks[lo];
+    const int32_t c = col - t.col_pre;
+    const T *src = s.ws + t.ws_off + (int64_t)c * t.m;
+    if (c < t.ncol) {
+        if (!s.lst) return;
+        T *dst = s.lst + t.l_off + (int64_t)c * t.m;
+        for (int32_t i = threadIdx.x; i < t.m; i += blockDim.x) dst[i] = src[i];
+    } else {
+        const int32_t j = c - t.ncol, nr = t.m - t.ncol;
+        T *dst = s.cb + t.cb_off + (int64_t)j * nr;
+        src += t.ncol;
+        for (int32_t i = j + threadIdx.x; i < nr; i += blockDim.x) dst[i] = src[i];
+    }
 }
 
 // ---------------------------------------------------------------- K2: diagonal block
@@ -95,7 +128,7 @@ __global__ void __launch_bounds__(256) k_diag_bk(const StepTask *__restrict__ ta
     __shared__ unsigned long long c_neg, c_zero, c_pos, c_tiny, c_2x2;
     __shared__ double s_minpiv;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const T *F = s.arena + tk.front_off;
+    const T *F = s.ws + tk.front_off;
 
     for (int q = tid; q < w * w; q += nt) {
         int j = q / w, i = q % w;            // column j, row i (coalesced on i)
@@ -297,7 +330,7 @@ __global__ void __launch_bounds__(256) k_panel(const StepTask *__restrict__ task
     const int w = tk.w, m = tk.m;
     const int r0 = (tile - tk.tiles4_pre) * TR;           // first row within the r rows
     const int nr = min(TR, tk.r - r0);
-    T *F = s.arena + tk.front_off;
+    T *F = s.ws + tk.front_off;
     const int64_t rowbase = tk.k0 + w + r0;
     const T *mt = s.mt + (int64_t)tk.mt_slot * NB * NB;
     const int tid = threadIdx.x;
@@ -376,7 +409,7 @@ __global__ void __launch_bounds__(256) k_schur(const StepTask *__restrict__ task
     const int w = tk.w, m = tk.m, r = tk.r;
     const int i0 = bi * TR, j0 = bj * TR;
     const int ni = min(TR, r - i0), nj = min(TR, r - j0);
-    T *F = s.arena + tk.front_off;
+    T *F = s.ws + tk.front_off;
     const T *W = s.wbuf + tk.wbuf_off;
     const int64_t base = tk.k0 + w;               // first trailing row/col in the front
     const int tid = threadIdx.x;

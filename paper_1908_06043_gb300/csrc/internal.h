@@ -19,6 +19,8 @@ struct ss_ctx {
     int sm_count = 0;
     std::string err;
     int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
+    int schur_mode = SS_SCHUR_SIMT;           // FP64 Schur update: tensor cores or CUDA cores
+    double tc_min_flops = 2.0e7;              // a factor step's Schur flops below which it stays on CUDA cores
     GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
     int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)
     // per-class launch timing (ss_profile): event pairs recorded around launches
@@ -62,11 +64,17 @@ inline void ss_launch(ss_ctx *ctx, int cls, void (*kern)(KArgs...), dim3 grid, d
 }
 #endif
 
+// Operand slices of the tensor-core Schur update (tc_kernels.cuh): kTcSlices FP16 blocks
+// of 128 rows x 64 columns per 128-row tile of L21 and of W.
+constexpr int kTcSlices = 7;
+constexpr int64_t kTcSliceBytes = 128 * 64 * 2;
+
 // One panel of the blocked front factorisation: columns [k0, k0+w) of front `sn`.
 // The panel's L rows below its diagonal block are front rows [k0+w, m), whose global
 // (permuted) indices are idx[idx_off + k0 + w ...].
 struct PanelDesc {
-    int64_t front_off;   // arena offset (entries) of the front, column-major m x m
+    int64_t front_off;   // L storage offset (entries) of the supernode's m x ncol panel columns
+                         // (column-major, leading dimension m)
     int64_t idx_off;     // offset of the front's global index list in idx
     int32_t m;           // front dimension
     int32_t k0;          // first front column of the panel
@@ -79,13 +87,17 @@ struct PanelDesc {
 // One front taking part in factor step (level, t): panel `panel` is eliminated and
 // the trailing front [k0+w, m) x [k0+w, m) is updated.
 struct StepTask {
-    int64_t front_off;
+    int64_t front_off;   // workspace offset of the m x m front (column-major)
     int64_t wbuf_off;    // offset of this task's W = L21 D block (r x w, col-major) in W scratch
     int32_t m, k0, w, r; // r = m - k0 - w
     int32_t panel;
     int32_t mt_slot;     // slot of the w x w transform in the Mt scratch
     int32_t tiles4_pre;  // exclusive prefix of panel-transform row tiles
     int32_t tiles3_pre;  // exclusive prefix of Schur-update tiles
+    int32_t sl_pre;      // exclusive prefix of 128-row slice tiles (2 per 128 rows: L21, W)
+    int32_t tc_pre;      // exclusive prefix of 128 x 64 tensor-core Schur tiles
+    int64_t sl_off;      // byte offset of this task's operand slices in the slice scratch
+    int64_t ex_off;      // offset of its row exponents (r for L21, then r for W)
 };
 
 struct StepDesc {
@@ -94,14 +106,25 @@ struct StepDesc {
     int32_t tiles4, tiles3;
     int32_t level;
     double flops4, flops3;   // algorithmic flops of the panel transform / Schur update
+    int32_t sl_tiles, tc_tiles;   // slice tiles and tensor-core Schur tiles of the step
+    int64_t sl_bytes, ex_count;   // slice scratch bytes and row exponents of the step
 };
 
-// Child -> parent extend-add unit: child front contribution block (rows [ncol, m))
-// added into the parent front through relmap.
+// Child -> parent extend-add unit: the child's contribution block (pool, leading
+// dimension child_m = its nr, child_ncol = 0) added into the parent front (workspace)
+// through relmap.
 struct ExtendTask {
     int64_t child_off, parent_off;
     int64_t rel_off;     // into relmap (length nr)
     int32_t child_m, child_ncol, parent_m, col_pre;  // col_pre: exclusive prefix of columns
+};
+
+// After a level is factored: copy front columns of one supernode out of the workspace.
+// Column c < ncol goes to L storage (the whole column, m entries); column ncol + j (the
+// contribution block) goes to the pool, rows j .. nr-1 (nr = m - ncol, leading dim nr).
+struct StoreTask {
+    int64_t ws_off, l_off, cb_off;   // cb_off < 0: no contribution block (a root)
+    int32_t m, ncol, col_pre, pad;   // col_pre: exclusive prefix of columns in the level
 };
 
 struct ExtendPass {     // one non-conflicting pass (the q-th child of each parent)
@@ -129,15 +152,21 @@ struct ss_symbolic {
     std::vector<int32_t> sn_parent, sn_nrow, sn_level;
     std::vector<int64_t> sn_idx_off;         // nsn + 1
     std::vector<int32_t> idx;                // per supernode: [its columns, its rows]
-    std::vector<int64_t> front_off;          // arena offsets (level-ordered)
-    int64_t arena = 0;
+    // memory plan of the numeric factorisation (entries, per shift)
+    std::vector<int64_t> front_off;          // front offset in its level's workspace
+    std::vector<int64_t> l_off;              // L storage offset (m x ncol, leading dim m)
+    std::vector<int64_t> cb_off;             // contribution-block pool offset (-1: none)
+    std::vector<int64_t> lev_ws;             // workspace entries used by each level
+    int64_t ws_total = 0, l_total = 0, cb_total = 0;
+    std::vector<StoreTask> store_tasks;
+    std::vector<int32_t> lev_store_off;      // nlev + 1, into store_tasks
+    std::vector<int32_t> lev_store_cols;     // columns stored per level
     int32_t nlev = 0;
-    std::vector<int64_t> lev_arena_begin, lev_arena_end;   // arena range per level
 
     // assembly of the original entries, grouped by level
     std::vector<int64_t> asm_lev_off;        // nlev + 1
     std::vector<int32_t> asm_e;              // CSR entry index
-    std::vector<int64_t> asm_dest;           // arena offset
+    std::vector<int64_t> asm_dest;           // workspace offset
 
     std::vector<int32_t> relmap;             // child rows -> parent front positions
     std::vector<ExtendTask> ext_tasks;
@@ -149,6 +178,7 @@ struct ss_symbolic {
     std::vector<StepDesc> steps;
     std::vector<int32_t> lev_step_off;       // nlev + 1, into steps
     int64_t wbuf_max = 0;                    // max W scratch entries over steps
+    int64_t sl_max = 0, ex_max = 0;          // max slice bytes / row exponents over steps
     int32_t mt_max = 0;                      // max fronts in one step
 
     std::vector<int32_t> solve_panels;       // panel ids grouped by solve level
@@ -168,6 +198,7 @@ struct ss_symbolic {
     int32_t *d_relmap = nullptr;
     ExtendTask *d_ext_tasks = nullptr;
     PanelDesc *d_panels = nullptr;
+    StoreTask *d_store_tasks = nullptr;
     StepTask *d_tasks = nullptr;
     int32_t *d_solve_panels = nullptr;
     int32_t *d_solve_tile_pre = nullptr;
@@ -184,9 +215,10 @@ struct ss_numeric {
     std::vector<double> sigma;
     const double *a_vals = nullptr, *b_vals = nullptr;   // caller-owned device arrays
     double norm_a1 = 0, norm_b1 = 0;
+    bool inertia_only = false;            // no L storage kept: inertia counts only
     // per shift
-    std::vector<void *> arena;            // front arena (double or float)
-    std::vector<float *> arena_lo;        // FP32 rounding of an FP64 arena that solves read, or null
+    std::vector<void *> arena;            // L storage (double or float), l_total entries
+    std::vector<float *> arena_lo;        // FP32 rounding of an FP64 L storage that solves read, or null
     std::vector<double *> linv;           // npanels * nb * nb, L11^-1 of each panel
     std::vector<double *> dblk;           // npanels * nb * 2: D diagonal, D sub-diagonal
     std::vector<int32_t *> piv;           // npanels * nb: local pivot order
@@ -208,7 +240,8 @@ void ss_symbolic_free_device(ss_symbolic *s);
 int ss_factor_fetch_counts(ss_numeric *f);
 int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
                      int32_t n_shift, int32_t precision, ss_numeric **out);
-constexpr int SS_NCOUNT = 7;   // per-shift device counters: neg, zero, pos, tiny, min pivot, 2x2, max |L|
+constexpr int SS_NCOUNT = 8;   // per-shift device counters: neg, zero, pos, tiny, min pivot, 2x2, max |L|,
+                               // device waits that ran out
 int ss_norm1(ss_symbolic *s, const double *vals, double *out);
 int solve_contraction(ss_numeric *f, int j, double *rho);
 // in-place solve (A - sigma_j B) x = b of a permuted-order N x k block

@@ -617,8 +617,8 @@ extern "C" ss_status ss_slice_solve(ss_numeric *f, int32_t j, double lo, double 
     if (!f) return SS_ERR_ARG;
     ss_ctx *ctx = f->sym->ctx;
     if (j < 0 || j >= f->n_shift || !V0 || !X || !lambda || !resid || k <= 0 || k > f->sym->n || k > 4096 ||
-        !(lo < hi))
-        return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: bad argument");
+        !(lo < hi) || f->inertia_only)
+        return ctx->set_error(SS_ERR_ARG, "ss_slice_solve: bad argument (or an inertia-only factor)");
     ss_solve_opts o{};
     if (opts) o = *opts;
     if (o.driver != SS_SUBSPACE && o.driver != SS_BLOCK_LANCZOS)

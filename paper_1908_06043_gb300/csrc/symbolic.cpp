@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <map>
 #include <numeric>
 
 #include "internal.h"
@@ -292,23 +293,94 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
     auto ncol = [&](int32_t b) { return first[b + 1] - first[b]; };
     auto msz = [&](int32_t b) { return (int64_t)ncol(b) + s->sn_nrow[b]; };
 
-    // ---- 3. level-ordered front arena
+    // ---- 3. memory plan of the numeric factorisation (per shift)
+    // L storage: supernode b keeps the first ncol columns of its m x m front (column-major,
+    // leading dimension m) -- the factor the solves read.  Level workspace: while level l
+    // is factored, its fronts are packed from offset 0 of one workspace reused by every
+    // level.  Contribution-block pool: after level l is factored, the trailing nr x nr
+    // block (nr = m - ncol) of each of its fronts is stored in the pool until the parent's
+    // extend-add reads it; the pool addresses are planned here by first fit over the
+    // blocks' lifetimes (stored at the end of the child's level, dead once the parent's
+    // level has started).
     std::vector<std::vector<int32_t>> lev_sn(nlev);
     for (int32_t b = 0; b < nsn; ++b) lev_sn[s->sn_level[b]].push_back(b);
+    auto al32 = [](int64_t x) { return (x + 31) / 32 * 32; };      // 256-byte aligned blocks
     s->front_off.assign(nsn, 0);
-    s->lev_arena_begin.assign(nlev, 0);
-    s->lev_arena_end.assign(nlev, 0);
-    int64_t off = 0;
+    s->l_off.assign(nsn, 0);
+    s->cb_off.assign(nsn, -1);
+    s->lev_ws.assign(nlev, 0);
+    s->ws_total = 0;
+    int64_t loff = 0;
     for (int32_t l = 0; l < nlev; ++l) {
-        s->lev_arena_begin[l] = off;
+        int64_t off = 0;
         for (int32_t b : lev_sn[l]) {
             s->front_off[b] = off;
-            int64_t m = msz(b);
-            off += ((m * m + 31) / 32) * 32;     // 256-byte aligned fronts
+            off += al32(msz(b) * msz(b));
+            s->l_off[b] = loff;
+            loff += al32(msz(b) * ncol(b));
         }
-        s->lev_arena_end[l] = off;
+        s->lev_ws[l] = off;
+        s->ws_total = std::max(s->ws_total, off);
     }
-    s->arena = off;
+    s->l_total = loff;
+    {
+        std::map<int64_t, int64_t> hole;         // free intervals of the pool: start -> length
+        int64_t top = 0;
+        auto release = [&](int64_t st, int64_t len) {
+            auto it = hole.emplace(st, len).first;
+            if (it != hole.begin()) {
+                auto pv = std::prev(it);
+                if (pv->first + pv->second == it->first) { pv->second += it->second; hole.erase(it); it = pv; }
+            }
+            auto nx = std::next(it);
+            if (nx != hole.end() && it->first + it->second == nx->first) { it->second += nx->second; hole.erase(nx); }
+            if (it->first + it->second == top) { top = it->first; hole.erase(it); }
+        };
+        for (int32_t l = 0; l < nlev; ++l) {
+            for (int32_t p : lev_sn[l])
+                for (int32_t c : children[p])
+                    if (s->cb_off[c] >= 0) release(s->cb_off[c], al32((int64_t)s->sn_nrow[c] * s->sn_nrow[c]));
+            for (int32_t b : lev_sn[l]) {
+                const int64_t nr = s->sn_nrow[b];
+                if (nr == 0) continue;
+                const int64_t need = al32(nr * nr);
+                auto it = hole.begin();
+                while (it != hole.end() && it->second < need) ++it;
+                if (it != hole.end()) {
+                    s->cb_off[b] = it->first;
+                    const int64_t st = it->first + need, len = it->second - need;
+                    hole.erase(it);
+                    if (len > 0) hole.emplace(st, len);
+                } else {
+                    s->cb_off[b] = top;
+                    top += need;
+                    s->cb_total = std::max(s->cb_total, top);
+                }
+            }
+        }
+    }
+    // per-level store tasks: copy each front's L columns to L storage and its
+    // contribution block to the pool (one unit per front column)
+    s->store_tasks.clear();
+    s->lev_store_off.assign(nlev + 1, 0);
+    s->lev_store_cols.assign(nlev, 0);
+    for (int32_t l = 0; l < nlev; ++l) {
+        s->lev_store_off[l] = (int32_t)s->store_tasks.size();
+        int32_t cols = 0;
+        for (int32_t b : lev_sn[l]) {
+            StoreTask t{};
+            t.ws_off = s->front_off[b];
+            t.l_off = s->l_off[b];
+            t.cb_off = s->cb_off[b];
+            t.m = (int32_t)msz(b);
+            t.ncol = ncol(b);
+            t.col_pre = cols;
+            cols += t.m;
+            s->store_tasks.push_back(t);
+        }
+        s->lev_store_cols[l] = cols;
+    }
+    s->lev_store_off[nlev] = (int32_t)s->store_tasks.size();
 
     // assembly map of the stored entries whose permuted position is in the lower triangle
     {
@@ -331,7 +403,7 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
                     lr = ncol(b) + (std::lower_bound(rb, re, r) - rb);
                 }
                 elev[p] = s->sn_level[b];
-                edest[p] = s->front_off[b] + (int64_t)lc * msz(b) + lr;
+                edest[p] = s->front_off[b] + (int64_t)lc * msz(b) + lr;   // workspace offset
             }
         }
         s->asm_lev_off.assign(nlev + 1, 0);
@@ -381,11 +453,11 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
                 int32_t c = children[p][qn];
                 if (s->sn_nrow[c] == 0) continue;
                 ExtendTask t{};
-                t.child_off = s->front_off[c];
-                t.parent_off = s->front_off[p];
+                t.child_off = s->cb_off[c];              // the child's block in the pool
+                t.parent_off = s->front_off[p];          // the parent's front in the workspace
                 t.rel_off = rel_off[c];
-                t.child_m = (int32_t)msz(c);
-                t.child_ncol = ncol(c);
+                t.child_m = s->sn_nrow[c];               // leading dimension of the block
+                t.child_ncol = 0;
                 t.parent_m = (int32_t)msz(p);
                 t.col_pre = ps.cols;
                 ps.cols += s->sn_nrow[c];
@@ -404,7 +476,7 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
         sn_panel0[b] = (int32_t)s->panels.size();
         for (int32_t k0 = 0; k0 < ncol(b); k0 += nb) {
             PanelDesc pd{};
-            pd.front_off = s->front_off[b];
+            pd.front_off = s->l_off[b];                  // the solves read L storage
             pd.idx_off = s->sn_idx_off[b];
             pd.m = (int32_t)msz(b);
             pd.k0 = k0;
@@ -419,12 +491,14 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
     s->lev_step_off.assign(nlev + 1, 0);
     s->wbuf_max = 0;
     s->mt_max = 0;
+    s->sl_max = 0;
+    s->ex_max = 0;
     for (int32_t l = 0; l < nlev; ++l) {
         s->lev_step_off[l] = (int32_t)s->steps.size();
         int32_t T = 0;
         for (int32_t b : lev_sn[l]) T = std::max<int32_t>(T, (int32_t)cdiv(ncol(b), nb));
         for (int32_t t = 0; t < T; ++t) {
-            StepDesc sd{(int64_t)s->tasks.size(), 0, 0, 0, l, 0.0, 0.0};
+            StepDesc sd{(int64_t)s->tasks.size(), 0, 0, 0, l, 0.0, 0.0, 0, 0, 0, 0};
             int64_t wb = 0;
             for (int32_t b : lev_sn[l]) {
                 if ((int64_t)t * nb >= ncol(b)) continue;
@@ -443,6 +517,17 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
                 int32_t nt = (int32_t)cdiv(tk.r, 64);
                 sd.tiles4 += nt;
                 sd.tiles3 += nt * (nt + 1) / 2;
+                // tensor-core Schur update: 128-row slice tiles of L21 and W, and the
+                // 128 x 64 output tiles (bi, bj <= 2 bi + 1) of the lower triangle
+                const int32_t nrt = (int32_t)cdiv(tk.r, 128), nct = nt;
+                tk.sl_pre = sd.sl_tiles;
+                tk.tc_pre = sd.tc_tiles;
+                tk.sl_off = sd.sl_bytes;
+                tk.ex_off = sd.ex_count;
+                sd.sl_tiles += 2 * nrt;
+                sd.tc_tiles += nrt > 0 ? (nrt - 1) * nrt + nct : 0;
+                sd.sl_bytes += (int64_t)2 * nrt * kTcSlices * kTcSliceBytes;
+                sd.ex_count += 2 * (int64_t)tk.r;
                 sd.flops4 += 2.0 * tk.r * (double)tk.w * tk.w;
                 sd.flops3 += (double)tk.w * tk.r * (tk.r + 1.0);
                 sd.count++;
@@ -450,6 +535,8 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
             }
             s->wbuf_max = std::max(s->wbuf_max, wb);
             s->mt_max = std::max(s->mt_max, sd.count);
+            s->sl_max = std::max(s->sl_max, sd.sl_bytes);
+            s->ex_max = std::max(s->ex_max, sd.ex_count);
             s->steps.push_back(sd);
         }
     }
@@ -512,6 +599,9 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
         inf.l_offdiag_entries += (int64_t)tk.r * tk.w;
         inf.l_diag_entries += (int64_t)tk.w * tk.w;
     }
+    inf.l_storage_entries = s->l_total;
+    inf.workspace_entries = s->ws_total;
+    inf.cb_pool_entries = s->cb_total;
     inf.analyze_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return SS_OK;
@@ -587,18 +677,77 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
         }
         const int32_t lev = s->sn_level[b];
         if (lev < 0 || lev >= s->nlev) return fail("bad level");
-        if (s->front_off[b] < s->lev_arena_begin[lev] || s->front_off[b] + m * m > s->lev_arena_end[lev])
-            return fail("front outside its level's arena range");
-        if (s->front_off[b] % 32) return fail("front not 256-byte aligned");
+        if (s->front_off[b] < 0 || s->front_off[b] + m * m > s->lev_ws[lev] || s->lev_ws[lev] > s->ws_total)
+            return fail("front outside its level's workspace");
+        if (s->front_off[b] % 32 || s->l_off[b] % 32) return fail("front or L block not 256-byte aligned");
+        if (s->l_off[b] < 0 || s->l_off[b] + m * ncol > s->l_total) return fail("L block outside L storage");
+        const int64_t nr = s->sn_nrow[b];
+        if ((nr > 0) != (s->cb_off[b] >= 0)) return fail("contribution block without a pool slot (or vice versa)");
+        if (nr > 0 && (s->cb_off[b] % 32 || s->cb_off[b] + nr * nr > s->cb_total))
+            return fail("contribution block outside the pool");
         const int32_t p = s->sn_parent[b];
         if (p >= 0 && (p <= b || s->sn_level[p] <= lev)) return fail("parent not after child");
+        if ((p >= 0) != (nr > 0)) return fail("a root with rows below its block, or a child without");
     }
-    if (s->lev_arena_end[s->nlev - 1] != s->arena) return fail("arena size mismatch");
+    // fronts of one level do not overlap in the workspace; L blocks never overlap
+    for (int32_t l = 0; l < s->nlev; ++l) {
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        for (int32_t b = 0; b < nsn; ++b)
+            if (s->sn_level[b] == l) {
+                const int64_t m = (int64_t)(s->sn_first[b + 1] - s->sn_first[b]) + s->sn_nrow[b];
+                iv.push_back({s->front_off[b], s->front_off[b] + m * m});
+            }
+        std::sort(iv.begin(), iv.end());
+        for (size_t i = 1; i < iv.size(); ++i)
+            if (iv[i].first < iv[i - 1].second) return fail("two fronts of one level overlap");
+    }
+    {
+        std::vector<std::pair<int64_t, int64_t>> iv;
+        for (int32_t b = 0; b < nsn; ++b) {
+            const int64_t nc = s->sn_first[b + 1] - s->sn_first[b];
+            iv.push_back({s->l_off[b], s->l_off[b] + (nc + s->sn_nrow[b]) * nc});
+        }
+        std::sort(iv.begin(), iv.end());
+        for (size_t i = 1; i < iv.size(); ++i)
+            if (iv[i].first < iv[i - 1].second) return fail("two L blocks overlap");
+    }
+    // two contribution blocks alive at the same time never share pool entries: block b
+    // lives from the end of level(b) until level(parent(b)) has started
+    {
+        struct Live { int64_t a, e; int32_t born, dies; };
+        std::vector<Live> lv;
+        for (int32_t b = 0; b < nsn; ++b)
+            if (s->cb_off[b] >= 0)
+                lv.push_back({s->cb_off[b], s->cb_off[b] + (int64_t)s->sn_nrow[b] * s->sn_nrow[b], s->sn_level[b],
+                              s->sn_level[s->sn_parent[b]]});
+        std::sort(lv.begin(), lv.end(), [](const Live &x, const Live &y) { return x.a < y.a; });
+        for (size_t i = 0; i < lv.size(); ++i)
+            for (size_t j = i + 1; j < lv.size() && lv[j].a < lv[i].e; ++j) {
+                // overlapping addresses: one must die (its parent's level starts) no later
+                // than the level whose end stores the other
+                const bool ok = lv[i].dies <= lv[j].born || lv[j].dies <= lv[i].born;
+                if (!ok) return fail("two live contribution blocks share pool entries");
+            }
+    }
+    // store tasks: every front of a level, column prefixes, offsets matching the plan
+    for (int32_t l = 0; l < s->nlev; ++l) {
+        int32_t cols = 0;
+        for (int32_t q = s->lev_store_off[l]; q < s->lev_store_off[l + 1]; ++q) {
+            const StoreTask &t = s->store_tasks[q];
+            if (t.col_pre != cols) return fail("store column prefix");
+            cols += t.m;
+            if (t.ws_off + (int64_t)t.m * t.m > s->lev_ws[l]) return fail("store source outside the workspace");
+            if (t.l_off + (int64_t)t.m * t.ncol > s->l_total) return fail("store L destination out of range");
+            const int64_t nr = t.m - t.ncol;
+            if (nr > 0 && (t.cb_off < 0 || t.cb_off + nr * nr > s->cb_total)) return fail("store pool destination");
+        }
+        if (cols != s->lev_store_cols[l]) return fail("store column total");
+    }
     for (int32_t l = 0; l < s->nlev; ++l) {
         for (int64_t q = s->asm_lev_off[l]; q < s->asm_lev_off[l + 1]; ++q) {
             if (s->asm_e[q] < 0 || s->asm_e[q] >= s->nnz) return fail("assembly entry out of range");
-            if (s->asm_dest[q] < s->lev_arena_begin[l] || s->asm_dest[q] >= s->lev_arena_end[l])
-                return fail("assembly destination outside the level's arena range");
+            if (s->asm_dest[q] < 0 || s->asm_dest[q] >= s->lev_ws[l])
+                return fail("assembly destination outside the level's workspace");
         }
     }
     // every stored lower entry is assembled exactly once, into the right front
@@ -635,9 +784,10 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
                 if (v < 0 || v >= et.parent_m) return fail("relmap entry outside the parent front");
                 if (r > 0 && v <= s->relmap[et.rel_off + r - 1]) return fail("relmap not increasing");
             }
-            if (et.child_off + (int64_t)et.child_m * et.child_m > s->arena ||
-                et.parent_off + (int64_t)et.parent_m * et.parent_m > s->arena)
-                return fail("extend-add front outside the arena");
+            if (et.child_ncol != 0 || et.child_off < 0 || et.child_off + (int64_t)et.child_m * et.child_m > s->cb_total)
+                return fail("extend-add source outside the contribution-block pool");
+            if (et.parent_off < 0 || et.parent_off + (int64_t)et.parent_m * et.parent_m > s->ws_total)
+                return fail("extend-add destination outside the workspace");
         }
         if (cols != ps.cols) return fail("extend-add pass column count");
         std::sort(parents.begin(), parents.end());
@@ -649,17 +799,18 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
         const int32_t b = pd.sn;
         const int32_t ncol = s->sn_first[b + 1] - s->sn_first[b];
         if (pd.w <= 0 || pd.w > s->nb || pd.k0 < 0 || pd.k0 + pd.w > ncol) return fail("panel columns");
-        if (pd.g0 != s->sn_first[b] + pd.k0 || pd.front_off != s->front_off[b] ||
+        if (pd.g0 != s->sn_first[b] + pd.k0 || pd.front_off != s->l_off[b] ||
             pd.idx_off != s->sn_idx_off[b] || pd.m != ncol + s->sn_nrow[b])
             return fail("panel descriptor mismatch");
     }
     for (const StepDesc &sd : s->steps) {
-        int32_t t4 = 0, t3 = 0;
+        int32_t t4 = 0, t3 = 0, tsl = 0, ttc = 0;
+        int64_t slb = 0, exc = 0;
         for (int32_t t = 0; t < sd.count; ++t) {
             const StepTask &tk = s->tasks[sd.task_off + t];
             if (tk.panel < 0 || tk.panel >= npan) return fail("step panel id");
             const PanelDesc &pd = s->panels[tk.panel];
-            if (tk.k0 != pd.k0 || tk.w != pd.w || tk.m != pd.m || tk.front_off != pd.front_off)
+            if (tk.k0 != pd.k0 || tk.w != pd.w || tk.m != pd.m || tk.front_off != s->front_off[pd.sn])
                 return fail("step task / panel mismatch");
             if (tk.r != tk.m - tk.k0 - tk.w || tk.r < 0) return fail("step trailing size");
             if (tk.wbuf_off < 0 || tk.wbuf_off + (int64_t)tk.r * tk.w > s->wbuf_max) return fail("W scratch range");
@@ -668,8 +819,20 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
             int32_t nt = (tk.r + 63) / 64;
             t4 += nt;
             t3 += nt * (nt + 1) / 2;
+            // tensor-core path: slice tiles, output tiles, scratch ranges of this task
+            const int32_t nrt = (tk.r + 127) / 128;
+            if (tk.sl_pre != tsl || tk.tc_pre != ttc || tk.sl_off != slb || tk.ex_off != exc)
+                return fail("tensor-core prefixes");
+            tsl += 2 * nrt;
+            ttc += nrt > 0 ? (nrt - 1) * nrt + nt : 0;
+            slb += (int64_t)2 * nrt * kTcSlices * kTcSliceBytes;
+            exc += 2 * (int64_t)tk.r;
+            if (slb > s->sl_max || exc > s->ex_max) return fail("tensor-core scratch range");
+            if (tk.sl_off % 16) return fail("slice block not 16-byte aligned");
         }
         if (t4 != sd.tiles4 || t3 != sd.tiles3) return fail("step tile totals");
+        if (tsl != sd.sl_tiles || ttc != sd.tc_tiles || slb != sd.sl_bytes || exc != sd.ex_count)
+            return fail("tensor-core step totals");
     }
     std::vector<char> pseen(npan, 0);
     for (const SolveLevel &sl : s->solve_levels) {

@@ -1,0 +1,78 @@
+"""Tensor-core Schur update (tcgen05.mma on sliced FP16 operands, FP64-accurate) against
+the CUDA-core FP64 path and the oracle: the MMA tile self-test (exact integer products),
+the inertia of factors whose every Schur step runs on the tensor cores (bit-exact against
+the dense oracle's eigenvalue counts), and solves with those factors against the dense
+solution and against the CUDA-core factor."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import dense, spectral
+from tests.gpu_util import mid_gap_shifts, setup
+from workloads.pencils import config_pencil, normal_block
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_mma_tile_selftest_exact(gpu_lib, seed):
+    ctx = gpu_lib.Context(0)
+    assert ctx.selftest_tc(seed) == 0.0
+
+
+def _factor_pair(gpu_lib, p, shifts):
+    ctx, sym, a, b = setup(gpu_lib, p)
+    ctx.set_schur_mode("tensor", 0.0)            # every Schur step on the tensor cores
+    n0 = ctx.launch_count()
+    ctx.profile(["schur_tc", "schur"])
+    ft = sym.factor(a, b, shifts, "fp64")
+    tc_launches = ctx.profile_query("schur_tc")[0]
+    simt_launches = ctx.profile_query("schur")[0]
+    ctx.profile(())
+    ctx.set_schur_mode("simt")
+    fs = sym.factor(a, b, shifts, "fp64")
+    ctx.set_schur_mode("tensor")
+    return ctx, sym, a, b, ft, fs, tc_launches, simt_launches
+
+
+def test_config1_tensor_core_factor_inertia_and_solves(gpu_lib):
+    p = config_pencil(1)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    shifts = mid_gap_shifts(lam, [0, 10, 40, 85, 300, 600])
+    ctx, sym, a, b, ft, fs, n_tc, n_simt = _factor_pair(gpu_lib, p, shifts)
+    assert n_tc > 0 and n_simt == 0
+    for j, s in enumerate(shifts):
+        assert ft.inertia(j)[0] == spectral.count_below(lam, s)
+        assert ft.inertia(j)[:3] == fs.inertia(j)[:3]
+    A, B = p.dense("a"), p.dense("b")
+    R = torch.tensor(normal_block(p.n, 6, 11), device="cuda")
+    for j in (0, 3, 5):
+        Xt = ft.solve(j, R, refine=0).cpu().numpy()
+        Xs = fs.solve(j, R, refine=0).cpu().numpy()
+        ref = np.linalg.solve(A - shifts[j] * B, R.cpu().numpy())
+        assert np.abs(Xt - ref).max() <= 1e-9 * np.abs(ref).max()
+        # the two factors agree as closely as two FP64 factorisations in another order
+        assert np.abs(Xt - Xs).max() <= 1e-9 * np.abs(Xs).max()
+
+
+def test_gauss16_tensor_core_inertia_matches_golden(gpu_lib):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "gauss16_inertia.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    sig = [float(r[0]) for r in rows]
+    neg = [int(r[1]) for r in rows]
+    p = config_pencil(2)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    ctx.set_schur_mode("tensor")
+    ctx.profile(["schur_tc"])
+    f = sym.factor(a, b, sig, "fp64")
+    assert ctx.profile_query("schur_tc")[0] > 0
+    ctx.profile(())
+    for j in range(len(sig)):
+        assert f.inertia(j)[0] == neg[j]
+    # solve to 1e-10 with one refinement step against the pencil's own residual
+    R = torch.tensor(normal_block(p.n, 4, 3), device="cuda")
+    for j in (0, 3):
+        X = f.solve(j, R, refine=1)
+        res = sym.spmm(a, b, X, 1.0, -sig[j]) - R
+        assert (res.norm() / R.norm()).item() <= 1e-10
