@@ -1,12 +1,19 @@
 #!/usr/bin/env python
 """Benchmark: slice solves per second on synthetic Gaussian-orbital pencils.
 
-A step is one pass of the whole hot path over one pencil: Lanczos DOS estimate
-(Section 3.1), shift placement by CDOS roots, one batched LDL^T of A - sigma_j B for
-every shift plus the two region bounds, inertia counts, shift-invert subspace
-iterations on every probe until every slice validates (Section 2.2), and validation.
-value = shifts (slice solves) completed per second; every validated eigenpair must
-meet the normalised residual 1e-10.
+A step is one slice solve (the unit of the metric): the LDL^T of A - sigma_j B for one
+shift (Alg. 2 step 2), its Sylvester inertia (Section 2.2), the shift-invert subspace
+iteration of that shift's window (Alg. 2) until as many Ritz pairs as the window's exact
+eigenvalue count meet the normalised residual 1e-10, and the validation of the window
+against the inertia counts.  The shifts and window bounds of the pencil are placed once
+(Lanczos DOS estimate, Section 3.1; ball partition; one batched FP64 factor for the exact
+counts at the window bounds) before the timed steps and reported separately.  Step s
+solves window s mod n_s.
+
+value = validated slice solves per second with the pencil resident in HBM (CUDA events
+over the timed steps).  e2e repeats the steps through the same public calls with the
+pencil's values copied in from pinned host memory every step and the eigenvalues and
+residuals read back.  fp64_side runs the plain FP64 path on a spread of the same windows.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU (torchrun, one rank per GPU): every rank solves its own replica of the
@@ -16,7 +23,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -32,23 +38,23 @@ WORKLOADS = {
     "gauss6": dict(config=1, n_e=86, n_s=4,
                    name="gaussian-s 6x6x6 lattice, 4 fn/atom, N=864, n_e=86, 4 shifts"),
 }
+DEFAULT_WORKLOAD = "gauss16"
 METRIC = "slice solves/s at N=110,592 (mixed vs FP64, resid<=1e-10); factor TFLOP/s"
-FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
-FP64_ALU_PEAK_TFLOPS = 1.25                               # GB300 FP64 nominal: 152 SMs x 2 FMA/clk x 2 x 2.07 GHz
 FLOP_CLASSES = {"schur", "panel", "fwd_update", "bwd_gather", "spmm", "gram", "gemm", "solve",
-                "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32", "solve_f32"}
+                "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32", "solve_f32", "schur_tc"}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gauss16", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side step")
+    ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side steps")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--sequence", type=int, default=0,
                     help="instead of the benchmark: solve this many pencils A_i = A_0 + 0.1 2^-i R of the "
@@ -135,49 +141,94 @@ def replica_rate(ws, units_per_rank, seconds_local):
 
 
 # ----------------------------------------------------------------- oracle (CPU) leg
-def oracle_sample(wl, seconds_budget=20.0):
-    """Time the CPU oracle on a bounded sample and scale it to slice solves/s of the
-    workload: the oracle's route to every slice's eigenpairs is one dense generalised
-    eigensolve (O(N^3)); it is timed on the 6^3 pencil (N=864) and scaled by (N/864)^3."""
+def band_work(rows, bw):
+    """Multiply-adds of the band LDL^T of a rows x rows block of bandwidth bw (column j
+    updates the (min(rows - 1 - j, bw))^2 entries below and right of its pivot)."""
+    import numpy as np
+    t = np.minimum(rows - 1 - np.arange(rows, dtype=np.float64), bw)
+    return float(np.sum(t * t))
+
+
+class OracleSample:
+    """The oracle's factor + inertia of one slice on a bounded sample: the band LDL^T
+    (natural order) of the leading rows x rows principal block of A - sigma B, its time
+    scaled to the whole N x N band by the elimination's multiply-add count."""
+
+    def __init__(self, p, target_s):
+        from oracle import spectral
+        from oracle.build_oracle import build
+        build()
+        self.p = p
+        self.band_a = spectral.band_of(p.with_a(p.a), 0.0)       # lower band of A
+        self.band_b = spectral.band_of(p.with_a(p.b), 0.0)       # lower band of B
+        self.bw = self.band_a.shape[1] - 1
+        probe = min(p.n, 2 * self.bw + 1)
+        _, ts = self.time(0.0, probe)
+        rate = band_work(probe, self.bw) / max(ts, 1e-6)
+        lo, hi = probe, p.n
+        while lo < hi:                               # largest block that fits target_s
+            mid = (lo + hi + 1) // 2
+            if band_work(mid, self.bw) / rate <= target_s:
+                lo = mid
+            else:
+                hi = mid - 1
+        self.rows = lo
+
+    def time(self, sigma, rows):
+        from oracle import dense
+        band = self.band_a[:rows] - sigma * self.band_b[:rows]
+        t0 = time.perf_counter()
+        dense.band_ldlt(band)
+        return None, time.perf_counter() - t0
+
+    def slice_seconds(self, sigma):
+        """(seconds for one full slice's factor + inertia, sample seconds)."""
+        _, ts = self.time(sigma, self.rows)
+        return ts * band_work(self.p.n, self.bw) / band_work(self.rows, self.bw), ts
+
+    def describe(self, ts):
+        return (f"band LDL^T inertia (natural order, bandwidth {self.bw}) of the leading {self.rows} x "
+                f"{self.rows} block of A - sigma B ({ts:.2f} s), scaled to the N={self.p.n} band by the "
+                f"elimination's multiply-add count; the oracle's in-slice eigenpairs (a dense O(N^3) "
+                f"reduction shared by all slices) are not in the sample, so the rate bounds the oracle's "
+                f"slice-solve rate from above")
+
+
+def cpu_baseline(p, sigma, target_s=15.0):
     from oracle import dense
-    from workloads.pencils import config_pencil
-    from oracle.build_oracle import build
-    build()
-    p1 = config_pencil(1)
-    A, B = p1.dense("a"), p1.dense("b")
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        dense.gen_eig(A, B, vectors=True)
-        reps += 1
-        if time.perf_counter() - t0 > min(seconds_budget, 3.0) and reps >= 1:
-            break
-    t864 = (time.perf_counter() - t0) / reps
-    n = 16384 if wl["config"] == 2 else 864
-    t_full = t864 * (n / 864) ** 3
-    return dict(value=wl["n_s"] / t_full, unit="slice solves/s", cores=dense.num_threads(), kind="oracle",
-                sample=f"dense generalised eigensolve (Cholesky + Householder + QL, all eigenpairs) of the "
-                       f"N=864 pencil, {reps} run(s) x {t864:.3f} s, scaled by (N/864)^3 to N={n} "
-                       f"and divided among {wl['n_s']} slices"), t864
+    smp = OracleSample(p, target_s)
+    full, ts = smp.slice_seconds(sigma)
+    return dict(value=1.0 / full, unit="slice solves/s", cores=dense.num_threads(), kind="oracle",
+                sample=smp.describe(ts))
 
 
 def run_reference(args, wl):
     ws, rank, _ = dist_setup(args)
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample(wl, 1.0)
-    vals = []
-    for _ in range(args.steps):
-        base, _ = oracle_sample(wl, 2.0)
-        vals.append(base["value"])
-    v = sum(vals) / len(vals)
-    base["value"] = v
+    from oracle import dense
+    from workloads.pencils import config_pencil
+    p = config_pencil(wl["config"])
+    smp = OracleSample(p, 4.0)
+    sig = [-1.0 + 0.1 * i for i in range(args.warmup + args.steps)]
+    for w in range(args.warmup):
+        smp.slice_seconds(sig[w])
+    t0 = time.perf_counter()
+    fulls, samples = [], []
+    for s in range(args.steps):
+        full, ts = smp.slice_seconds(sig[args.warmup + s])
+        fulls.append(full)
+        samples.append(ts)
+    wall = time.perf_counter() - t0
+    v = len(fulls) / sum(fulls)
+    cpu = dict(value=v, unit="slice solves/s", cores=dense.num_threads(), kind="oracle",
+               sample="per step: " + smp.describe(sum(samples) / len(samples)))
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": "slice solves/s",
                       "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": 1e3 * wl["n_s"] / v, "higher_is_better": True, "scaling": "weak",
+                      "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
                       "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                       "config": {"workload": wl["name"], "l2": "inputs larger than L2"},
-                      "cpu_baseline": base,
+                      "cpu_baseline": cpu,
                       "e2e": {"value": v, "unit": "slice solves/s", "h2d_bytes_per_step": 0,
                               "d2h_bytes_per_step": 0}}), flush=True)
 
@@ -192,12 +243,13 @@ def main():
     import torch
 
     from paper_1908_06043_gb300 import api, build
-    from paper_1908_06043_gb300.driver import DosModel, SliceSolver, default_basis_width
+    from paper_1908_06043_gb300.driver import DosModel, SliceSolver, plan_slices, solve_slice
     from workloads.pencils import config_pencil, normal_block
 
     build()
     ws, rank, local = dist_setup(args)
     dev = torch.cuda.current_device()
+    t_setup = time.perf_counter()
     p = config_pencil(wl["config"])
     ctx = api.Context(dev)
     sym = ctx.analyze(p.rowptr, p.colind)
@@ -205,39 +257,11 @@ def main():
     a = torch.tensor(p.a, device="cuda")
     b = torch.tensor(p.b, device="cuda")
     n_e, n_s = wl["n_e"], wl["n_s"]
-    k = 0                                     # probe basis: 2 c + 16 per window of c eigenvalues
-    steps_dos, n_vec = 100, 4
     ha = torch.tensor(p.a).pin_memory()
     hb = torch.tensor(p.b).pin_memory()
-
-    def step(precision, a_dev, b_dev, seed):
-        t0 = time.perf_counter()
-        start = torch.tensor(normal_block(p.n, n_vec, 1000 + seed), device="cuda")
-        runs = sym.dos_estimate(a_dev, b_dev, steps_dos, start)
-        model = DosModel(p.n, runs)
-        solver = SliceSolver(sym, a_dev, b_dev, precision=precision)
-        lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
-        t1 = time.perf_counter()
-        res = solver.run(shifts, lam_min, lam_max, model, seed=seed, splits=splits, ks=ks)
-        # band-energy gradient of the delivered eigenpairs (SDDMM on the stored pattern)
-        tg = time.perf_counter()
-        lam_d = torch.tensor(res.eigenvalues, device="cuda")
-        ga, gb = sym.band_energy_grad(res.eigenvectors, lam_d)
-        res.timings["grad"] = (ga, gb)
-        res.timings["grad_s"] = time.perf_counter() - tg
-        if args.verbose:
-            print(f"[step {precision} seed={seed}] dos+place {t1 - t0:.3f}s factor {res.timings['factor_s']:.3f}s "
-                  f"probes {res.timings['solve_s']:.3f}s total {time.perf_counter() - t0:.3f}s rounds {res.rounds} "
-                  f"found {len(res.eigenvalues)} (nu(max)={res.timings['n_below_max']}) "
-                  f"maxres {res.residuals.max() if len(res.residuals) else -1:.2e} "
-                  f"slices {[i[:3] for i in res.slices]} "
-                  f"quality {[(q[0], float(f'{q[1]:.2e}')) for q in res.timings['quality']]}", file=sys.stderr, flush=True)
-        return res
-
-    def check(res):
-        ok = bool(res.timings["converged"]) and len(res.residuals) > 0 and float(res.residuals.max()) <= 1e-10
-        ok = ok and all(n_conv >= n_exact for n_exact, _, n_conv, _ in res.slices)
-        return ok
+    steps_dos, n_vec = 100, 4
+    peak64 = ctx.measure_peak("fp64", 0.5)
+    peak32 = ctx.measure_peak("fp32", 0.5)
 
     if args.sequence:
         # SCF-like pencil sequence: DOS placement for the first pencil, k-means probe
@@ -255,10 +279,11 @@ def main():
         t1 = time.perf_counter()
         for i, rs in enumerate(res):
             mig = rs.timings["migration"]
+            ok = bool(rs.timings["converged"]) and len(rs.residuals) > 0 and float(rs.residuals.max()) <= 1e-10
             print(json.dumps({"sequence_step": i, "workload": wl["name"], "precision": args.precision,
                               "seconds": rs.timings["total_s"], "factor_s": rs.timings["factor_s"],
                               "rounds": rs.rounds, "probe_iterations": rs.timings["iterations"],
-                              "validated": check(rs), "eigenpairs": int(len(rs.eigenvalues)),
+                              "validated": ok, "eigenpairs": int(len(rs.eigenvalues)),
                               "max_resid": float(rs.residuals.max()),
                               "shifts": [float(x) for x in rs.shifts], "n_probes": len(rs.shifts),
                               "migration_init": mig["init"] if mig else "DOS placement",
@@ -266,142 +291,170 @@ def main():
         print(json.dumps({"sequence_total_s": t1 - t0, "pencils": len(res)}), flush=True)
         return
 
+    # placement, once per pencil: DOS estimate, shifts and windows, exact window counts
+    torch.cuda.synchronize()
+    t_place = time.perf_counter()
+    start = torch.tensor(normal_block(p.n, n_vec, 1000), device="cuda")
+    model = DosModel(p.n, sym.dos_estimate(a, b, steps_dos, start))
+    solver = SliceSolver(sym, a, b, precision=args.precision)
+    plan = plan_slices(solver, model, n_e, n_s)
+    torch.cuda.synchronize()
+    placement_s = time.perf_counter() - t_place
+    setup_s = time.perf_counter() - t_setup
+
     if args.only_probe:
-        # one representative probe of the workload (shift 8 of the placement), for ncu; a
-        # short DOS run (20 steps, one vector) keeps the launch count small
-        start = torch.tensor(normal_block(p.n, 1, 1000), device="cuda")
-        model = DosModel(p.n, sym.dos_estimate(a, b, 20, start))
-        solver = SliceSolver(sym, a, b, precision="fp64")
-        lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s)
+        # one representative probe of the workload (window n_s/2), for ncu
         j = n_s // 2
-        f = sym.factor(a, b, [shifts[j]], "fp64")
-        V0 = torch.tensor(normal_block(p.n, ks[j], 7), device="cuda")
+        f = sym.factor(a, b, [plan.shifts[j]], "fp64")
+        V0 = torch.tensor(normal_block(p.n, plan.ks[j], 7), device="cuda")
         t0 = time.perf_counter()
-        pr = f.slice_solve(0, splits[j], splits[j + 1], V0, max_iter=6, check_every=2, allow_noconv=True)
+        lo, hi = plan.window(j)
+        pr = f.slice_solve(0, lo, hi, V0, max_iter=6, check_every=2, allow_noconv=True)
         torch.cuda.synchronize()
-        print(json.dumps({"only_probe": True, "sigma": shifts[j], "k": ks[j], "iterations": pr.iterations,
-                          "seconds": time.perf_counter() - t0}), flush=True)
+        print(json.dumps({"only_probe": True, "sigma": plan.shifts[j], "k": plan.ks[j],
+                          "iterations": pr.iterations, "seconds": time.perf_counter() - t0}), flush=True)
         return
+
+    def log(tag, o, dt):
+        if args.verbose:
+            print(f"[{tag}] j={o.j} sigma={o.sigma:.4f} exact={o.n_exact} ok={o.ok} k={plan.ks[o.j]} "
+                  f"iters={o.iterations} rounds={o.rounds} factor={o.factor_s:.3f}s total={dt:.3f}s "
+                  f"prec={o.precision_used} maxres={o.resid.max() if o.resid.size else -1:.2e}",
+                  file=sys.stderr, flush=True)
 
     # warm-up; the last warm-up step is profiled per kernel class (CUDA events on the
     # launching stream) to pick the dominant kernel whose roofline the timed steps report
     for w in range(args.warmup):
         if w == args.warmup - 1:
             ctx.profile(api.L.KERNEL_CLASSES)
-        res = step(args.precision, a, b, w)
+        t0 = time.perf_counter()
+        o = solve_slice(solver, plan, w % n_s, seed=w)
+        log("warmup", o, time.perf_counter() - t0)
     prof = {c: ctx.profile_query(c) for c in api.L.KERNEL_CLASSES}
     ctx.profile(())
     if args.warmup == 0:                       # nothing profiled: report the solve sweep
-        prof["fwd_update"] = (1, 1e-9, 0.0)
+        prof["solve"] = (1, 1e-9, 0.0)
     dom = max(prof, key=lambda c: prof[c][1])
     tot_prof = sum(v[1] for v in prof.values())
 
-    # timed region (device-resident inputs)
+    # timed region: the pencil resident in HBM
     clocks = Clocks(dev)
     torch.cuda.synchronize()
     barrier(ws)
     clocks.start()
     ctx.profile([dom])
     n0 = ctx.launch_count()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    results = []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record()
+    outs = []
     for s in range(args.steps):
-        results.append(step(args.precision, a, b, 200 + s))
-    e1.record()
+        t0 = time.perf_counter()
+        o = solve_slice(solver, plan, s % n_s, seed=100 + s)
+        ev[s + 1].record()
+        outs.append(o)
+        log("timed", o, time.perf_counter() - t0)
     torch.cuda.synchronize()
     launches = ctx.launch_count() - n0
     dom_n, dom_t, dom_flops = ctx.profile_query(dom)
     ctx.profile(())
     clk = clocks.stop()
     barrier(ws)
-    t_local = e0.elapsed_time(e1) / 1e3 / args.steps
-    value = replica_rate(ws, n_s, t_local)
-    t_step = ws * n_s / value
-    all_ok = all(check(r) for r in results)
-    factor_s = sum(r.timings["factor_s"] for r in results) / len(results)
-    factor_tflops = (n_s + 2) * info["factor_flops"] / factor_s / 1e12
+    step_s = [ev[s].elapsed_time(ev[s + 1]) / 1e3 for s in range(args.steps)]
+    t_local = sum(step_s)
+    n_ok = sum(1 for o in outs if o.ok)
+    value = replica_rate(ws, n_ok, t_local)
+    ms_per_step = 1e3 * t_local / args.steps
+    factor_s = float(np.mean([o.factor_s for o in outs]))
+    factor_tflops = info["factor_flops"] / factor_s / 1e12
 
-    # end to end through the public API with host buffers: H2D of the pencil values,
-    # the step, D2H of the eigenvalues and residuals
+    # end to end through the public calls with host buffers: the pencil's values copied
+    # in from pinned memory, the slice solve, its eigenvalues and residuals read back
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
-        d2h = 0
+        d2h, ok2 = 0, 0
         for s in range(args.steps):
-            a2 = ha.to("cuda", non_blocking=True)
-            b2 = hb.to("cuda", non_blocking=True)
-            r = step(args.precision, a2, b2, 300 + s)
-            lam_h = torch.tensor(r.eigenvalues).cpu().numpy()
-            d2h += lam_h.nbytes + r.residuals.nbytes
+            a.copy_(ha, non_blocking=True)
+            b.copy_(hb, non_blocking=True)
+            o = solve_slice(solver, plan, s % n_s, seed=300 + s)
+            lam_h = np.asarray(o.theta, dtype=np.float64)
+            res_h = np.asarray(o.resid, dtype=np.float64)
+            d2h += lam_h.nbytes + res_h.nbytes
+            ok2 += int(o.ok)
         torch.cuda.synchronize()
-        e2e = {"value": replica_rate(ws, n_s, (time.perf_counter() - t0) / args.steps), "unit": "slice solves/s",
-               "h2d_bytes_per_step": int(2 * p.nnz * 8),
-               "d2h_bytes_per_step": int(d2h // args.steps)}
+        e2e = {"value": replica_rate(ws, ok2, time.perf_counter() - t0), "unit": "slice solves/s",
+               "h2d_bytes_per_step": int(2 * p.nnz * 8), "d2h_bytes_per_step": int(d2h // args.steps),
+               "validated_steps": ok2}
 
-    # FP64 side by side (one step, same workload)
+    # the plain FP64 path on a spread of the same windows, against the mixed steps that
+    # solved those windows in the timed loop
     fp64 = None
     if not args.no_fp64_side and args.precision == "mixed" and rank == 0:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r64 = step("fp64", a, b, 400)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        fp64 = {"value": n_s / t64, "unit": "slice solves/s", "validated": check(r64),
-                "factor_tflops": (n_s + 2) * info["factor_flops"] / r64.timings["factor_s"] / 1e12,
-                "max_resid": float(r64.residuals.max()) if len(r64.residuals) else None}
+        m = min(args.steps, n_s, 8)
+        js = sorted({int(round(i * (min(args.steps, n_s) - 1) / max(1, m - 1))) for i in range(m)})
+        solver64 = SliceSolver(sym, a, b, precision="fp64")
+        t64, ok64, f64s, res64 = [], 0, [], []
+        for jx in js:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            o = solve_slice(solver64, plan, jx, seed=500 + jx)
+            e1.record()
+            torch.cuda.synchronize()
+            t64.append(e0.elapsed_time(e1) / 1e3)
+            ok64 += int(o.ok)
+            f64s.append(o.factor_s)
+            res64.append(float(o.resid.max()) if o.resid.size else 0.0)
+            log("fp64", o, t64[-1])
+        t_mixed_same = sum(step_s[jx] for jx in js)
+        fp64 = {"value": ok64 / sum(t64), "unit": "slice solves/s", "windows": js, "validated": ok64,
+                "mixed_value_same_windows": len(js) / t_mixed_same,
+                "mixed_over_fp64": sum(t64) / t_mixed_same,
+                "factor_tflops": info["factor_flops"] / float(np.mean(f64s)) / 1e12,
+                "max_resid": max(res64) if res64 else None}
 
     # roofline of the dominant kernel class: algorithmic flops of its launches in the
-    # timed region (counted by the library from the schedule) over their event time
+    # timed region (counted by the library from the schedule) over their event time,
+    # against the FMA peak measured on this GPU at the start of the run
     per_launch = dom_t / max(dom_n, 1)
     if dom in FLOP_CLASSES and dom_t > 0:
         achieved = dom_flops / dom_t / 1e12
         f32 = dom.endswith("_f32")
-        peak = FP32_ALU_PEAK_TFLOPS if f32 else FP64_ALU_PEAK_TFLOPS
+        peak = peak32 if f32 else peak64
         bound, unit = "alu", "TFLOP/s"
-        peak_src = ("derived: 152 SMs x 128 FP32 lanes x 2 flops/FMA x 2.07 GHz" if f32 else
-                    "nominal GB300 FP64 rate 1.25 TFLOP/s = 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz "
-                    "(CUDA-core FP64; MEASURED_PEAKS.json has no FP64 figure)")
+        peak_src = (f"measured: {'FP32' if f32 else 'FP64'} FMA chains on this GPU at the start of this run "
+                    f"(ss_measure_peak, 0.5 s launch)")
     else:
         achieved, bound, unit, peak, peak_src = None, "unknown", None, None, None
-    traffic, traffic_src = None, None
-    if dom == "solve" and dom_n > 0 and info["l_offdiag_entries"] > 0:
-        # DRAM bytes per launch of the FP64 sweep solve, scaled from one ncu capture
-        # (k = 304 probe solve on this pencil: 832.3 MB read + 91.1 MB written) by the
-        # launch's width: L is read once per sweep, the N x k right-hand sides four times
-        k_avg = dom_flops / dom_n / (4.0 * info["l_offdiag_entries"])
-        def model(k):
-            return 2 * 8.0 * info["l_offdiag_entries"] + 4 * 8.0 * p.n * k
-        traffic = (832.3e6 + 91.1e6) * model(k_avg) / model(304)
-        traffic_src = (f"ncu dram__bytes_read+write of one k=304 launch on the N=16384 pencil, scaled to the "
-                       f"mean launch width k={k_avg:.0f} by the L + 4 N k model")
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": (achieved / peak) if achieved and peak else None, "traffic": traffic,
-                "traffic_source": traffic_src,
+                "frac": (achieved / peak) if achieved and peak else None, "traffic": None,
                 "launches": dom_n, "avg_launch_ms": 1e3 * per_launch,
                 "share_of_profiled_time": prof[dom][1] / tot_prof if tot_prof else None,
                 "peak_source": peak_src}
 
     cpu = None
-    if rank == 0:
-        cpu, _ = oracle_sample(wl)
-    r0 = results[-1]
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        cpu = cpu_baseline(p, plan.shifts[n_s // 2])
     out = {"metric": METRIC, "value": value, "unit": "slice solves/s", "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+           "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
            "data": "synthetic",
            "config": {"workload": wl["name"], "precision": args.precision,
-                      "probe_driver": "shift-invert subspace iteration (Alg. 2), Rayleigh-Ritz every 3rd iteration in the first round, once per later round",
-                      "shift_placement": "DOS ball partition (radius 2h ball <= basis)",
+                      "step": "one slice solve: LDL^T of A - sigma_j B, inertia, shift-invert subspace "
+                              "iteration of window j to resid <= 1e-10, validation by inertia counts",
+                      "windows": f"step s solves window s mod {n_s}",
+                      "shift_placement": "DOS ball partition, once per pencil (placement_s)",
                       "lanczos_steps": steps_dos, "lanczos_vectors": n_vec, "parallelism": f"replicas x{ws}",
-                      "l2": "inputs larger than L2 (factor arena > 129 MB)",
-                      "eigenpairs_validated": int(len(r0.eigenvalues)), "all_validated": all_ok,
-                      "max_resid": float(r0.residuals.max()) if len(r0.residuals) else None,
+                      "l2": "inputs larger than L2 (factor and N x k blocks of 100s of MB)",
+                      "placement_s": placement_s, "setup_s": setup_s,
+                      "validated_steps": n_ok, "step_s": [round(x, 4) for x in step_s],
+                      "max_resid": max(float(o.resid.max()) for o in outs if o.resid.size),
                       "factor_tflops": factor_tflops, "factor_s_per_step": factor_s,
-                      "rounds": r0.rounds, "probe_iterations": r0.timings["iterations"],
-                      "shift_solve_precision": [q[0] for q in r0.timings["quality"]]},
+                      "factor_flops_per_shift": info["factor_flops"],
+                      "probe_iterations": [o.iterations for o in outs],
+                      "solve_precision": [o.precision_used for o in outs],
+                      "measured_fma_peaks_tflops": {"fp64": peak64, "fp32": peak32}},
            "fp64_side": fp64, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
            "gpu_launches": int(launches), "clocks": clk,
            "profile_ms": {c: round(1e3 * v[1], 3) for c, v in prof.items() if v[0]},

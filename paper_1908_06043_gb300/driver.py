@@ -20,6 +20,9 @@ the library; this module sequences it and holds the O(n_s k) scalar logic:
 * ``SliceSolver.run``: factor every shift (one batched call), inertia, probes, rounds of
   subspace iterations until every slice validates; ``run_with_recovery`` inserts probes
   where eigenvalues are missing (Section 3.3).
+* ``plan_slices`` / ``solve_slice``: the same work one slice at a time -- shifts, window
+  bounds and their exact counts placed once per pencil, then per slice one factor, its
+  inertia, its probe and its validation (the benchmark's unit of work).
 * ``solve_sequence``: a sequence of pencils on one pattern with migration, warm starts and
   the trace monitor of Eq. 9.
 """
@@ -377,8 +380,9 @@ class SliceSolver:
         self.precision, self.tol, self.refine = precision, tol, refine
 
     def count_below(self, sigmas):
-        """Exact eigenvalue counts below each sigma (inertia of one batched factor)."""
-        f = self.sym.factor(self.a, self.b, sigmas, self.precision)
+        """Exact eigenvalue counts below each sigma (inertia of one batched FP64 factor
+        that keeps no L)."""
+        f = self.sym.factor(self.a, self.b, sigmas, "inertia")
         out = [f.inertia(j)[0] for j in range(len(sigmas))]
         f.close()
         return out
@@ -619,6 +623,124 @@ class SliceSolver:
         splits = [None] + [iv[j][0] for j in range(1, n_s)]
         ks = [int(-(-(1.15 * bc + 16) // 16) * 16) for bc in balls]
         return lam_min, lam_max, shifts, splits, ks
+
+
+@dataclass
+class SlicePlan:
+    """Shifts and windows of one pencil, placed once and reused by every slice solve:
+    probe j owns the window (bounds[j], bounds[j+1]] around shifts[j]; counts[i] is the
+    exact number of eigenvalues below bounds[i] (Sylvester inertia of an FP64 factor)."""
+    shifts: list
+    bounds: list
+    counts: list
+    ks: list
+    lam_min: float
+    lam_max: float
+
+    def window(self, j: int):
+        return self.bounds[j], self.bounds[j + 1]
+
+    def exact(self, j: int) -> int:
+        return self.counts[j + 1] - self.counts[j]
+
+
+@dataclass
+class SliceOutcome:
+    """One validated slice solve: the eigenpairs of window j (Section 2.2 validation)."""
+    j: int
+    sigma: float
+    theta: np.ndarray
+    X: torch.Tensor
+    resid: np.ndarray
+    n_exact: int
+    n_neg_sigma: int
+    ok: bool
+    factor_s: float
+    iterations: int
+    rounds: int
+    precision_used: str
+
+
+def plan_slices(solver: "SliceSolver", model: "DosModel", n_e: int, n_s: int, mode: str = "ball") -> SlicePlan:
+    """Place n_s shifts for the lowest n_e eigenvalues (place_shifts) and count the
+    eigenvalues below every window bound with one batched FP64 factor."""
+    lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s, mode=mode)
+    inner = [splits[j] if splits is not None and splits[j] is not None else 0.5 * (shifts[j - 1] + shifts[j])
+             for j in range(1, n_s)]
+    bounds = [lam_min] + inner + [lam_max]
+    counts = solver.count_below(bounds)
+    if ks is None:
+        ks = [None] * n_s
+    n = solver.sym.n
+    ks = [min(n, 4096, max(k or 0, _ceil16(2 * (counts[j + 1] - counts[j]) + 16), _ceil16(counts[j + 1] - counts[j] + 16)))
+          for j, k in enumerate(ks)]
+    return SlicePlan(list(shifts), bounds, counts, ks, lam_min, lam_max)
+
+
+def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, first_iters: int = 80,
+                iters_per_round: int = 3, max_rounds: int = 30) -> SliceOutcome:
+    """One slice solve (the unit of the benchmark): factor A - sigma_j B, its inertia,
+    the shift-invert probe of window j (Alg. 2) until as many Ritz pairs as the window's
+    exact count meet the residual tolerance, then validation (Section 2.2): the window's
+    converged count equals its inertia count, and the converged values below sigma_j
+    number n_neg(sigma_j) - nu(lower bound).  A probe still short after a round restarts
+    from its Ritz vectors; every 4th restart widens its basis by half (at least 16
+    columns); a mixed-precision probe whose residuals stall for 3 rounds moves to an FP64
+    factor of its shift.  Extra converged candidates (case 3) keep the smallest
+    residuals."""
+    sym, n = solver.sym, solver.sym.n
+    lo, hi = plan.window(j)
+    exact = plan.exact(j)
+    sigma = plan.shifts[j]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    f = sym.factor(solver.a, solver.b, [sigma], solver.precision)
+    ev1.record()
+    neg = f.inertia(0)[0]
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    kk = plan.ks[j]
+    V0 = torch.randn(n, kk, generator=g, device="cuda", dtype=torch.float64)
+    pr = f.slice_solve(0, lo, hi, V0, tol=solver.tol, max_iter=first_iters, refine=solver.refine,
+                       n_expect=max(1, exact), allow_noconv=True, check_every=3)
+    iters, rounds = pr.iterations, 1
+    f64, best, stall = None, np.inf, 0
+
+    def n_conv(q):
+        return int(np.sum((q.theta > lo) & (q.theta <= hi) & (q.resid <= solver.tol)))
+
+    while n_conv(pr) < exact and rounds < max_rounds:
+        rounds += 1
+        X = pr.X
+        if rounds % 4 == 0 and X.shape[1] < min(n, 4096):
+            extra = min(min(n, 4096) - X.shape[1], max(16, X.shape[1] // 2))
+            X = torch.cat([X, torch.randn(n, extra, generator=g, device="cuda", dtype=torch.float64)],
+                          dim=1).contiguous()
+        if solver.precision == "mixed" and f64 is None and f.quality(0)[0] != "fp64":
+            inw = (pr.theta > lo) & (pr.theta <= hi)
+            r = float(np.sort(pr.resid[inw])[-1]) if inw.any() else np.inf
+            stall = stall + 1 if not (r < 0.5 * best) else 0
+            best = min(best, r)
+            if stall >= 3:
+                f64 = sym.factor(solver.a, solver.b, [sigma], "fp64")
+        fj = f64 if f64 is not None else f
+        pr = fj.slice_solve(0, lo, hi, X, tol=solver.tol, max_iter=iters_per_round, refine=solver.refine,
+                            n_expect=max(1, exact), allow_noconv=True, refine_from_start=True,
+                            check_every=iters_per_round)
+        iters += pr.iterations
+    torch.cuda.synchronize()
+    factor_s = ev0.elapsed_time(ev1) / 1e3
+    quality = "fp64" if f64 is not None else f.quality(0)[0]
+    inw = (pr.theta > lo) & (pr.theta <= hi) & (pr.resid <= solver.tol)
+    idx = np.nonzero(inw)[0]
+    if idx.size > exact:                      # case 3: keep the smallest residuals
+        idx = np.sort(idx[np.argsort(pr.resid[idx], kind="stable")[:exact]])
+    theta = pr.theta[idx]
+    ok = idx.size == exact and int(np.sum(theta < sigma)) == neg - plan.counts[j]
+    X = pr.X[:, torch.as_tensor(idx, device=pr.X.device)] if idx.size else pr.X[:, :0]
+    f.close()
+    if f64 is not None:
+        f64.close()
+    return SliceOutcome(j, sigma, theta, X, pr.resid[idx], exact, neg, bool(ok), factor_s, iters, rounds, quality)
 
 
 def v0_never(X) -> int:

@@ -127,3 +127,29 @@ def test_eta_monitor_trace_form(gpu_lib):
     eta = trace_form(sym, a, Xd)
     assert abs(eta - float(np.trace(X[:, :86].T @ p.dense("a") @ X[:, :86]))) <= 1e-10 * abs(eta)
     assert abs(eta - float(lam[:86].sum())) <= 1e-9 * max(1.0, abs(eta))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_config1_slice_at_a_time(gpu_lib, precision):
+    """plan_slices + solve_slice (the benchmark's unit of work): every window's eigenpairs
+    against the dense oracle -- membership exact, eigenvalues to 1e-10, residuals by the
+    oracle's SpMV, the window's validation flag."""
+    from paper_1908_06043_gb300.driver import DosModel, SliceSolver, plan_slices, solve_slice
+    p = config_pencil(1)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    lam, _ = dense.gen_eig(p.dense("a"), p.dense("b"), vectors=False)
+    start = torch.tensor(normal_block(p.n, 4, 1000), device="cuda")
+    model = DosModel(p.n, sym.dos_estimate(a, b, 100, start))
+    solver = SliceSolver(sym, a, b, precision=precision)
+    plan = plan_slices(solver, model, 86, 4)
+    assert plan.counts == [spectral.count_below(lam, x) for x in plan.bounds]
+    assert plan.counts[0] == 0
+    for j in range(4):
+        o = solve_slice(solver, plan, j, seed=j)
+        lo, hi = plan.window(j)
+        ref = lam[spectral.slice_members(lam, lo, hi)]
+        assert o.ok and o.n_exact == ref.size == o.theta.size
+        assert o.n_neg_sigma == spectral.count_below(lam, plan.shifts[j])
+        assert np.all(np.abs(o.theta - ref) <= 1e-10 * np.maximum(np.abs(ref), 1.0))
+        r = spectral.residual_norms(p, o.theta, o.X.cpu().numpy())
+        assert r.max() <= 1e-10
