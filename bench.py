@@ -37,6 +37,8 @@ WORKLOADS = {
                     name="gaussian-s 16x16x16 lattice, 4 fn/atom, N=16384, n_e=1640, 16 shifts"),
     "gauss6": dict(config=1, n_e=86, n_s=4,
                    name="gaussian-s 6x6x6 lattice, 4 fn/atom, N=864, n_e=86, 4 shifts"),
+    "gauss24": dict(config=3, n_e=11059, n_s=64,
+                    name="gaussian-s 24x24x24 lattice, 8 fn/atom, N=110592, n_e=11059, 64 shifts"),
 }
 DEFAULT_WORKLOAD = "gauss16"
 METRIC = "slice solves/s at N=110,592 (mixed vs FP64, resid<=1e-10); factor TFLOP/s"
@@ -54,6 +56,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side steps")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end pass (default: --steps)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--verbose", action="store_true")
     ap.add_argument("--sequence", type=int, default=0,
@@ -375,7 +378,8 @@ def main():
         barrier(ws)
         t0 = time.perf_counter()
         d2h, ok2 = 0, 0
-        for s in range(args.steps):
+        n2 = args.e2e_steps if args.e2e_steps > 0 else args.steps
+        for s in range(n2):
             a.copy_(ha, non_blocking=True)
             b.copy_(hb, non_blocking=True)
             o = solve_slice(solver, plan, s % n_s, seed=300 + s)
@@ -385,8 +389,8 @@ def main():
             ok2 += int(o.ok)
         torch.cuda.synchronize()
         e2e = {"value": replica_rate(ws, ok2, time.perf_counter() - t0), "unit": "slice solves/s",
-               "h2d_bytes_per_step": int(2 * p.nnz * 8), "d2h_bytes_per_step": int(d2h // args.steps),
-               "validated_steps": ok2}
+               "h2d_bytes_per_step": int(2 * p.nnz * 8), "d2h_bytes_per_step": int(d2h // n2),
+               "steps": n2, "validated_steps": ok2}
 
     # the plain FP64 path on a spread of the same windows, against the mixed steps that
     # solved those windows in the timed loop

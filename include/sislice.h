@@ -285,8 +285,10 @@ ss_status ss_solve_noalloc(ss_numeric *f, int32_t shift_idx, const double *R, in
  * count from inertia), or every Ritz value in (lo, hi] is (n_expect = 0), or max_iter.
  * Unconverged Ritz values inside the window can be spurious mixtures of eigenvectors
  * at equal distance on both sides of sigma; validation (Section 2.2) discards them.
- * Outputs (k_out entries; k_out = k for SS_SUBSPACE): lambda (HOST float64, ascending
- * Ritz values), X (DEVICE N x k_out, B-orthonormal Ritz vectors in the same order),
+ * Outputs (k_out entries; k_out = k for SS_SUBSPACE): lambda (HOST float64: the Rayleigh
+ * quotients x^T A x / x^T B x of the returned vectors, summed and divided in double-double,
+ * in the ascending order of the Ritz values), X (DEVICE N x k_out, B-orthonormal Ritz
+ * vectors in the same order),
  * resid (HOST float64), n_found (HOST: #converged Ritz values in (lo, hi]), stats
  * (HOST, may be NULL).
  * Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_NOCONV (outputs still valid). */

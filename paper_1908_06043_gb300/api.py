@@ -356,13 +356,17 @@ def band_energy_grad(sym: Symbolic, X: torch.Tensor, lam: torch.Tensor):
 class BandEnergy(torch.autograd.Function):
     """E = sum of the n_e eigenvalues returned by ``solver(a_vals, b_vals)``.
 
-    ``solver`` returns (lam [n_e] CUDA float64, X [N, n_e] B-orthonormal).  The backward
-    pass is the SDDMM kernel of ``band_energy_grad`` (Hellmann-Feynman): dE/dA sampled
-    on the pattern is X X^T, dE/dB is -X Lambda X^T."""
+    ``solver`` returns (lam [n_e] CUDA float64, X [N, n_e] B-orthonormal) or (lam, X,
+    differentiable).  The backward pass is the SDDMM kernel of ``band_energy_grad``
+    (Hellmann-Feynman): dE/dA sampled on the pattern is X X^T, dE/dB is -X Lambda X^T.
+    When the solver reports E as not differentiable (lambda_(n_e+1) too close to
+    lambda_(n_e)), both gradients are NaN."""
 
     @staticmethod
     def forward(ctx, a_vals, b_vals, sym, solver):
-        lam, X = solver(a_vals, b_vals)
+        out = solver(a_vals.detach(), b_vals.detach())
+        lam, X = out[0], out[1]
+        ctx.differentiable = bool(out[2]) if len(out) > 2 else True
         ctx.sym = sym
         ctx.save_for_backward(X, lam)
         return lam.sum()
@@ -371,4 +375,6 @@ class BandEnergy(torch.autograd.Function):
     def backward(ctx, g):
         X, lam = ctx.saved_tensors
         ga, gb = band_energy_grad(ctx.sym, X.contiguous(), lam)
+        if not ctx.differentiable:
+            ga, gb = torch.full_like(ga, float("nan")), torch.full_like(gb, float("nan"))
         return g * ga, g * gb, None, None

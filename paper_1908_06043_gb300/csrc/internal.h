@@ -19,7 +19,7 @@ struct ss_ctx {
     int sm_count = 0;
     std::string err;
     int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
-    int schur_mode = SS_SCHUR_SIMT;           // FP64 Schur update: tensor cores or CUDA cores
+    int schur_mode = SS_SCHUR_TENSOR;         // FP64 Schur update: tensor cores or CUDA cores
     double tc_min_flops = 2.0e7;              // a factor step's Schur flops below which it stays on CUDA cores
     GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
     int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)

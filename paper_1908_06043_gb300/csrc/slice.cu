@@ -14,6 +14,7 @@
 
 #include "dense_kernels.cuh"
 #include "internal.h"
+#include "rq_kernels.cuh"
 
 namespace {
 
@@ -249,6 +250,29 @@ int cholqr_track(ss_numeric *f, double *&W, double *&BW, double *&Wt, double *&B
     return SS_OK;
 }
 
+// Rayleigh quotients x^T A x / x^T B x of the k columns of X (N x k), summed and divided
+// in double-double: the eigenvalue estimates a probe returns.  A Rayleigh-Ritz value
+// carries the rounding of forming W^T A W, about u ||A|| ||x||_2^2 -- up to 2e-9 on the
+// low tail of the Gaussian pencils, whose B-normalised eigenvectors have ||x||_2 of
+// hundreds -- while the quotient of the Ritz vector is second-order in the vector's error.
+int rq_polish(ss_numeric *f, const double *X, int k, double *theta_d, DevBuf &buf) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    const int64_t n = s->n;
+    const int nby = (int)cdiv(k, 128);
+    const int64_t nbx = std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 32), cdiv(8ll * ctx->sm_count, nby)));
+    const int64_t rows_per = (n + nbx - 1) / nbx;
+    const int64_t nparts = (n + rows_per - 1) / rows_per;
+    double *part;
+    TRY_ALLOC(ctx, buf.get(&part, (size_t)nparts * k * 4));
+    ss_launch(ctx, SS_K_MISC, sss::k_rq_dd_partial, dim3((unsigned)nparts, nby), 128, 0, ctx->stream, n, s->d_rowptr,
+              s->d_colind, f->a_vals, f->b_vals, X, k, rows_per, part);
+    ss_launch(ctx, SS_K_MISC, sss::k_rq_dd_finish, cdiv(k, 256), 256, 0, ctx->stream, k, (int)nparts,
+              (const double *)part, theta_d);
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
 // Alg. 2 with a Rayleigh-Ritz step every check_every iterations.  Per iteration: one
 // solve (A - sigma B) W = B V, one SpMM for B W, Cholesky-QR2 in the B inner product
 // carrying B W, and at a check one SpMM for A W, H = W^T A W = Q Theta Q^T, X = W Q with
@@ -373,8 +397,12 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
             near_conv = near_conv || rt <= 1e-6 || stalled;
         }
     }
-    (void)have_rr;
     (void)maxr_all;
+    // the returned eigenvalues: double-double Rayleigh quotients of the Ritz vectors
+    if (have_rr) {
+        if ((rc = rq_polish(f, V, k, theta_d, buf)) != SS_OK) return rc;
+        SS_CUDA_TRY(ctx, cudaMemcpyAsync(th.data(), theta_d, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    }
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(X, V, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     std::memcpy(lambda, th.data(), sizeof(double) * k);
@@ -492,6 +520,9 @@ int block_lanczos_impl(ss_numeric *f, int j, double lo, double hi, const ss_solv
     ss_launch(ctx, SS_K_MISC, ssd::k_resid_finish, cdiv(kout, 256), 256, 0, st, kout, (const double *)rr,
               (const double *)(rr + kout), f->norm_a1, resid_d);
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(resid, resid_d, sizeof(double) * kout, cudaMemcpyDeviceToHost, st));
+    // the returned eigenvalues: double-double Rayleigh quotients of the Ritz vectors
+    if ((rc = rq_polish(f, X, kout, theta_d, buf)) != SS_OK) return rc;
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(ths.data(), theta_d, sizeof(double) * kout, cudaMemcpyDeviceToHost, st));
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     std::memcpy(lambda, ths.data(), sizeof(double) * kout);
     int nf = 0;

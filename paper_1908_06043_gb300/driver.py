@@ -678,7 +678,7 @@ def plan_slices(solver: "SliceSolver", model: "DosModel", n_e: int, n_s: int, mo
 
 
 def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, first_iters: int = 80,
-                iters_per_round: int = 3, max_rounds: int = 30) -> SliceOutcome:
+                iters_per_round: int = 3, max_rounds: int = 30, V0: torch.Tensor = None) -> SliceOutcome:
     """One slice solve (the unit of the benchmark): factor A - sigma_j B, its inertia,
     the shift-invert probe of window j (Alg. 2) until as many Ritz pairs as the window's
     exact count meet the residual tolerance, then validation (Section 2.2): the window's
@@ -687,7 +687,8 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
     from its Ritz vectors; every 4th restart widens its basis by half (at least 16
     columns); a mixed-precision probe whose residuals stall for 3 rounds moves to an FP64
     factor of its shift.  Extra converged candidates (case 3) keep the smallest
-    residuals."""
+    residuals.  V0 (N x c, optional) warm-starts the probe, e.g. with the window's
+    eigenvectors of a nearby pencil; N(0,1) columns fill it up to the planned width."""
     sym, n = solver.sym, solver.sym.n
     lo, hi = plan.window(j)
     exact = plan.exact(j)
@@ -699,9 +700,15 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
     neg = f.inertia(0)[0]
     g = torch.Generator(device="cuda").manual_seed(seed)
     kk = plan.ks[j]
-    V0 = torch.randn(n, kk, generator=g, device="cuda", dtype=torch.float64)
+    warm = V0 is not None
+    if warm:
+        extra = max(0, kk - V0.shape[1])
+        V0 = torch.cat([V0, torch.randn(n, extra, generator=g, device="cuda", dtype=torch.float64)],
+                       dim=1).contiguous() if extra else V0.contiguous()
+    else:
+        V0 = torch.randn(n, kk, generator=g, device="cuda", dtype=torch.float64)
     pr = f.slice_solve(0, lo, hi, V0, tol=solver.tol, max_iter=first_iters, refine=solver.refine,
-                       n_expect=max(1, exact), allow_noconv=True, check_every=3)
+                       n_expect=max(1, exact), allow_noconv=True, check_every=3, refine_from_start=warm)
     iters, rounds = pr.iterations, 1
     f64, best, stall = None, np.inf, 0
 
@@ -741,6 +748,31 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
     if f64 is not None:
         f64.close()
     return SliceOutcome(j, sigma, theta, X, pr.resid[idx], exact, neg, bool(ok), factor_s, iters, rounds, quality)
+
+
+def solve_plan(solver: "SliceSolver", plan: SlicePlan, seed: int = 0, warm=None, first_iters: int = 80):
+    """Every window of the plan (solve_slice), optionally warm-started from a list of
+    per-window start blocks.  Returns (eigenvalues ascending, eigenvectors N x n_e as a
+    CUDA tensor, outcomes); raises if a window does not validate."""
+    outs = []
+    for j in range(len(plan.shifts)):
+        o = solve_slice(solver, plan, j, seed=seed + j, first_iters=first_iters,
+                        V0=None if warm is None else warm[j])
+        if not o.ok:
+            raise RuntimeError(f"window {j} did not validate ({o.theta.size} of {o.n_exact})")
+        outs.append(o)
+    lam = np.concatenate([o.theta for o in outs])
+    X = torch.cat([o.X for o in outs], dim=1)
+    order = np.argsort(lam, kind="stable")
+    return lam[order], X[:, torch.as_tensor(order, device=X.device)].contiguous(), outs
+
+
+def energy_differentiable(solver: "SliceSolver", lam: np.ndarray, gap: float = 1e-8) -> bool:
+    """The band energy E = sum of the n_e lowest eigenvalues is differentiable when
+    lambda_(n_e+1) - lambda_(n_e) >= gap: Sylvester's inertia at lambda_(n_e) + gap must
+    still count n_e eigenvalues below it."""
+    n_e = int(np.asarray(lam).size)
+    return solver.count_below([float(np.max(lam)) + gap])[0] == n_e
 
 
 def v0_never(X) -> int:
