@@ -61,7 +61,9 @@ __global__ void k_assemble(int64_t count, const int32_t *__restrict__ asm_e,
 }
 
 // ---------------------------------------------------------------- extend-add
-// One block per contribution column: parent[rel[i], rel[j]] += cb[i, j], i >= j.
+// One block per contribution column: parent[rel[i], rel[j]] += cb[i, j], i >= j.  A block
+// in the pool is its lower triangle packed by columns: column j (rows j .. nr-1) starts
+// at j (2 nr - j + 1) / 2.
 template <typename T>
 __global__ void k_extend_add(const ExtendTask *__restrict__ tasks, int32_t ntask,
                              const int32_t *__restrict__ relmap, const ShiftPtrs<T> *sp) {
@@ -76,14 +78,14 @@ __global__ void k_extend_add(const ExtendTask *__restrict__ tasks, int32_t ntask
     const int32_t j = col - t.col_pre;
     const int32_t nr = t.child_m - t.child_ncol;
     const int32_t *rel = relmap + t.rel_off;
-    const T *cc = s.cb + t.child_off + (int64_t)(t.child_ncol + j) * t.child_m + t.child_ncol;
+    const T *cc = s.cb + t.child_off + (int64_t)j * (2 * (int64_t)nr - j - 1) / 2;   // cc[i]: row i >= j
     T *pc = s.ws + t.parent_off + (int64_t)rel[j] * t.parent_m;
     for (int32_t i = j + threadIdx.x; i < nr; i += blockDim.x) pc[rel[i]] += cc[i];
 }
 
 // ---------------------------------------------------------------- store
 // One block per front column of a level: column c < ncol to L storage (all m rows),
-// column ncol + j to the contribution-block pool (rows j .. nr-1, leading dimension nr).
+// column ncol + j to the contribution-block pool (rows j .. nr-1, packed lower triangle).
 template <typename T>
 __global__ void k_level_store(const StoreTask *__restrict__ tasks, int32_t ntask, const ShiftPtrs<T> *sp) {
     const ShiftPtrs<T> s = sp[blockIdx.y];
@@ -102,7 +104,7 @@ __global__ void k_level_store(const StoreTask *__restrict__ tasks, int32_t ntask
         for (int32_t i = threadIdx.x; i < t.m; i += blockDim.x) dst[i] = src[i];
     } else {
         const int32_t j = c - t.ncol, nr = t.m - t.ncol;
-        T *dst = s.cb + t.cb_off + (int64_t)j * nr;
+        T *dst = s.cb + t.cb_off + (int64_t)j * (2 * (int64_t)nr - j - 1) / 2;    // dst[i]: row i >= j
         src += t.ncol;
         for (int32_t i = j + threadIdx.x; i < nr; i += blockDim.x) dst[i] = src[i];
     }

@@ -110,9 +110,9 @@ struct StepDesc {
     int64_t sl_bytes, ex_count;   // slice scratch bytes and row exponents of the step
 };
 
-// Child -> parent extend-add unit: the child's contribution block (pool, leading
-// dimension child_m = its nr, child_ncol = 0) added into the parent front (workspace)
-// through relmap.
+// Child -> parent extend-add unit: the child's contribution block (pool, packed lower
+// triangle of order child_m = its nr; child_ncol = 0) added into the parent front
+// (workspace) through relmap.
 struct ExtendTask {
     int64_t child_off, parent_off;
     int64_t rel_off;     // into relmap (length nr)
@@ -121,7 +121,8 @@ struct ExtendTask {
 
 // After a level is factored: copy front columns of one supernode out of the workspace.
 // Column c < ncol goes to L storage (the whole column, m entries); column ncol + j (the
-// contribution block) goes to the pool, rows j .. nr-1 (nr = m - ncol, leading dim nr).
+// contribution block) goes to the pool, rows j .. nr-1 (nr = m - ncol), packed lower
+// triangle: column j starts at j (2 nr - j + 1) / 2.
 struct StoreTask {
     int64_t ws_off, l_off, cb_off;   // cb_off < 0: no contribution block (a root)
     int32_t m, ncol, col_pre, pad;   // col_pre: exclusive prefix of columns in the level

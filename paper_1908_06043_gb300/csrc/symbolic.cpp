@@ -301,10 +301,11 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
     // block (nr = m - ncol) of each of its fronts is stored in the pool until the parent's
     // extend-add reads it; the pool addresses are planned here by first fit over the
     // blocks' lifetimes (stored at the end of the child's level, dead once the parent's
-    // level has started).
+    // level has started).  Blocks are stored as packed lower triangles.
     std::vector<std::vector<int32_t>> lev_sn(nlev);
     for (int32_t b = 0; b < nsn; ++b) lev_sn[s->sn_level[b]].push_back(b);
     auto al32 = [](int64_t x) { return (x + 31) / 32 * 32; };      // 256-byte aligned blocks
+    auto tri = [](int64_t r) { return r * (r + 1) / 2; };          // packed lower triangle
     s->front_off.assign(nsn, 0);
     s->l_off.assign(nsn, 0);
     s->cb_off.assign(nsn, -1);
@@ -339,11 +340,11 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
         for (int32_t l = 0; l < nlev; ++l) {
             for (int32_t p : lev_sn[l])
                 for (int32_t c : children[p])
-                    if (s->cb_off[c] >= 0) release(s->cb_off[c], al32((int64_t)s->sn_nrow[c] * s->sn_nrow[c]));
+                    if (s->cb_off[c] >= 0) release(s->cb_off[c], al32(tri((int64_t)s->sn_nrow[c])));
             for (int32_t b : lev_sn[l]) {
                 const int64_t nr = s->sn_nrow[b];
                 if (nr == 0) continue;
-                const int64_t need = al32(nr * nr);
+                const int64_t need = al32(tri(nr));
                 auto it = hole.begin();
                 while (it != hole.end() && it->second < need) ++it;
                 if (it != hole.end()) {
@@ -683,7 +684,7 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
         if (s->l_off[b] < 0 || s->l_off[b] + m * ncol > s->l_total) return fail("L block outside L storage");
         const int64_t nr = s->sn_nrow[b];
         if ((nr > 0) != (s->cb_off[b] >= 0)) return fail("contribution block without a pool slot (or vice versa)");
-        if (nr > 0 && (s->cb_off[b] % 32 || s->cb_off[b] + nr * nr > s->cb_total))
+        if (nr > 0 && (s->cb_off[b] % 32 || s->cb_off[b] + nr * (nr + 1) / 2 > s->cb_total))
             return fail("contribution block outside the pool");
         const int32_t p = s->sn_parent[b];
         if (p >= 0 && (p <= b || s->sn_level[p] <= lev)) return fail("parent not after child");
@@ -718,7 +719,7 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
         std::vector<Live> lv;
         for (int32_t b = 0; b < nsn; ++b)
             if (s->cb_off[b] >= 0)
-                lv.push_back({s->cb_off[b], s->cb_off[b] + (int64_t)s->sn_nrow[b] * s->sn_nrow[b], s->sn_level[b],
+                lv.push_back({s->cb_off[b], s->cb_off[b] + (int64_t)s->sn_nrow[b] * (s->sn_nrow[b] + 1) / 2, s->sn_level[b],
                               s->sn_level[s->sn_parent[b]]});
         std::sort(lv.begin(), lv.end(), [](const Live &x, const Live &y) { return x.a < y.a; });
         for (size_t i = 0; i < lv.size(); ++i)
@@ -739,7 +740,7 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
             if (t.ws_off + (int64_t)t.m * t.m > s->lev_ws[l]) return fail("store source outside the workspace");
             if (t.l_off + (int64_t)t.m * t.ncol > s->l_total) return fail("store L destination out of range");
             const int64_t nr = t.m - t.ncol;
-            if (nr > 0 && (t.cb_off < 0 || t.cb_off + nr * nr > s->cb_total)) return fail("store pool destination");
+            if (nr > 0 && (t.cb_off < 0 || t.cb_off + nr * (nr + 1) / 2 > s->cb_total)) return fail("store pool destination");
         }
         if (cols != s->lev_store_cols[l]) return fail("store column total");
     }
@@ -784,7 +785,7 @@ static int validate_impl(const ss_symbolic *s, std::string &why) {
                 if (v < 0 || v >= et.parent_m) return fail("relmap entry outside the parent front");
                 if (r > 0 && v <= s->relmap[et.rel_off + r - 1]) return fail("relmap not increasing");
             }
-            if (et.child_ncol != 0 || et.child_off < 0 || et.child_off + (int64_t)et.child_m * et.child_m > s->cb_total)
+            if (et.child_ncol != 0 || et.child_off < 0 || et.child_off + (int64_t)et.child_m * (et.child_m + 1) / 2 > s->cb_total)
                 return fail("extend-add source outside the contribution-block pool");
             if (et.parent_off < 0 || et.parent_off + (int64_t)et.parent_m * et.parent_m > s->ws_total)
                 return fail("extend-add destination outside the workspace");

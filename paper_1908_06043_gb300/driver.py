@@ -889,6 +889,35 @@ def migrated_windows(values, groups, lam_min: float, lam_max: float):
     return splits, ks
 
 
+class SpectrumCount:
+    """The count function Phi(w) = #{previous eigenvalues < w} of a validated spectrum, in
+    the interface of DosModel (Phi returns an array), for placing the probes of the next
+    pencil.  Above the last value the count is continued with the mean spacing of the top
+    tenth of the spectrum."""
+
+    def __init__(self, values):
+        self.x = np.sort(np.asarray(values, dtype=np.float64))
+        top = self.x[-max(2, self.x.size // 10):]
+        self.spacing = max(float(np.mean(np.diff(top))), 1e-12) if top.size > 1 else 1.0
+
+    def Phi(self, w):
+        w = np.atleast_1d(np.asarray(w, dtype=np.float64))
+        c = np.searchsorted(self.x, w, side="left").astype(np.float64)
+        above = w > self.x[-1]
+        c[above] = self.x.size + (w[above] - self.x[-1]) / self.spacing
+        return c
+
+
+def ball_windows_from_spectrum(values, lam_min: float, lam_max: float, n_s: int):
+    """Ball placement (ball_partition) on the previous pencil's validated eigenvalues:
+    (shifts, splits, basis widths), the widths as in place_shifts."""
+    model = SpectrumCount(values)
+    iv, shifts, balls = ball_partition(model, lam_min, lam_max, n_s)
+    splits = [None] + [iv[j][0] for j in range(1, n_s)]
+    ks = [min(4096, _ceil16(1.15 * bc + 16)) for bc in balls]
+    return shifts, splits, ks
+
+
 def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precision: str = "mixed",
                    tol: float = 1e-10, lanczos_steps: int = 100, n_vec: int = 4, seed: int = 0,
                    start=None, uniforms=None, eta_tol: float = np.inf, balance: float = 2.0):
@@ -905,7 +934,11 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
     Tr(X^T A X) over the previous eigenvectors (Eq. 9) above which a step is placed from a
     new DOS estimate instead of by migration (inf: never).  balance: a migrated probe with
     more than balance x the mean number of eigenvalues gets an inserted neighbour (None:
-    only deleted probes are replaced).  Returns one SliceResult per
+    only deleted probes are replaced).  When the migrated windows would need more than
+    twice the total basis of a ball placement on the previous step's eigenvalues (k-means
+    on a tail-heavy spectrum leaves wide clusters in the dense part), the step is placed by
+    that ball placement instead, each probe warm-started from the previous eigenvectors
+    in its window.  Returns one SliceResult per
     pencil; timings["migration"] records the shifts and cluster sizes chosen and
     timings["eta"] the monitor's (old, new, changed)."""
     n = sym.n
@@ -949,6 +982,14 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
             groups = _inside_region(migrated, lam_min, lam_max)
             shifts = [s_ for s_, _ in groups]
             splits, ks = migrated_windows(prev.eigenvalues, groups, lam_min, lam_max)
+            b_shifts, b_splits, b_ks = ball_windows_from_spectrum(prev.eigenvalues, lam_min, lam_max, n_s)
+            fallback = sum(ks) > 2 * sum(b_ks)
+            if fallback:
+                shifts, splits, ks = b_shifts, b_splits, b_ks
+                bounds = [lam_min] + [splits[j] for j in range(1, len(shifts))] + [lam_max]
+                ev = np.asarray(prev.eigenvalues)
+                groups = [(shifts[j], [int(i) for i in np.flatnonzero((ev > bounds[j]) & (ev <= bounds[j + 1]))])
+                          for j in range(len(shifts))]
             V0 = []
             for (_, m), kk in zip(groups, ks):
                 kk = min(n, max(kk, len(m) + 16))
@@ -958,7 +999,8 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
                                            seed=seed + i, warm=True)
             res.timings["migration"] = dict(shifts=[s_ for s_, _ in migrated], sizes=[len(m) for _, m in migrated],
                                             init="kmeans++" if after_dos else "previous shifts",
-                                            shifts_used=shifts, balance=balance)
+                                            shifts_used=shifts, balance=balance,
+                                            ball_fallback=bool(fallback))
         res.timings["eta"] = etas[-1] if i > 0 else None
         results.append(res)
     return results

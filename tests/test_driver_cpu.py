@@ -175,3 +175,28 @@ def test_recovery_inserts_probes_in_deficient_slices():
     assert res.timings["converged"] and res.timings["inserted"] == [[0.5]]
     assert calls[1][0] == [0.0, 0.5, 1.0, 2.0]
     assert calls[1][1] == ["X0", None, "X1", "X2"]
+
+
+def test_ball_windows_from_previous_spectrum():
+    """Migration fallback: the ball placement on a validated spectrum gives n_s shifts
+    inside [lambda_min, lambda_max], increasing splits strictly between neighbouring
+    shifts, and on a uniform spectrum equal interior windows (the end windows' balls reach
+    past the spectrum, where it counts fewer eigenvalues, so those windows may differ)."""
+    from paper_1908_06043_gb300.driver import SpectrumCount, ball_windows_from_spectrum
+    v = np.linspace(0.0, 1.0, 401)
+    sh, sp, ks = ball_windows_from_spectrum(v, -0.00125, 1.00125, 8)
+    assert len(sh) == 8 and len(sp) == 8 and sp[0] is None
+    w = np.diff([-0.00125] + sp[1:] + [1.00125])
+    assert np.allclose(w[1:-1], w[1:-1].mean(), rtol=0.05)
+    assert all(sh[j - 1] < sp[j] < sh[j] for j in range(1, 8))
+    # the count function: exact below the last value, linear continuation above it
+    m = SpectrumCount(v)
+    assert m.Phi(0.5)[0] == 200 and m.Phi(-1.0)[0] == 0
+    assert abs(m.Phi(1.0 + 10 * 0.0025)[0] - 411) < 1e-9
+    # a tail-heavy spectrum: the sparse tail gets the wide windows, the body narrow ones
+    t = np.concatenate([np.linspace(-45, -10, 37), np.linspace(-8, 0.3, 1600)])
+    sh, sp, ks = ball_windows_from_spectrum(t, -46.0, 0.31, 16)
+    b = [-46.0] + sp[1:] + [0.31]
+    counts = [int(np.sum((t > b[j]) & (t <= b[j + 1]))) for j in range(16)]
+    assert sum(counts) == t.size
+    assert max(ks) <= 4096 and min(counts[2:]) > 0
