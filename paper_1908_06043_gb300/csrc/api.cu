@@ -414,7 +414,8 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
                 if (sd.tiles3 > 0 && tc && sd.tc_tiles > 0 && sd.flops3 >= ctx->tc_min_flops) {
                     ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_slice, dim3(sd.sl_tiles, ns), 128, 0, st, tk, sd.count,
                               (const ShiftPtrs<double> *)dp);
-                    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_schur_tc, dim3(sd.tc_tiles, ns), 128, sstc::kSchurTcSmem,
+                    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_schur_tc, dim3(sd.tc_tiles, ns), sstc::kSchurTcThreads,
+                              sstc::kSchurTcSmem,
                               st, tk, sd.count, (const ShiftPtrs<double> *)dp);
                     ctx->add_flops(SS_K_SCHUR_TC, sd.flops3 * ns);
                 } else if (sd.tiles3 > 0) {

@@ -14,8 +14,12 @@
 // below 7 * 64 * 128^2 < 2^23, so the FP32 accumulation is exact.
 // Combination.  With a_d the accumulator of p + q = d + 2 (d = 0..6), the update is
 //   2^(e_i + f_j - 62) (hi 2^32 + lo),  hi = a_0 2^16 + a_1 2^8 + a_2,
-//   lo = a_3 2^24 + a_4 2^16 + a_5 2^8 + a_6,
-// formed in 64-bit integers (exact) and applied with two FP64 fused multiply-adds.
+//   lo = a_3 2^24 + a_4 2^16 + a_5 2^8 + a_6.
+// The accumulators are converted to 32-bit integers (the 64-bit conversions run at the FP64
+// rate on this GPU), hi and lo are formed in 64-bit integers (exact), and
+// v = hi 2^15 + floor(lo / 2^17) (below 2^54) is converted to FP64 once: the 17 dropped bits
+// are below the rounding unit of the largest possible product (2^68 in these units), so the
+// update keeps the accuracy of an FP64 product.  One FMA applies 2^(e_i + f_j - 45) v.
 //
 // Data flow per factor step: k_panel writes L21 (in place) and W (scratch) in FP64;
 // k_tc_slice writes their slices, already in the MMA's shared-memory layout (see
@@ -44,6 +48,7 @@ constexpr uint32_t kHalfSliceBytes = 64 * 64 * 2;           // its 64-row half
 constexpr int kAccum = kSlices;               // accumulators, one per p + q
 constexpr uint32_t kTmemCols = 512;           // 7 x 64 columns, rounded to a power of two
 constexpr size_t kSchurTcSmem = 1024 + (size_t)kSlices * kSliceBytes + (size_t)kSlices * kHalfSliceBytes;
+constexpr int kSchurTcThreads = 256;          // 8 warps: lane quarter w % 4, column half w / 4
 constexpr long long kWaitLimit = 1ll << 24;   // mbarrier polls (about a second)
 
 // ---------------------------------------------------------------- self-test
@@ -160,9 +165,11 @@ __global__ void __launch_bounds__(128) k_tc_slice(const StepTask *__restrict__ t
 
 // ---------------------------------------------------------------- Schur update
 // Block = one 128 x 64 tile (bi, bj) of the lower triangle of a task's trailing r x r
-// block; tiles of a task are numbered q = bi (bi + 1) + bj, bj <= 2 bi + 1.
-__global__ void __launch_bounds__(128, 1) k_schur_tc(const StepTask *__restrict__ tasks, int32_t ntask,
-                                                      const ssk::ShiftPtrs<double> *sp) {
+// block; tiles of a task are numbered q = bi (bi + 1) + bj, bj <= 2 bi + 1.  256 threads:
+// warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its rows) and columns 32 (w / 4)
+// .. + 31 of every accumulator.
+__global__ void __launch_bounds__(kSchurTcThreads, 1) k_schur_tc(const StepTask *__restrict__ tasks, int32_t ntask,
+                                                                  const ssk::ShiftPtrs<double> *sp) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sa = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     unsigned char *sb = sa + kSlices * kSliceBytes;
@@ -237,29 +244,38 @@ __global__ void __launch_bounds__(128, 1) k_schur_tc(const StepTask *__restrict_
     if (s_ok) {
         const int r = tk.r, m = tk.m;
         const int64_t base = tk.k0 + tk.w;
-        const int i = bi * kTileM + 32 * warp + lane;            // trailing row of this thread
+        const int quarter = warp & 3, half = warp >> 2;
+        const int i = bi * kTileM + 32 * quarter + lane;          // trailing row of this thread
         const int ei = i < r ? s.ex[tk.ex_off + i] : 0;
         double *F = s.ws + tk.front_off;
-        for (int c0 = 0; c0 < kTileN; c0 += 16) {
+        const int32_t *fex = s.ex + tk.ex_off + r;
+        for (int c0 = 32 * half; c0 < 32 * half + 32; c0 += 16) {
             float a[kAccum][16];
 #pragma unroll
             for (int d = 0; d < kAccum; ++d)
-                tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(d * kTileN + c0), a[d]);
+                tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(d * kTileN + c0), a[d]);
+            const int j0 = bj * kTileN + c0;
+            // this thread's 16 front entries, loaded before any is used
+            double cv[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
-                const int j = bj * kTileN + c0 + c;
-                if (i >= r || j >= r || j > i) continue;
-                const long long hi2 = (long long)__float2ll_rn(a[0][c]) * 65536ll +
-                                      (long long)__float2ll_rn(a[1][c]) * 256ll + (long long)__float2ll_rn(a[2][c]);
-                const long long lo2 = (long long)__float2ll_rn(a[3][c]) * 16777216ll +
-                                      (long long)__float2ll_rn(a[4][c]) * 65536ll +
-                                      (long long)__float2ll_rn(a[5][c]) * 256ll + (long long)__float2ll_rn(a[6][c]);
-                const double v = fma((double)hi2, 4294967296.0, (double)lo2);
-                const int E = ei + s.ex[tk.ex_off + r + j] - 62;
+                const int j = j0 + c;
+                cv[c] = (i < r && j <= i) ? F[(base + j) * (int64_t)m + base + i] : 0.0;
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int j = j0 + c;
+                if (i >= r || j > i) continue;
+                const long long h2 = ((long long)__float2int_rn(a[0][c]) << 16) +
+                                     ((long long)__float2int_rn(a[1][c]) << 8) + (long long)__float2int_rn(a[2][c]);
+                const long long l2 = ((long long)__float2int_rn(a[3][c]) << 24) +
+                                     ((long long)__float2int_rn(a[4][c]) << 16) +
+                                     ((long long)__float2int_rn(a[5][c]) << 8) + (long long)__float2int_rn(a[6][c]);
+                const long long v = (h2 << 15) + (l2 >> 17);            // |v| < 2^54
+                const int E = ei + fex[j] - 45;
                 const double sc = (E >= -1022 && E <= 1023) ? __longlong_as_double((long long)(E + 1023) << 52)
                                                             : ldexp(1.0, E);
-                double *cp = F + (base + j) * (int64_t)m + base + i;
-                *cp = fma(-v, sc, *cp);
+                F[(base + j) * (int64_t)m + base + i] = fma(-__ll2double_rn(v), sc, cv[c]);
             }
         }
     }
