@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "fp64"])
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end pass (default: --steps)")
@@ -395,7 +395,7 @@ def main():
     # the plain FP64 path on a spread of the same windows, against the mixed steps that
     # solved those windows in the timed loop
     fp64 = None
-    if not args.no_fp64_side and args.precision == "mixed" and rank == 0:
+    if not args.no_fp64_side and args.precision != "fp64" and rank == 0:
         m = min(args.steps, n_s, 8)
         js = sorted({int(round(i * (min(args.steps, n_s) - 1) / max(1, m - 1))) for i in range(m)})
         solver64 = SliceSolver(sym, a, b, precision="fp64")
@@ -442,7 +442,7 @@ def main():
         cpu = cpu_baseline(p, plan.shifts[n_s // 2])
     out = {"metric": METRIC, "value": value, "unit": "slice solves/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+           "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
            "data": "synthetic",
            "config": {"workload": wl["name"], "precision": args.precision,
                       "step": "one slice solve: LDL^T of A - sigma_j B, inertia, shift-invert subspace "

@@ -44,6 +44,7 @@ enum {
 };
 
 enum { SS_FP64 = 0, SS_MIXED = 1 };      /* factor precision                     */
+enum { SS_MIXED_TC = 3 };                  /* FP64 fronts, FP32 solves from the rounded factor */
 enum { SS_INERTIA_ONLY = 4 };              /* or-ed into the precision of ss_factor: FP64
                                               fronts, only the inertia is kept          */
 enum { SS_FP64_SOLVE32 = 2 };              /* reported only: FP64 factor, FP32 solves */
@@ -199,7 +200,11 @@ ss_status ss_symbolic_validate(const ss_symbolic *sym);
  * shift is refactored in FP64.  The FP64 factor of such a shift is then rounded once to
  * FP32; if one FP32 solve from the rounded copy contracts by rho <= 0.25, the shift's
  * solves run in FP32 inside FP64 refinement, else in FP64 (ss_factor_quality reports
- * which).  precision | SS_INERTIA_ONLY factors in FP64 and keeps no L (inertia,
+ * which).  precision = SS_MIXED_TC factors every shift with FP64 fronts (the Schur updates
+ * on the tensor cores, see ss_set_schur_mode) and rounds the factor once to FP32; where one
+ * FP32 solve from that copy contracts by rho <= 0.25 the shift's solves run in FP32 inside
+ * FP64 refinement, else in FP64 (no FP32 factorisation is attempted).
+ * precision | SS_INERTIA_ONLY factors in FP64 and keeps no L (inertia,
  * ss_factor_stats only; solves on such a factor return SS_ERR_ARG): the counts at many
  * shifts at a fraction of the memory.
  * Memory: each shift keeps its L storage (info.l_storage_entries); while it is factored

@@ -15,6 +15,7 @@ SS_OK, SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_SINGULAR, SS_ERR_NOT_SPD, SS_
     SS_ERR_TIMEOUT, SS_ERR_INTERNAL = range(9)
 SS_FP64, SS_MIXED, SS_FP64_SOLVE32 = 0, 1, 2
 SS_INERTIA_ONLY = 4
+SS_MIXED_TC = 3
 SS_SOLVE_SWEEP_KERNEL, SS_SOLVE_PER_STEP = 0, 1
 SS_SUBSPACE, SS_BLOCK_LANCZOS = 0, 1
 SS_PEAK_FP64_FMA, SS_PEAK_FP32_FMA = 0, 1

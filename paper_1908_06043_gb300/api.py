@@ -193,14 +193,17 @@ class Symbolic:
 def factor(sym: Symbolic, a_vals, b_vals, sigma, precision: str = "fp64",
            allow_singular: bool = False) -> "Factor":
     """LDL^T of A - sigma_j B for every shift (one factor per shift).  precision "fp64",
-    "mixed", or "inertia" (FP64 fronts, only the inertia kept: no solves)."""
+    "mixed" (FP32 fronts, refactored in FP64 where one FP32 solve does not contract),
+    "mixed_tc" (FP64 fronts on the tensor cores, FP32 solves from the factor rounded once
+    where they contract), or "inertia" (FP64 fronts, only the inertia kept: no solves)."""
     ctx = sym.ctx
     _dev(a_vals, "a_vals")
     _dev(b_vals, "b_vals")
     if a_vals.numel() != sym.nnz or b_vals.numel() != sym.nnz:
         raise ValueError("value arrays must match the analysed pattern")
     sig = np.ascontiguousarray(np.atleast_1d(np.asarray(sigma, dtype=np.float64)))
-    prec = {"fp64": L.SS_FP64, "mixed": L.SS_MIXED, "inertia": L.SS_FP64 | L.SS_INERTIA_ONLY}[precision]
+    prec = {"fp64": L.SS_FP64, "mixed": L.SS_MIXED, "mixed_tc": L.SS_MIXED_TC,
+            "inertia": L.SS_FP64 | L.SS_INERTIA_ONLY}[precision]
     h = C.c_void_p()
     rc = ctx.lib.ss_factor(sym.h, _ptr(a_vals), _ptr(b_vals), _ptr(sig), sig.size, prec, C.byref(h))
     ctx.check(rc, "ss_factor", allow=(L.SS_ERR_SINGULAR,) if allow_singular else ())

@@ -550,6 +550,33 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
                 f->arena_lo[j] = nullptr;
             }
         }
+    } else if (precision == SS_MIXED_TC) {
+        // FP64 fronts (tensor-core Schur updates), every shift's factor rounded once to
+        // FP32 for its solves where one FP32 solve contracts by rho <= kRoundedRhoMax
+        rc = factor_run<double>(f, all);
+        for (int j = 0; j < n_shift && rc == SS_OK; ++j) {
+            f->shift_prec[j] = SS_FP64;
+            const int64_t na = std::max<int64_t>(1, sym->l_total);
+            cudaError_t e2 = cudaMalloc((void **)&f->arena_lo[j], sizeof(float) * na);
+            if (e2 != cudaSuccess) {
+                cudaGetLastError();
+                f->arena_lo[j] = nullptr;
+                continue;                               // no room for the copy: FP64 solves
+            }
+            const unsigned g = (unsigned)std::min<int64_t>((na + 255) / 256, (int64_t)ctx->sm_count * 16);
+            ss_launch(ctx, SS_K_MISC, k_round_f32, g, 256, 0, ctx->stream, na, (const double *)f->arena[j],
+                      f->arena_lo[j]);
+            double rho_lo = INFINITY;
+            rc = solve_contraction(f, j, &rho_lo);
+            if (rc != SS_OK) break;
+            if (rho_lo <= kRoundedRhoMax) {
+                f->rho[j] = rho_lo;
+            } else {
+                SS_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+                cudaFree(f->arena_lo[j]);
+                f->arena_lo[j] = nullptr;
+            }
+        }
     } else {
         rc = factor_run<double>(f, all);
     }
@@ -590,7 +617,7 @@ extern "C" ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const dou
     if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "ss_factor: host-only context");
     const int32_t base_prec = precision & ~SS_INERTIA_ONLY;
     if (!out || !a_vals || !b_vals || !sigma || n_shift <= 0 || n_shift > 65535 ||
-        (base_prec != SS_FP64 && base_prec != SS_MIXED))
+        (base_prec != SS_FP64 && base_prec != SS_MIXED && base_prec != SS_MIXED_TC))
         return ctx->set_error(SS_ERR_ARG, "ss_factor: bad argument");
     for (int j = 0; j < n_shift; ++j)
         if (!std::isfinite(sigma[j])) return ctx->set_error(SS_ERR_ARG, "ss_factor: non-finite shift");

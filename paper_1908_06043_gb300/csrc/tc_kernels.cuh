@@ -16,10 +16,11 @@
 //   2^(e_i + f_j - 62) (hi 2^32 + lo),  hi = a_0 2^16 + a_1 2^8 + a_2,
 //   lo = a_3 2^24 + a_4 2^16 + a_5 2^8 + a_6.
 // The accumulators are converted to 32-bit integers (the 64-bit conversions run at the FP64
-// rate on this GPU), hi and lo are formed in 64-bit integers (exact), and
-// v = hi 2^15 + floor(lo / 2^17) (below 2^54) is converted to FP64 once: the 17 dropped bits
-// are below the rounding unit of the largest possible product (2^68 in these units), so the
-// update keeps the accuracy of an FP64 product.  One FMA applies 2^(e_i + f_j - 45) v.
+// rate on this GPU), hi and lo are formed in 64-bit integers (exact, below 2^40 and 2^49),
+// converted to FP64 (exact) and combined by one FMA, hi 2^32 + lo, rounded once; a second
+// FMA applies it to the front.  Every bit of lo is kept: dropping its low bits costs about
+// 2^-45 of a typical product per update, which the many updates of a front and the
+// conditioning of A - sigma B amplify past an FP64 factorisation's accuracy.
 //
 // Data flow per factor step: k_panel writes L21 (in place) and W (scratch) in FP64;
 // k_tc_slice writes their slices, already in the MMA's shared-memory layout (see
@@ -271,11 +272,11 @@ __global__ void __launch_bounds__(kSchurTcThreads, 1) k_schur_tc(const StepTask 
                 const long long l2 = ((long long)__float2int_rn(a[3][c]) << 24) +
                                      ((long long)__float2int_rn(a[4][c]) << 16) +
                                      ((long long)__float2int_rn(a[5][c]) << 8) + (long long)__float2int_rn(a[6][c]);
-                const long long v = (h2 << 15) + (l2 >> 17);            // |v| < 2^54
-                const int E = ei + fex[j] - 45;
+                const double v = fma(__ll2double_rn(h2), 4294967296.0, __ll2double_rn(l2));
+                const int E = ei + fex[j] - 62;
                 const double sc = (E >= -1022 && E <= 1023) ? __longlong_as_double((long long)(E + 1023) << 52)
                                                             : ldexp(1.0, E);
-                F[(base + j) * (int64_t)m + base + i] = fma(-__ll2double_rn(v), sc, cv[c]);
+                F[(base + j) * (int64_t)m + base + i] = fma(-v, sc, cv[c]);
             }
         }
     }

@@ -538,7 +538,7 @@ class SliceSolver:
             # a mixed-precision probe whose window residuals stop improving is moved to an
             # FP64 factor of its shift (the FP32 factor limits its accuracy)
             for j in active:
-                if self.precision != "mixed" or j in f64 or f.quality(j)[0] == "fp64":
+                if self.precision not in ("mixed", "mixed_tc") or j in f64 or f.quality(j)[0] == "fp64":
                     continue
                 lo, hi = windows[j]
                 pr = probes[j]
@@ -722,7 +722,7 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
             extra = min(min(n, 4096) - X.shape[1], max(16, X.shape[1] // 2))
             X = torch.cat([X, torch.randn(n, extra, generator=g, device="cuda", dtype=torch.float64)],
                           dim=1).contiguous()
-        if solver.precision == "mixed" and f64 is None and f.quality(0)[0] != "fp64":
+        if solver.precision in ("mixed", "mixed_tc") and f64 is None and f.quality(0)[0] != "fp64":
             inw = (pr.theta > lo) & (pr.theta <= hi)
             r = float(np.sort(pr.resid[inw])[-1]) if inw.any() else np.inf
             stall = stall + 1 if not (r < 0.5 * best) else 0

@@ -129,7 +129,7 @@ def test_eta_monitor_trace_form(gpu_lib):
     assert abs(eta - float(lam[:86].sum())) <= 1e-9 * max(1.0, abs(eta))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_tc"])
 def test_config1_slice_at_a_time(gpu_lib, precision):
     """plan_slices + solve_slice (the benchmark's unit of work): every window's eigenpairs
     against the dense oracle -- membership exact, eigenvalues to 1e-10, residuals by the

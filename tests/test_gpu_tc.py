@@ -76,3 +76,25 @@ def test_gauss16_tensor_core_inertia_matches_golden(gpu_lib):
         X = f.solve(j, R, refine=1)
         res = sym.spmm(a, b, X, 1.0, -sig[j]) - R
         assert (res.norm() / R.norm()).item() <= 1e-10
+
+
+def test_gauss16_mixed_tc_factor(gpu_lib):
+    """SS_MIXED_TC: FP64 fronts on the tensor cores, FP32 solves from the rounded factor
+    inside FP64 refinement: inertia bit-exact against the goldens, solves to 1e-10."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "gauss16_inertia.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    sig = [float(r[0]) for r in rows]
+    neg = [int(r[1]) for r in rows]
+    p = config_pencil(2)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    f = sym.factor(a, b, sig, "mixed_tc")
+    R = torch.tensor(normal_block(p.n, 4, 3), device="cuda")
+    used = []
+    for j in range(len(sig)):
+        assert f.inertia(j)[0] == neg[j]
+        used.append(f.quality(j)[0])
+        X = f.solve(j, R, refine=2)
+        res = sym.spmm(a, b, X, 1.0, -sig[j]) - R
+        assert (res.norm() / R.norm()).item() <= 1e-10
+    assert set(used) <= {"fp64", "fp64+f32solve"} and "fp64+f32solve" in used
