@@ -115,6 +115,9 @@ typedef struct ss_solve_opts {
                                    starts refining once the window is within 1e-6 or
                                    its residuals stop improving [0]                  */
     int32_t reserved;
+    double refine_ratio;        /* FP32 solves refine until their residual is this
+                                   fraction of the window's current residual (clamped
+                                   to 1e-14 .. 1e-8) [1e-3]                          */
 } ss_solve_opts;
 
 /* ---- context ---------------------------------------------------------------------
@@ -148,6 +151,17 @@ ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
  * Errors: SS_ERR_ARG. */
 enum { SS_SCHUR_TENSOR = 0, SS_SCHUR_SIMT = 1 };
 ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops);
+
+/* Replay of captured factorisations (batching of Alg. 2 step 2; no paper counterpart).
+ * on = 1: ss_factor records the launches of one wave of shifts of an analysis -- every
+ * level's memsets, assembly, extend-add, panel, Schur and store kernels -- into a CUDA
+ * graph the first time it meets that (number of shifts, precision, Schur settings), keeps
+ * the graph and its scratch with the analysis (freed by ss_symbolic_destroy), and on later
+ * calls only uploads the table of per-shift pointers and shifts and launches the graph.
+ * Waves whose scratch exceeds 8 GB, and factorisations timed per launch (ss_profile), run
+ * launch by launch.  The first call for a wave shape must not itself be inside a stream
+ * capture.  on = 0 (default): launch by launch.  Errors: SS_ERR_ARG. */
+ss_status ss_set_factor_graph(ss_ctx *ctx, int32_t on);
 
 /* Self-test of the tensor-core path (no paper counterpart): one 128 x 64 x 64 FP16 MMA tile
  * with seeded integer operands in [-128, 128], staged and read back exactly as the Schur
@@ -218,6 +232,18 @@ ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const double *b_vals
                     const double *sigma, int32_t n_shift, int32_t precision,
                     ss_numeric **out);
 ss_status ss_factor_destroy(ss_numeric *f);
+
+/* Autotuner of the Schur-update path per factor step (no paper counterpart): factors
+ * A - sigma B (DEVICE a_vals, b_vals; inertia only, FP64) once with every eligible step's
+ * Schur update on the tensor cores and once with every step on the CUDA cores, times each
+ * step's update with CUDA events, and records for every step the faster path in the
+ * analysis; later ss_factor calls on it follow these choices in place of the min_flops
+ * rule of ss_set_schur_mode (while the Schur mode is SS_SCHUR_TENSOR).  The steps are the
+ * analysis's front-size buckets, so the choice holds for every shift and every pencil on
+ * the pattern.  *n_tc_steps (HOST, may be NULL): steps that chose the tensor cores.
+ * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_TIMEOUT. */
+ss_status ss_autotune_schur(ss_symbolic *sym, const double *a_vals, const double *b_vals, double sigma,
+                            int32_t *n_tc_steps);
 
 /* ---- ss_inertia (Section 2.2: Sylvester's law of inertia) ------------------------
  * Inertia of A - sigma_j B from the block-diagonal D: n_neg = #negative 1x1 pivots

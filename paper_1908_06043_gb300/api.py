@@ -87,6 +87,10 @@ class Context:
         m = {"tensor": L.SS_SCHUR_TENSOR, "simt": L.SS_SCHUR_SIMT}[mode]
         self.check(self.lib.ss_set_schur_mode(self.h, m, float(min_flops)), "ss_set_schur_mode")
 
+    def set_factor_graph(self, on: bool = True):
+        """Replay captured CUDA graphs of the factorisation (per analysis and wave shape)."""
+        self.check(self.lib.ss_set_factor_graph(self.h, 1 if on else 0), "ss_set_factor_graph")
+
     def selftest_tc(self, seed: int = 1) -> float:
         """Largest error of one FP16 tensor-core MMA tile against the exact product."""
         out = C.c_double()
@@ -168,6 +172,17 @@ class Symbolic:
 
     def spmm(self, a_vals, b_vals, X, alpha=None, beta=None) -> torch.Tensor:
         return spmm(self, a_vals, b_vals, X, alpha, beta)
+
+    def autotune_schur(self, a_vals, b_vals, sigma: float) -> int:
+        """Time every factor step's Schur update on the tensor cores and on the CUDA cores
+        (one inertia-only factorisation at sigma each) and keep the faster path per step.
+        Returns the number of steps that chose the tensor cores."""
+        _dev(a_vals, "a_vals")
+        _dev(b_vals, "b_vals")
+        n = C.c_int32()
+        self.ctx.check(self.ctx.lib.ss_autotune_schur(self.h, _ptr(a_vals), _ptr(b_vals), float(sigma), C.byref(n)),
+                       "ss_autotune_schur")
+        return n.value
 
     def dos_estimate(self, a_vals, b_vals, steps: int, start: torch.Tensor):
         return dos_estimate(self, a_vals, b_vals, steps, start)
@@ -287,7 +302,7 @@ def solve(f: Factor, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
 def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: float = 1e-10,
                 max_iter: int = 0, check_every: int = 1, refine: int = 2, n_expect: int = 0,
                 allow_noconv: bool = False, driver: str = "subspace", k_out: int = 0,
-                refine_from_start: bool = False) -> ProbeResult:
+                refine_from_start: bool = False, refine_ratio: float = 0.0) -> ProbeResult:
     """Spectral probe of shift j: shift-invert subspace iteration (Alg. 2; max_iter
     iterations) or shift-invert block Lanczos (max_iter blocks of width V0.shape[1],
     returning the k_out Ritz pairs nearest sigma_j)."""
@@ -299,6 +314,7 @@ def slice_solve(f: Factor, j: int, lo: float, hi: float, V0: torch.Tensor, tol: 
     opts.max_iter, opts.check_every, opts.refine, opts.tol, opts.n_expect = max_iter, check_every, refine, tol, n_expect
     opts.k_out = kout
     opts.refine_from_start = 1 if refine_from_start else 0
+    opts.refine_ratio = refine_ratio
     lam = np.empty(kout)
     res = np.empty(kout)
     X = torch.empty((n, kout), dtype=torch.float64, device=V0.device)

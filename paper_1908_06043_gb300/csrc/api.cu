@@ -149,6 +149,14 @@ extern "C" ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flo
         return ctx->set_error(SS_ERR_ARG, "ss_set_schur_mode: bad argument");
     ctx->schur_mode = mode;
     ctx->tc_min_flops = min_flops;
+    ctx->plan_gen++;
+    return SS_OK;
+}
+
+extern "C" ss_status ss_set_factor_graph(ss_ctx *ctx, int32_t on) {
+    if (!ctx) return SS_ERR_ARG;
+    if (on != 0 && on != 1) return ctx->set_error(SS_ERR_ARG, "ss_set_factor_graph: on must be 0 or 1");
+    ctx->factor_graph = on;
     return SS_OK;
 }
 
@@ -330,9 +338,237 @@ static void set_smem_attrs(int device) {
     }
 }
 
+// Scratch of one wave of ns shifts: W = L21 D, the Mt transforms, level workspace,
+// contribution-block pool, tensor-core operand slices and their row exponents.
+struct WaveScratch {
+    int64_t ws_n, cb_n, mt_n, wb_n, sl_n, ex_n;
+};
+
+template <typename T>
+static WaveScratch wave_sizes(const ss_symbolic *s, bool tc) {
+    WaveScratch z;
+    z.ws_n = std::max<int64_t>(1, s->ws_total);
+    z.cb_n = std::max<int64_t>(1, s->cb_total);
+    z.mt_n = std::max<int64_t>(1, (int64_t)s->mt_max * NB * NB);
+    z.wb_n = std::max<int64_t>(1, s->wbuf_max);
+    z.sl_n = tc ? std::max<int64_t>(16, s->sl_max) : 16;
+    z.ex_n = tc ? std::max<int64_t>(1, s->ex_max) : 1;
+    return z;
+}
+
+template <typename T>
+static double wave_bytes(const WaveScratch &z) {
+    return (double)sizeof(T) * (double)(z.ws_n + z.cb_n + z.mt_n + z.wb_n) + (double)z.sl_n + 4.0 * (double)z.ex_n;
+}
+
+// whether factor step q runs its Schur update on the tensor cores
+static bool step_uses_tc(const ss_symbolic *s, const ss_ctx *ctx, int q, bool tc) {
+    const StepDesc &sd = s->steps[q];
+    if (!tc || sd.tiles3 <= 0 || sd.tc_tiles <= 0) return false;
+    const int mode = q < (int)s->step_mode.size() ? s->step_mode[q] : -1;
+    if (mode >= 0) return mode == 1;
+    return sd.flops3 >= ctx->tc_min_flops;
+}
+
+// The launches of one factorisation of ns shifts over every level (no host
+// synchronisation: this sequence is also what a CUDA graph captures).  hp: the host copy of
+// the shift table dp (its scratch pointers give the workspace memsets).
+template <typename T>
+static int factor_levels(ss_numeric *f, int ns, ShiftPtrs<T> *dp, const std::vector<ShiftPtrs<T>> &hp, bool tc,
+                         std::vector<std::pair<cudaEvent_t, cudaEvent_t>> *step_ev) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    for (int32_t l = 0; l < s->nlev; ++l) {
+        for (int q = 0; q < ns; ++q)
+            SS_CUDA_TRY(ctx, cudaMemsetAsync(hp[q].ws, 0, sizeof(T) * s->lev_ws[l], st));
+        const int64_t a0 = s->asm_lev_off[l], acount = s->asm_lev_off[l + 1] - a0;
+        if (acount > 0) {
+            unsigned gx = (unsigned)std::min<int64_t>((acount + 255) / 256, 8192);
+            ss_launch(ctx, SS_K_ASSEMBLE, k_assemble<T>, dim3(gx, ns), 256, 0, st, acount, s->d_asm_e + a0,
+                      s->d_asm_dest + a0, (const ShiftPtrs<T> *)dp);
+        }
+        for (int32_t q = s->lev_ext_pass_off[l]; q < s->lev_ext_pass_off[l + 1]; ++q) {
+            const ExtendPass &ps = s->ext_pass[q];
+            ss_launch(ctx, SS_K_EXTEND_ADD, k_extend_add<T>, dim3(ps.cols, ns), 128, 0, st,
+                      s->d_ext_tasks + ps.task_off, ps.count, s->d_relmap, (const ShiftPtrs<T> *)dp);
+        }
+        for (int32_t q = s->lev_step_off[l]; q < s->lev_step_off[l + 1]; ++q) {
+            const StepDesc &sd = s->steps[q];
+            const StepTask *tk = s->d_tasks + sd.task_off;
+            ss_launch(ctx, SS_K_DIAG_BK, k_diag_bk<T>, dim3(sd.count, ns), 256, kDiagSmem, st, tk,
+                      (const ShiftPtrs<T> *)dp, 0);
+            if (sd.tiles4 > 0) {
+                const int cls = std::is_same<T, float>::value ? SS_K_PANEL_F32 : SS_K_PANEL;
+                ss_launch(ctx, cls, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count,
+                          (const ShiftPtrs<T> *)dp);
+                ctx->add_flops(cls, sd.flops4 * ns);
+            }
+            if (step_ev && sd.tiles3 > 0) {
+                cudaEvent_t e0, e1;
+                SS_CUDA_TRY(ctx, cudaEventCreate(&e0));
+                SS_CUDA_TRY(ctx, cudaEventCreate(&e1));
+                SS_CUDA_TRY(ctx, cudaEventRecord(e0, st));
+                (*step_ev)[q] = {e0, e1};
+            }
+            if (step_uses_tc(s, ctx, q, tc)) {
+                ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_slice, dim3(sd.sl_tiles, ns), 128, 0, st, tk, sd.count,
+                          (const ShiftPtrs<double> *)(void *)dp);
+                ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_schur_tc, dim3(sd.tc_tiles, ns), sstc::kSchurTcThreads,
+                          sstc::kSchurTcSmem, st, tk, sd.count, (const ShiftPtrs<double> *)(void *)dp);
+                ctx->add_flops(SS_K_SCHUR_TC, sd.flops3 * ns);
+            } else if (sd.tiles3 > 0) {
+                const int cls = std::is_same<T, float>::value ? SS_K_SCHUR_F32 : SS_K_SCHUR;
+                ss_launch(ctx, cls, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count,
+                          (const ShiftPtrs<T> *)dp);
+                ctx->add_flops(cls, sd.flops3 * ns);
+            }
+            if (step_ev && sd.tiles3 > 0) SS_CUDA_TRY(ctx, cudaEventRecord((*step_ev)[q].second, st));
+        }
+        const int32_t t0 = s->lev_store_off[l], nt = s->lev_store_off[l + 1] - t0;
+        if (nt > 0 && s->lev_store_cols[l] > 0)
+            ss_launch(ctx, SS_K_MISC, k_level_store<T>, dim3(s->lev_store_cols[l], ns), 128, 0, st,
+                      (const StoreTask *)(s->d_store_tasks + t0), nt, (const ShiftPtrs<T> *)dp);
+    }
+    SS_CUDA_TRY(ctx, cudaGetLastError());
+    return SS_OK;
+}
+
+template <typename T>
+static void fill_shift(ss_numeric *f, int j, ShiftPtrs<T> &p) {
+    p.a = f->a_vals;
+    p.b = f->b_vals;
+    p.lst = (T *)f->arena[j];
+    p.linv = f->linv[j];
+    p.dblk = f->dblk[j];
+    p.piv = f->piv[j];
+    p.counts = f->d_counts + SS_NCOUNT * j;
+    p.sigma = f->sigma[j];
+    p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
+    p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
+}
+
+template <typename T>
+static void point_scratch(ShiftPtrs<T> &p, const WaveScratch &z, int q, T *mt, T *wb, T *ws, T *cb, unsigned char *sl,
+                          int32_t *ex) {
+    p.ws = ws + (int64_t)q * z.ws_n;
+    p.cb = cb + (int64_t)q * z.cb_n;
+    p.mt = mt + (int64_t)q * z.mt_n;
+    p.wbuf = wb + (int64_t)q * z.wb_n;
+    p.sl = sl + (int64_t)q * z.sl_n;
+    p.ex = ex + (int64_t)q * z.ex_n;
+}
+
+void ss_free_plans(ss_symbolic *s) {
+    for (FactorPlan *pl : s->plans) {
+        if (pl->exec) cudaGraphExecDestroy(pl->exec);
+        void *ptrs[] = {pl->mt, pl->wb, pl->ws, pl->cb, pl->sl, pl->ex, pl->dp};
+        for (void *q : ptrs)
+            if (q) cudaFree(q);
+        delete pl;
+    }
+    s->plans.clear();
+}
+
+// Captured factorisations are kept while their scratch stays within this many bytes.
+constexpr double kPlanScratchMax = 8.0e9;
+
+// One wave through a captured CUDA graph: the plan for (ns, precision, tensor cores) is
+// captured on first use (scratch allocated once and kept with the analysis), then every
+// call only uploads the shift table and launches the graph.
+template <typename T>
+static int factor_wave_graph(ss_numeric *f, const std::vector<int> &js, bool tc, const WaveScratch &z) {
+    ss_symbolic *s = f->sym;
+    ss_ctx *ctx = s->ctx;
+    cudaStream_t st = ctx->stream;
+    const int ns = (int)js.size();
+    const int fp32 = std::is_same<T, float>::value ? 1 : 0;
+    // a plan captured under other Schur settings is stale
+    for (size_t q = 0; q < s->plans.size();) {
+        FactorPlan *c = s->plans[q];
+        if (c->gen != ctx->plan_gen) {
+            SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+            if (c->exec) cudaGraphExecDestroy(c->exec);
+            void *ptrs[] = {c->mt, c->wb, c->ws, c->cb, c->sl, c->ex, c->dp};
+            for (void *v : ptrs)
+                if (v) cudaFree(v);
+            delete c;
+            s->plans.erase(s->plans.begin() + q);
+        } else {
+            ++q;
+        }
+    }
+    FactorPlan *pl = nullptr;
+    for (FactorPlan *c : s->plans)
+        if (c->ns == ns && c->fp32 == fp32 && c->tc == (tc ? 1 : 0)) pl = c;
+    std::vector<ShiftPtrs<T>> hp(ns);
+    const bool fresh = pl == nullptr;
+    if (fresh) {
+        pl = new FactorPlan();
+        pl->gen = ctx->plan_gen;
+        pl->ns = ns;
+        pl->fp32 = fp32;
+        pl->tc = tc ? 1 : 0;
+        cudaError_t e = cudaMalloc(&pl->mt, sizeof(T) * z.mt_n * ns);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->wb, sizeof(T) * z.wb_n * ns);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->ws, sizeof(T) * z.ws_n * ns);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->cb, sizeof(T) * z.cb_n * ns);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->sl, (size_t)z.sl_n * ns);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->ex, sizeof(int32_t) * z.ex_n * ns);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->dp, sizeof(ShiftPtrs<T>) * ns);
+        s->plans.push_back(pl);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ctx->set_error(SS_ERR_OOM, "ss_factor: allocation of a captured factorisation's scratch failed");
+        }
+    }
+    for (int q = 0; q < ns; ++q) {
+        fill_shift<T>(f, js[q], hp[q]);
+        point_scratch<T>(hp[q], z, q, (T *)pl->mt, (T *)pl->wb, (T *)pl->ws, (T *)pl->cb, (unsigned char *)pl->sl,
+                         (int32_t *)pl->ex);
+    }
+    SS_CUDA_TRY(ctx, cudaMemcpyAsync(pl->dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
+    if (fresh) {
+        cudaGraph_t graph = nullptr;
+        SS_CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        ctx->capturing = true;
+        int rc = factor_levels<T>(f, ns, (ShiftPtrs<T> *)pl->dp, hp, tc, nullptr);
+        ctx->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (rc != SS_OK) return rc;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return ctx->set_error(SS_ERR_CUDA, std::string("ss_factor: graph capture failed: ") + cudaGetErrorString(e));
+        }
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+        int64_t kn = 0;
+        for (cudaGraphNode_t nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kn;
+        }
+        pl->kernel_nodes = kn;
+        e = cudaGraphInstantiate(&pl->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            pl->exec = nullptr;
+            return ctx->set_error(SS_ERR_CUDA, std::string("ss_factor: graph instantiation failed: ") +
+                                                   cudaGetErrorString(e));
+        }
+    }
+    SS_CUDA_TRY(ctx, cudaGraphLaunch(pl->exec, st));
+    g_ss_launches.fetch_add(pl->kernel_nodes, std::memory_order_relaxed);
+    return SS_OK;
+}
+
 // Factorisation of the shifts in `which`, in waves of as many shifts as the free device
 // memory holds: each shift of a wave has its own level workspace, contribution-block pool
 // and panel scratch for the duration of the wave; the L storage (f->arena) persists.
+// With ss_set_factor_graph on (and no per-launch profiling), a wave whose scratch fits
+// kPlanScratchMax replays a captured CUDA graph instead of launching kernel by kernel.
 template <typename T>
 static int factor_run(ss_numeric *f, const std::vector<int> &which) {
     ss_symbolic *s = f->sym;
@@ -341,12 +577,10 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
     set_smem_attrs<T>(ctx->device);
     const int ns_all = (int)which.size();
     if (ns_all == 0) return SS_OK;
-    const int64_t ws_n = std::max<int64_t>(1, s->ws_total), cb_n = std::max<int64_t>(1, s->cb_total);
-    const int64_t mt_n = std::max<int64_t>(1, (int64_t)s->mt_max * NB * NB), wb_n = std::max<int64_t>(1, s->wbuf_max);
     // FP64 steps with enough Schur work run the tensor-core update (tc_kernels.cuh)
     const bool tc = std::is_same<T, double>::value && ctx->schur_mode == SS_SCHUR_TENSOR && s->sl_max > 0;
-    const int64_t sl_n = tc ? s->sl_max : 16, ex_n = tc ? std::max<int64_t>(1, s->ex_max) : 1;
-    const double per_shift = (double)sizeof(T) * (double)(ws_n + cb_n + mt_n + wb_n) + (double)sl_n + 4.0 * ex_n;
+    const WaveScratch z = wave_sizes<T>(s, tc);
+    const double per_shift = wave_bytes<T>(z);
     size_t mem_free = 0, mem_tot = 0;
     SS_CUDA_TRY(ctx, cudaMemGetInfo(&mem_free, &mem_tot));
     int wave = (int)std::max(1.0, std::min((double)std::min(ns_all, 65535), std::floor(0.8 * (double)mem_free / per_shift)));
@@ -355,81 +589,35 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
         SS_CUDA_TRY(ctx, cudaMemcpyAsync(f->d_counts + SS_NCOUNT * which[q], init, sizeof(init),
                                          cudaMemcpyHostToDevice, st));
     SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));    // init is a host array
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> step_ev;
+    if (ctx->step_times) step_ev.assign(s->steps.size(), {nullptr, nullptr});
     for (int w0 = 0; w0 < ns_all; w0 += wave) {
         const int ns = std::min(wave, ns_all - w0);
+        std::vector<int> js(which.begin() + w0, which.begin() + w0 + ns);
+        if (ctx->factor_graph && !ctx->prof_mask && !ctx->step_times && per_shift * ns <= kPlanScratchMax) {
+            int rc = factor_wave_graph<T>(f, js, tc, z);
+            if (rc != SS_OK) return rc;
+            continue;
+        }
         T *mt = nullptr, *wb = nullptr, *ws = nullptr, *cb = nullptr;
         unsigned char *sl = nullptr;
         int32_t *ex = nullptr;
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&sl, (size_t)sl_n * ns, st));
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&ex, sizeof(int32_t) * ex_n * ns, st));
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mt, sizeof(T) * mt_n * ns, st));
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wb, sizeof(T) * wb_n * ns, st));
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&ws, sizeof(T) * ws_n * ns, st));
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&cb, sizeof(T) * cb_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&sl, (size_t)z.sl_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&ex, sizeof(int32_t) * z.ex_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&mt, sizeof(T) * z.mt_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&wb, sizeof(T) * z.wb_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&ws, sizeof(T) * z.ws_n * ns, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&cb, sizeof(T) * z.cb_n * ns, st));
         std::vector<ShiftPtrs<T>> hp(ns);
         for (int q = 0; q < ns; ++q) {
-            const int j = which[w0 + q];
-            ShiftPtrs<T> &p = hp[q];
-            p.ws = ws + (int64_t)q * ws_n;
-            p.cb = cb + (int64_t)q * cb_n;
-            p.lst = (T *)f->arena[j];
-            p.linv = f->linv[j];
-            p.dblk = f->dblk[j];
-            p.piv = f->piv[j];
-            p.mt = mt + (int64_t)q * mt_n;
-            p.wbuf = wb + (int64_t)q * wb_n;
-            p.sl = sl + (int64_t)q * sl_n;
-            p.ex = ex + (int64_t)q * ex_n;
-            p.counts = f->d_counts + SS_NCOUNT * j;
-            p.sigma = f->sigma[j];
-            p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
-            p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
+            fill_shift<T>(f, js[q], hp[q]);
+            point_scratch<T>(hp[q], z, q, mt, wb, ws, cb, sl, ex);
         }
         ShiftPtrs<T> *dp = nullptr;
         SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&dp, sizeof(ShiftPtrs<T>) * ns, st));
         SS_CUDA_TRY(ctx, cudaMemcpyAsync(dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
-        for (int32_t l = 0; l < s->nlev; ++l) {
-            for (int q = 0; q < ns; ++q)
-                SS_CUDA_TRY(ctx, cudaMemsetAsync(hp[q].ws, 0, sizeof(T) * s->lev_ws[l], st));
-            const int64_t a0 = s->asm_lev_off[l], acount = s->asm_lev_off[l + 1] - a0;
-            if (acount > 0) {
-                unsigned gx = (unsigned)std::min<int64_t>((acount + 255) / 256, 8192);
-                ss_launch(ctx, SS_K_ASSEMBLE, k_assemble<T>, dim3(gx, ns), 256, 0, st, acount, s->d_asm_e + a0,
-                          s->d_asm_dest + a0, f->a_vals, f->b_vals, dp);
-            }
-            for (int32_t q = s->lev_ext_pass_off[l]; q < s->lev_ext_pass_off[l + 1]; ++q) {
-                const ExtendPass &ps = s->ext_pass[q];
-                ss_launch(ctx, SS_K_EXTEND_ADD, k_extend_add<T>, dim3(ps.cols, ns), 128, 0, st,
-                          s->d_ext_tasks + ps.task_off, ps.count, s->d_relmap, dp);
-            }
-            for (int32_t q = s->lev_step_off[l]; q < s->lev_step_off[l + 1]; ++q) {
-                const StepDesc &sd = s->steps[q];
-                const StepTask *tk = s->d_tasks + sd.task_off;
-                ss_launch(ctx, SS_K_DIAG_BK, k_diag_bk<T>, dim3(sd.count, ns), 256, kDiagSmem, st, tk, dp, 0);
-                if (sd.tiles4 > 0) {
-                    const int cls = std::is_same<T, float>::value ? SS_K_PANEL_F32 : SS_K_PANEL;
-                    ss_launch(ctx, cls, k_panel<T>, dim3(sd.tiles4, ns), 256, panel_smem<T>(), st, tk, sd.count, dp);
-                    ctx->add_flops(cls, sd.flops4 * ns);
-                }
-                if (sd.tiles3 > 0 && tc && sd.tc_tiles > 0 && sd.flops3 >= ctx->tc_min_flops) {
-                    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_slice, dim3(sd.sl_tiles, ns), 128, 0, st, tk, sd.count,
-                              (const ShiftPtrs<double> *)dp);
-                    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_schur_tc, dim3(sd.tc_tiles, ns), sstc::kSchurTcThreads,
-                              sstc::kSchurTcSmem,
-                              st, tk, sd.count, (const ShiftPtrs<double> *)dp);
-                    ctx->add_flops(SS_K_SCHUR_TC, sd.flops3 * ns);
-                } else if (sd.tiles3 > 0) {
-                    const int cls = std::is_same<T, float>::value ? SS_K_SCHUR_F32 : SS_K_SCHUR;
-                    ss_launch(ctx, cls, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count, dp);
-                    ctx->add_flops(cls, sd.flops3 * ns);
-                }
-            }
-            const int32_t t0 = s->lev_store_off[l], nt = s->lev_store_off[l + 1] - t0;
-            if (nt > 0 && s->lev_store_cols[l] > 0)
-                ss_launch(ctx, SS_K_MISC, k_level_store<T>, dim3(s->lev_store_cols[l], ns), 128, 0, st,
-                          (const StoreTask *)(s->d_store_tasks + t0), nt, dp);
-        }
-        SS_CUDA_TRY(ctx, cudaGetLastError());
+        int rc = factor_levels<T>(f, ns, dp, hp, tc, ctx->step_times ? &step_ev : nullptr);
+        if (rc != SS_OK) return rc;
         SS_CUDA_TRY(ctx, cudaFreeAsync(dp, st));
         SS_CUDA_TRY(ctx, cudaFreeAsync(mt, st));
         SS_CUDA_TRY(ctx, cudaFreeAsync(wb, st));
@@ -437,6 +625,18 @@ static int factor_run(ss_numeric *f, const std::vector<int> &which) {
         SS_CUDA_TRY(ctx, cudaFreeAsync(cb, st));
         SS_CUDA_TRY(ctx, cudaFreeAsync(sl, st));
         SS_CUDA_TRY(ctx, cudaFreeAsync(ex, st));
+    }
+    if (ctx->step_times) {
+        SS_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+        ctx->step_times->assign(s->steps.size(), 0.0);
+        for (size_t q = 0; q < step_ev.size(); ++q) {
+            if (!step_ev[q].first) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, step_ev[q].first, step_ev[q].second);
+            (*ctx->step_times)[q] += 1e-3 * ms;
+            cudaEventDestroy(step_ev[q].first);
+            cudaEventDestroy(step_ev[q].second);
+        }
     }
     return SS_OK;
 }
@@ -626,6 +826,41 @@ extern "C" ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const dou
     } catch (const std::bad_alloc &) {
         return ctx->set_error(SS_ERR_OOM, "ss_factor: host allocation failed");
     }
+}
+
+extern "C" ss_status ss_autotune_schur(ss_symbolic *sym, const double *a_vals, const double *b_vals, double sigma,
+                                       int32_t *n_tc_steps) {
+    if (!sym) return SS_ERR_ARG;
+    ss_ctx *ctx = sym->ctx;
+    if (ctx->device < 0 || !a_vals || !b_vals || !std::isfinite(sigma))
+        return ctx->set_error(SS_ERR_ARG, "ss_autotune_schur: bad argument or host-only context");
+    const int saved_mode = ctx->schur_mode;
+    std::vector<double> t_tc, t_simt;
+    int rc = SS_OK;
+    // the same inertia-only FP64 factorisation, once with every eligible step on the tensor
+    // cores and once with every step on the CUDA cores, each step's Schur update timed
+    ctx->schur_mode = SS_SCHUR_TENSOR;
+    for (int pass = 0; pass < 2 && rc == SS_OK; ++pass) {
+        std::fill(sym->step_mode.begin(), sym->step_mode.end(), (int8_t)(pass == 0 ? 1 : 0));
+        std::vector<double> &dst = pass == 0 ? t_tc : t_simt;
+        ctx->step_times = &dst;
+        ss_numeric *f = nullptr;
+        rc = ss_factor_create(sym, a_vals, b_vals, &sigma, 1, SS_FP64 | SS_INERTIA_ONLY, &f);
+        ctx->step_times = nullptr;
+        if (f) ss_factor_destroy(f);
+        if (rc == SS_ERR_SINGULAR) rc = SS_OK;      // the timing stands; the shift is irrelevant
+    }
+    ctx->schur_mode = saved_mode;
+    int32_t n = 0;
+    for (size_t q = 0; q < sym->steps.size(); ++q) {
+        const bool eligible = sym->steps[q].tiles3 > 0 && sym->steps[q].tc_tiles > 0;
+        const bool use = rc == SS_OK && eligible && q < t_tc.size() && q < t_simt.size() && t_tc[q] < t_simt[q];
+        sym->step_mode[q] = (int8_t)(rc == SS_OK ? (use ? 1 : 0) : -1);
+        n += use ? 1 : 0;
+    }
+    ctx->plan_gen++;
+    if (n_tc_steps) *n_tc_steps = n;
+    return rc;
 }
 
 extern "C" ss_status ss_factor_destroy(ss_numeric *f) {

@@ -31,6 +31,7 @@ template <typename T> constexpr size_t schur_smem() { return 2 * NB * (TR + 1) *
 
 template <typename T>
 struct ShiftPtrs {
+    const double *a, *b;            // pencil values on the pattern (caller-owned)
     T *ws;                          // level workspace (fronts of the level being factored)
     T *cb;                          // contribution-block pool
     T *lst;                         // L storage (null: inertia only, nothing kept)
@@ -50,13 +51,12 @@ struct ShiftPtrs {
 // ---------------------------------------------------------------- assembly
 template <typename T>
 __global__ void k_assemble(int64_t count, const int32_t *__restrict__ asm_e,
-                           const int64_t *__restrict__ asm_dest, const double *__restrict__ a,
-                           const double *__restrict__ b, const ShiftPtrs<T> *sp) {
+                           const int64_t *__restrict__ asm_dest, const ShiftPtrs<T> *sp) {
     const ShiftPtrs<T> s = sp[blockIdx.y];
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
          q += (int64_t)gridDim.x * blockDim.x) {
         int32_t e = asm_e[q];
-        s.ws[asm_dest[q]] = (T)(a[e] - s.sigma * b[e]);
+        s.ws[asm_dest[q]] = (T)(s.a[e] - s.sigma * s.b[e]);
     }
 }
 

@@ -20,6 +20,10 @@ struct ss_ctx {
     std::string err;
     int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
     int schur_mode = SS_SCHUR_TENSOR;         // FP64 Schur update: tensor cores or CUDA cores
+    int factor_graph = 0;                     // replay captured CUDA graphs of the factorisation
+    bool capturing = false;                   // a factorisation is being captured (launches not counted)
+    std::vector<double> *step_times = nullptr;   // per factor step Schur time (autotuner), or null
+    int64_t plan_gen = 0;                     // bumped when a setting baked into captured graphs changes
     double tc_min_flops = 2.0e7;              // a factor step's Schur flops below which it stays on CUDA cores
     GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
     int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)
@@ -53,7 +57,7 @@ void ss_prof_end(ss_ctx *ctx, int cls, size_t slot);
 template <typename... KArgs, typename... Args>
 inline void ss_launch(ss_ctx *ctx, int cls, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
                       cudaStream_t st, Args &&...args) {
-    g_ss_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!ctx->capturing) g_ss_launches.fetch_add(1, std::memory_order_relaxed);
     if (ctx->prof_mask & (1u << cls)) {
         size_t slot = ss_prof_begin(ctx, cls);
         kern<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
@@ -140,8 +144,24 @@ struct SolveLevel {      // panels whose forward step can run together
     double offdiag;      // sum over its panels of (rows below the diagonal block) x w
 };
 
+// A captured factorisation of `ns` shifts (one wave) in one precision: persistent scratch
+// and the instantiated CUDA graph of the whole level loop.  A replay only refreshes the
+// device table of per-shift pointers and values (dp) the kernels read.
+struct FactorPlan {
+    int ns = 0;
+    int fp32 = 0;          // fronts in FP32
+    int tc = 0;            // tensor-core Schur steps enabled
+    void *mt = nullptr, *wb = nullptr, *ws = nullptr, *cb = nullptr, *sl = nullptr, *ex = nullptr, *dp = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernel_nodes = 0;
+    int64_t gen = 0;       // ss_ctx::plan_gen at capture
+};
+
 struct ss_symbolic {
     ss_ctx *ctx = nullptr;
+    std::vector<FactorPlan *> plans;         // captured factorisations (freed with the analysis)
+    std::vector<int8_t> step_mode;           // per factor step: -1 rule of ss_set_schur_mode,
+                                             // 0 CUDA cores, 1 tensor cores (autotuner)
     int64_t n = 0, nnz = 0;
     int nb = 64;
     std::vector<int32_t> perm, iperm;        // perm[new] = old, iperm[old] = new
@@ -238,6 +258,7 @@ inline bool ss_solves_f32(const ss_numeric *f, int j) {
 // helpers implemented in the .cu files
 int ss_symbolic_upload(ss_symbolic *s);
 void ss_symbolic_free_device(ss_symbolic *s);
+void ss_free_plans(ss_symbolic *s);
 int ss_factor_fetch_counts(ss_numeric *f);
 int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
                      int32_t n_shift, int32_t precision, ss_numeric **out);

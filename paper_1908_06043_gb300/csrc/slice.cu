@@ -260,7 +260,7 @@ int rq_polish(ss_numeric *f, const double *X, int k, double *theta_d, DevBuf &bu
     ss_ctx *ctx = s->ctx;
     const int64_t n = s->n;
     const int nby = (int)cdiv(k, 128);
-    const int64_t nbx = std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 32), cdiv(8ll * ctx->sm_count, nby)));
+    const int64_t nbx = std::max<int64_t>(1, std::min<int64_t>(cdiv(n, 16), cdiv(32ll * ctx->sm_count, nby)));
     const int64_t rows_per = (n + nbx - 1) / nbx;
     const int64_t nparts = (n + rows_per - 1) / rows_per;
     double *part;
@@ -314,6 +314,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     const int every = o.check_every > 0 ? o.check_every : 1;
     const int refine = o.refine > 0 ? o.refine : 2;
     const double tol = o.tol > 0 ? o.tol : 1e-10;
+    const double ratio = o.refine_ratio > 0 ? std::min(o.refine_ratio, 1.0) : 1e-3;
     const int64_t per = 2048;
     while (it < max_iter) {
         ++it;
@@ -325,7 +326,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // (1e-13 before the first Rayleigh-Ritz of this call, at most 1e-8)
         double ref_target = 0.0;
         if (near_conv && ss_solves_f32(f, j))
-            ref_target = hist.empty() ? 1e-13 : std::max(1e-14, std::min(1e-8, 1e-3 * hist.back()));
+            ref_target = hist.empty() ? 1e-13 : std::max(1e-14, std::min(1e-8, ratio * hist.back()));
         if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref, ref_target)) != SS_OK) return rc;
         refine_total += done_ref;
         if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;

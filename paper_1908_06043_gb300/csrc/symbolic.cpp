@@ -542,6 +542,7 @@ static int analyze_impl(ss_ctx *ctx, int64_t n, const int64_t *rowptr, const int
         }
     }
     s->lev_step_off[nlev] = (int32_t)s->steps.size();
+    s->step_mode.assign(s->steps.size(), -1);
 
     // solve levels: panel (b, t) waits for panel (b, t-1), or for the last panel of
     // every child when t = 0
@@ -646,6 +647,7 @@ extern "C" ss_status ss_symbolic_perm(const ss_symbolic *sym, int32_t *perm) {
 
 extern "C" ss_status ss_symbolic_destroy(ss_symbolic *sym) {
     if (!sym) return SS_OK;
+    ss_free_plans(sym);
     ss_symbolic_free_device(sym);
     delete sym;
     return SS_OK;

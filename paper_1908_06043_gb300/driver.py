@@ -375,9 +375,11 @@ class SliceResult:
 class SliceSolver:
     """Lowest-n_e eigenpairs of (A, B) by spectrum slicing on one GPU."""
 
-    def __init__(self, sym: api.Symbolic, a_vals, b_vals, precision="mixed", tol=1e-10, refine=2):
+    def __init__(self, sym: api.Symbolic, a_vals, b_vals, precision="mixed", tol=1e-10, refine=2,
+                 refine_ratio=0.0):
         self.sym, self.a, self.b = sym, a_vals, b_vals
         self.precision, self.tol, self.refine = precision, tol, refine
+        self.refine_ratio = refine_ratio       # 0: the library default (1e-3)
 
     def count_below(self, sigmas):
         """Exact eigenvalue counts below each sigma (inertia of one batched FP64 factor
@@ -661,20 +663,29 @@ class SliceOutcome:
     precision_used: str
 
 
-def plan_slices(solver: "SliceSolver", model: "DosModel", n_e: int, n_s: int, mode: str = "ball") -> SlicePlan:
+def plan_slices(solver: "SliceSolver", model: "DosModel", n_e: int, n_s: int, mode: str = "ball",
+                windows=None) -> SlicePlan:
     """Place n_s shifts for the lowest n_e eigenvalues (place_shifts) and count the
-    eigenvalues below every window bound with one batched FP64 factor."""
+    eigenvalues below the window bounds with one batched inertia-only FP64 factor: below
+    every bound, or (windows = a list of window indices) only below the bounds of those
+    windows (the other counts stay None and those windows cannot be solved)."""
     lam_min, lam_max, shifts, splits, ks = solver.place_shifts(model, n_e, n_s, mode=mode)
     inner = [splits[j] if splits is not None and splits[j] is not None else 0.5 * (shifts[j - 1] + shifts[j])
              for j in range(1, n_s)]
     bounds = [lam_min] + inner + [lam_max]
-    counts = solver.count_below(bounds)
+    need = sorted(set(range(n_s + 1)) if windows is None else {b for j in windows for b in (j, j + 1)})
+    got = solver.count_below([bounds[b] for b in need])
+    counts = [None] * (n_s + 1)
+    for b, c in zip(need, got):
+        counts[b] = c
     if ks is None:
         ks = [None] * n_s
     n = solver.sym.n
-    ks = [min(n, 4096, max(k or 0, _ceil16(2 * (counts[j + 1] - counts[j]) + 16), _ceil16(counts[j + 1] - counts[j] + 16)))
-          for j, k in enumerate(ks)]
-    return SlicePlan(list(shifts), bounds, counts, ks, lam_min, lam_max)
+    out = []
+    for j, k in enumerate(ks):
+        c = counts[j + 1] - counts[j] if counts[j] is not None and counts[j + 1] is not None else 0
+        out.append(min(n, 4096, max(k or 0, _ceil16(2 * c + 16), _ceil16(c + 16))))
+    return SlicePlan(list(shifts), bounds, counts, out, lam_min, lam_max)
 
 
 def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, first_iters: int = 80,
@@ -708,7 +719,8 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
     else:
         V0 = torch.randn(n, kk, generator=g, device="cuda", dtype=torch.float64)
     pr = f.slice_solve(0, lo, hi, V0, tol=solver.tol, max_iter=first_iters, refine=solver.refine,
-                       n_expect=max(1, exact), allow_noconv=True, check_every=3, refine_from_start=warm)
+                       n_expect=max(1, exact), allow_noconv=True, check_every=3, refine_from_start=warm,
+                       refine_ratio=solver.refine_ratio)
     iters, rounds = pr.iterations, 1
     f64, best, stall = None, np.inf, 0
 
@@ -732,7 +744,7 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
         fj = f64 if f64 is not None else f
         pr = fj.slice_solve(0, lo, hi, X, tol=solver.tol, max_iter=iters_per_round, refine=solver.refine,
                             n_expect=max(1, exact), allow_noconv=True, refine_from_start=True,
-                            check_every=iters_per_round)
+                            check_every=iters_per_round, refine_ratio=solver.refine_ratio)
         iters += pr.iterations
     torch.cuda.synchronize()
     factor_s = ev0.elapsed_time(ev1) / 1e3

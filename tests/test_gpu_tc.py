@@ -98,3 +98,46 @@ def test_gauss16_mixed_tc_factor(gpu_lib):
         res = sym.spmm(a, b, X, 1.0, -sig[j]) - R
         assert (res.norm() / R.norm()).item() <= 1e-10
     assert set(used) <= {"fp64", "fp64+f32solve"} and "fp64+f32solve" in used
+
+
+def _golden_inertia():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "gauss16_inertia.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    return [float(r[0]) for r in rows], [int(r[1]) for r in rows]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed_tc"])
+def test_factor_graph_replay_matches_launches(gpu_lib, precision):
+    """A captured factorisation replayed for new shifts gives the factor the kernel-by-kernel
+    launches give (the same kernels in the same order: solves agree to the last bit)."""
+    sig, neg = _golden_inertia()
+    p = config_pencil(2)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    R = torch.tensor(normal_block(p.n, 3, 4), device="cuda")
+    ref = []
+    for s_ in sig[:3]:
+        f = sym.factor(a, b, [s_], precision)
+        ref.append((f.inertia(0)[0], f.solve(0, R, refine=0)))
+        f.close()
+    ctx.set_factor_graph(True)
+    n0 = ctx.launch_count()
+    for t, s_ in enumerate(sig[:3]):              # capture on the first, replay on the others
+        f = sym.factor(a, b, [s_], precision)
+        assert f.inertia(0)[0] == ref[t][0] == neg[t]
+        assert torch.equal(f.solve(0, R, refine=0), ref[t][1])
+        f.close()
+    assert ctx.launch_count() - n0 > 3 * 100      # the replayed kernels are counted
+    ctx.set_factor_graph(False)
+
+
+def test_schur_autotuner(gpu_lib):
+    """The autotuner times every factor step's Schur update on both paths and keeps the
+    faster one per step; factors afterwards keep the exact inertia."""
+    sig, neg = _golden_inertia()
+    p = config_pencil(2)
+    ctx, sym, a, b = setup(gpu_lib, p)
+    n_tc = sym.autotune_schur(a, b, -1.0)
+    assert 0 <= n_tc <= sym.info["n_panels"]
+    f = sym.factor(a, b, sig, "fp64")
+    assert [f.inertia(j)[0] for j in range(len(sig))] == neg
