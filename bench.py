@@ -43,7 +43,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "gauss16"
 METRIC = "slice solves/s at N=110,592 (mixed vs FP64, resid<=1e-10); factor TFLOP/s"
 FLOP_CLASSES = {"schur", "panel", "fwd_update", "bwd_gather", "spmm", "gram", "gemm", "solve",
-                "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32", "solve_f32", "schur_tc"}
+                "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32", "solve_f32", "schur_tc", "gemm_tc", "spmm_tc"}
 
 
 def parse():
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "fp64"])
+    ap.add_argument("--gemm", default="simt", choices=["tensor", "simt"],
+                    help="where the probes' dense FP64 products (Gram, tall) run")
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end pass (default: --steps)")
@@ -64,6 +66,12 @@ def parse():
                          "workload with probe migration and print one JSON line per pencil")
     ap.add_argument("--only-probe", action="store_true",
                     help="profiling case: factor one shift of the workload and run its probe for 6 iterations")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="profiling case: placement, one warm-up slice solve (window n_s/2 - 1), then one slice "
+                         "solve (window n_s/2) inside the NVTX range 'slice_step'")
+    ap.add_argument("--factor-only", default=None, choices=["tensor", "simt"],
+                    help="profiling case: one FP64 factorisation at sigma = -1 with the given Schur path "
+                         "(twice: the second is the one to capture)")
     return ap.parse_args()
 
 
@@ -266,6 +274,7 @@ def main():
     t_setup = time.perf_counter()
     p = config_pencil(wl["config"])
     ctx = api.Context(dev)
+    ctx.set_gemm_mode(args.gemm)
     sym = ctx.analyze(p.rowptr, p.colind)
     info = sym.info
     a = torch.tensor(p.a, device="cuda")
@@ -276,6 +285,20 @@ def main():
     steps_dos, n_vec = 100, 4
     peak64 = ctx.measure_peak("fp64", 0.5)
     peak32 = ctx.measure_peak("fp32", 0.5)
+
+    if args.factor_only:
+        ctx.set_schur_mode(args.factor_only)
+        out = {}
+        for rep in range(2):
+            ctx.profile(api.L.KERNEL_CLASSES)
+            f = sym.factor(a, b, [-1.0], "fp64")
+            prof = {c: ctx.profile_query(c) for c in api.L.KERNEL_CLASSES}
+            ctx.profile(())
+            f.close()
+            out = {c: [v[0], round(1e3 * v[1], 3), round(v[2] / v[1] / 1e12, 3) if v[1] > 0 else 0.0]
+                   for c, v in prof.items() if v[0]}
+        print(json.dumps({"factor_only": args.factor_only, "workload": wl["name"], "classes": out}), flush=True)
+        return
 
     if args.sequence:
         # SCF-like pencil sequence: DOS placement for the first pencil, k-means probe
@@ -313,11 +336,24 @@ def main():
     solver = SliceSolver(sym, a, b, precision=args.precision)
     # exact counts only at the bounds of the windows this run solves (warm-up, timed,
     # end-to-end and FP64 steps all take windows 0, 1, ... cyclically)
-    n_used = min(n_s, max(args.warmup, args.steps, args.e2e_steps))
+    n_used = min(n_s, max(args.warmup, args.steps, args.e2e_steps, n_s // 2 + 1 if args.profile_step else 0))
     plan = plan_slices(solver, model, n_e, n_s, windows=range(n_used))
     torch.cuda.synchronize()
     placement_s = time.perf_counter() - t_place
     setup_s = time.perf_counter() - t_setup
+
+    if args.profile_step:
+        j = n_s // 2
+        solve_slice(solver, plan, j - 1, seed=1)
+        torch.cuda.synchronize()
+        n0 = ctx.launch_count()
+        torch.cuda.nvtx.range_push("slice_step")
+        o = solve_slice(solver, plan, j, seed=2)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"profile_step": True, "window": j, "launches": ctx.launch_count() - n0, "ok": o.ok,
+                          "iterations": o.iterations, "precision_used": o.precision_used}), flush=True)
+        return
 
     if args.only_probe:
         # one representative probe of the workload (window n_s/2), for ncu
@@ -458,7 +494,7 @@ def main():
            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
            "data": "synthetic",
-           "config": {"workload": wl["name"], "precision": args.precision,
+           "config": {"workload": wl["name"], "precision": args.precision, "dense_products": args.gemm,
                       "step": "one slice solve: LDL^T of A - sigma_j B, inertia, shift-invert subspace "
                               "iteration of window j to resid <= 1e-10, validation by inertia counts",
                       "windows": f"step s solves window s mod {n_s}",

@@ -102,7 +102,10 @@ typedef struct ss_solve_opts {
     int32_t driver;             /* SS_SUBSPACE | SS_BLOCK_LANCZOS [SS_SUBSPACE]      */
     int32_t max_iter;           /* SS_SUBSPACE: iteration cap [200];
                                    SS_BLOCK_LANCZOS: Krylov blocks in the basis [6]  */
-    int32_t check_every;        /* Rayleigh-Ritz + residual check period [1]         */
+    int32_t check_every;        /* Rayleigh-Ritz + residual check period [1]; c < 0:
+                                   first check after |c| iterations, later ones where
+                                   the residual's reduction per iteration between the
+                                   last two checks predicts convergence (1 .. 8 apart) */
     int32_t refine;             /* FP64 refinement corrections per solve, mixed
                                    factor only [2]                                   */
     double tol;                 /* normalised residual target [1e-10]                */
@@ -151,6 +154,39 @@ ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
  * Errors: SS_ERR_ARG. */
 enum { SS_SCHUR_TENSOR = 0, SS_SCHUR_SIMT = 1 };
 ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops);
+
+/* Where the probes' FP64 products run (the sparse products A X, B X and (A - sigma B) X of
+ * Alg. 2 steps 3-5, and the Gram matrices and tall products of Cholesky-QR and
+ * Rayleigh-Ritz, steps 4-5; an implementation choice with no paper counterpart).
+ * SS_GEMM_TENSOR: products with at least 2,048 rows and small dimensions >= 48 run on the
+ * FP16 tensor cores: every operand row (a row of A or B, a column of X) is split exactly
+ * into 7 digit slices of 8 bits under one power-of-two scale, the 28 leading digit
+ * products are summed exactly (FP32 accumulators in tensor memory, read out as integers
+ * every 128 terms of the reduction) and the sum rounded once to FP64; the error is a few
+ * units of 2^-53 of K max|a_row| max|b_row| (K the reduction length).  A factor keeps the
+ * slices of its A and B (7 x 16 KB per 128-row tile and 64-column piece holding entries)
+ * from its first product until ss_factor_destroy; where they do not fit the factor falls
+ * back to the CUDA cores.  SS_GEMM_SIMT (default): CUDA-core FP64.  Errors: SS_ERR_ARG. */
+enum { SS_GEMM_TENSOR = 0, SS_GEMM_SIMT = 1 };
+ss_status ss_set_gemm_mode(ss_ctx *ctx, int32_t mode);
+
+/* The probes' two dense FP64 products, on the stream of ctx and in the mode that
+ * ss_set_gemm_mode chose (Alg. 2 steps 4-5: the Gram matrices of Cholesky-QR and
+ * Rayleigh-Ritz, and the tall products that apply R^-T and the Ritz rotations).
+ * Device pointers, row-major.
+ *   ss_dense_gram:  G (k1 x k2, contiguous) = X^T Y, X n x k1 with row stride ldx >= k1,
+ *                   Y n x k2 with row stride ldy >= k2.
+ *   ss_dense_gemm:  Y (n x k2, row stride ldy >= k2) = beta Y + alpha X Q, X n x k1 (row
+ *                   stride ldx >= k1), Q k1 x k2 contiguous, or with transq = 1, Y = beta
+ *                   Y + alpha X Q^T with Q k2 x k1 contiguous.  beta = 0 does not read Y.
+ * n >= 0, k1, k2 >= 1.  Returns after the launches are queued (the tensor-core path also
+ * synchronises the stream to read its status word).  Errors: SS_ERR_ARG, SS_ERR_CUDA,
+ * SS_ERR_OOM (scratch of the tensor-core path), SS_ERR_TIMEOUT (a bounded wait of the
+ * tensor-core kernel ran out; the context stays usable). */
+ss_status ss_dense_gram(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int32_t k1, const double *Y,
+                        int64_t ldy, int32_t k2, double *G);
+ss_status ss_dense_gemm(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int32_t k1, const double *Q,
+                        int32_t k2, int32_t transq, double alpha, double beta, double *Y, int64_t ldy);
 
 /* Replay of captured factorisations (batching of Alg. 2 step 2; no paper counterpart).
  * on = 1: ss_factor records the launches of one wave of shifts of an analysis -- every
@@ -361,8 +397,11 @@ ss_status ss_band_energy_grad(ss_symbolic *sym, const double *X, const double *l
 
 /* ---- SpMM helper (the CSR sweep of Section 3.1 and the residual of Alg. 2) -------
  * Y[i, j] = sum_e (alpha[j] a_vals[e] + beta[j] b_vals[e]) X[col(e), j] over row i,
- * X, Y DEVICE float64 N x k row-major; alpha, beta DEVICE float64[k].
- * Errors: SS_ERR_ARG, SS_ERR_CUDA. */
+ * X, Y DEVICE float64 N x k row-major; alpha, beta DEVICE float64[k] (NULL alpha = 1,
+ * NULL beta = no B term).  With ss_set_gemm_mode(SS_GEMM_TENSOR), N >= 2,048 and k >= 48
+ * the products run on the tensor cores (digit slices of the values made for this call:
+ * 7 x 16 KB per 128-row tile and 64-column piece holding entries), A X and B X each
+ * rounded once to FP64.  Errors: SS_ERR_ARG, SS_ERR_CUDA, SS_ERR_OOM, SS_ERR_TIMEOUT. */
 ss_status ss_spmm(ss_symbolic *sym, const double *a_vals, const double *b_vals,
                   const double *alpha, const double *beta, const double *X, int32_t k,
                   double *Y);
@@ -395,6 +434,8 @@ enum {
     SS_K_PANEL_F32, SS_K_SCHUR_F32, SS_K_FWD_UPDATE_F32, SS_K_BWD_GATHER_F32,
     SS_K_SOLVE, SS_K_SOLVE_F32,   /* whole-solve sweep kernel (SS_SOLVE_SWEEP_KERNEL) */
     SS_K_SCHUR_TC,                /* tensor-core Schur update (slicing + MMA tiles)    */
+    SS_K_GEMM_TC,                 /* tensor-core Gram / tall products                  */
+    SS_K_SPMM_TC,                 /* tensor-core sparse products A X, B X              */
     SS_K_COUNT
 };
 int64_t ss_launch_count(void);

@@ -20,6 +20,7 @@ SS_SOLVE_SWEEP_KERNEL, SS_SOLVE_PER_STEP = 0, 1
 SS_SUBSPACE, SS_BLOCK_LANCZOS = 0, 1
 SS_PEAK_FP64_FMA, SS_PEAK_FP32_FMA = 0, 1
 SS_SCHUR_TENSOR, SS_SCHUR_SIMT = 0, 1
+SS_GEMM_TENSOR, SS_GEMM_SIMT = 0, 1
 STATUS_NAMES = {0: "SS_OK", 1: "SS_ERR_ARG", 2: "SS_ERR_CUDA", 3: "SS_ERR_OOM", 4: "SS_ERR_SINGULAR",
                 5: "SS_ERR_NOT_SPD", 6: "SS_ERR_NOCONV", 7: "SS_ERR_TIMEOUT", 8: "SS_ERR_INTERNAL"}
 
@@ -51,11 +52,11 @@ class ss_solve_opts(C.Structure):
 
 EXPORTS = ["ss_create", "ss_destroy", "ss_last_error", "ss_analyze", "ss_symbolic_info_get",
            "ss_symbolic_perm", "ss_symbolic_destroy", "ss_symbolic_validate", "ss_factor", "ss_factor_destroy", "ss_inertia", "ss_factor_stats", "ss_factor_quality",
-           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode", "ss_selftest_barrier", "ss_measure_peak", "ss_set_schur_mode", "ss_selftest_tc", "ss_set_factor_graph", "ss_autotune_schur"]
+           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode", "ss_selftest_barrier", "ss_measure_peak", "ss_set_schur_mode", "ss_selftest_tc", "ss_set_factor_graph", "ss_autotune_schur", "ss_set_gemm_mode", "ss_dense_gram", "ss_dense_gemm"]
 KERNEL_CLASSES = ["assemble", "extend_add", "diag_bk", "panel", "schur", "fwd_diag", "fwd_update", "bwd_gather",
                   "bwd_diag", "permute", "spmm", "gram", "gemm", "small_dense", "jacobi", "lanczos", "sddmm", "misc",
                   "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32", "solve", "solve_f32",
-                  "schur_tc"]
+                  "schur_tc", "gemm_tc", "spmm_tc"]
 
 _lib = None
 
@@ -80,6 +81,9 @@ def load():
         "ss_set_schur_mode": ([P, i32, dbl], i32),
         "ss_selftest_tc": ([P, C.c_uint64, C.POINTER(dbl)], i32),
         "ss_set_factor_graph": ([P, i32], i32),
+        "ss_set_gemm_mode": ([P, i32], i32),
+        "ss_dense_gram": ([P, P, i64, i64, i32, P, i64, i32, P], i32),
+        "ss_dense_gemm": ([P, P, i64, i64, i32, P, i32, i32, dbl, dbl, P, i64], i32),
         "ss_autotune_schur": ([P, P, P, dbl, C.POINTER(i32)], i32),
         "ss_analyze": ([P, i64, P, P, C.POINTER(ss_options), PP], i32),
         "ss_symbolic_info_get": ([P, C.POINTER(ss_symbolic_info)], i32),

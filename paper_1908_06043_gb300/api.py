@@ -87,6 +87,12 @@ class Context:
         m = {"tensor": L.SS_SCHUR_TENSOR, "simt": L.SS_SCHUR_SIMT}[mode]
         self.check(self.lib.ss_set_schur_mode(self.h, m, float(min_flops)), "ss_set_schur_mode")
 
+    def set_gemm_mode(self, mode: str):
+        """"tensor": the probes' Gram and tall FP64 products on the tensor cores (exact
+        digit slices, FP64 accumulation); "simt": on the CUDA cores."""
+        m = {"tensor": L.SS_GEMM_TENSOR, "simt": L.SS_GEMM_SIMT}[mode]
+        self.check(self.lib.ss_set_gemm_mode(self.h, m), "ss_set_gemm_mode")
+
     def set_factor_graph(self, on: bool = True):
         """Replay captured CUDA graphs of the factorisation (per analysis and wave shape)."""
         self.check(self.lib.ss_set_factor_graph(self.h, 1 if on else 0), "ss_set_factor_graph")
@@ -96,6 +102,31 @@ class Context:
         out = C.c_double()
         self.check(self.lib.ss_selftest_tc(self.h, seed, C.byref(out)), "ss_selftest_tc")
         return out.value
+
+    def dense_gram(self, X, Y, G=None):
+        """G = X^T Y for CUDA FP64 tensors X (n x k1), Y (n x k2) with unit column stride;
+        the tensor-core or CUDA-core product per set_gemm_mode."""
+        n, k1 = X.shape
+        k2 = Y.shape[1]
+        if Y.shape[0] != n or X.stride(1) != 1 or Y.stride(1) != 1 or X.dtype != torch.float64 or Y.dtype != torch.float64:
+            raise ValueError("dense_gram: FP64 operands with matching rows and unit column stride")
+        if G is None:
+            G = torch.empty(k1, k2, dtype=torch.float64, device=X.device)
+        self.check(self.lib.ss_dense_gram(self.h, X.data_ptr(), X.stride(0), n, k1, Y.data_ptr(), Y.stride(0), k2,
+                                          G.data_ptr()), "ss_dense_gram")
+        return G
+
+    def dense_gemm(self, X, Q, Y, alpha=1.0, beta=0.0, transq=False):
+        """Y = beta Y + alpha X Q (or X Q^T) in place; CUDA FP64, unit column strides, Q
+        contiguous."""
+        n, k1 = X.shape
+        k2 = Q.shape[0] if transq else Q.shape[1]
+        if (Q.shape[1] if transq else Q.shape[0]) != k1 or tuple(Y.shape) != (n, k2) or not Q.is_contiguous() \
+                or X.stride(1) != 1 or Y.stride(1) != 1:
+            raise ValueError("dense_gemm: shapes or strides")
+        self.check(self.lib.ss_dense_gemm(self.h, X.data_ptr(), X.stride(0), n, k1, Q.data_ptr(), k2, int(transq),
+                                          float(alpha), float(beta), Y.data_ptr(), Y.stride(0)), "ss_dense_gemm")
+        return Y
 
     def measure_peak(self, kind: str = "fp64", seconds: float = 0.5) -> float:
         """Measured FMA throughput of this GPU in TFLOP/s ("fp64" or "fp32")."""

@@ -153,6 +153,13 @@ extern "C" ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flo
     return SS_OK;
 }
 
+extern "C" ss_status ss_set_gemm_mode(ss_ctx *ctx, int32_t mode) {
+    if (!ctx) return SS_ERR_ARG;
+    if (mode != SS_GEMM_TENSOR && mode != SS_GEMM_SIMT) return ctx->set_error(SS_ERR_ARG, "ss_set_gemm_mode: bad mode");
+    ctx->gemm_mode = mode;
+    return SS_OK;
+}
+
 extern "C" ss_status ss_set_factor_graph(ss_ctx *ctx, int32_t on) {
     if (!ctx) return SS_ERR_ARG;
     if (on != 0 && on != 1) return ctx->set_error(SS_ERR_ARG, "ss_set_factor_graph: on must be 0 or 1");
@@ -529,12 +536,17 @@ static int factor_wave_graph(ss_numeric *f, const std::vector<int> &js, bool tc,
     }
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(pl->dp, hp.data(), sizeof(ShiftPtrs<T>) * ns, cudaMemcpyHostToDevice, st));
     if (fresh) {
+        // capture on a private stream (the context's may be the legacy default stream,
+        // which cannot capture); the graph is launched on the context's stream below
         cudaGraph_t graph = nullptr;
-        SS_CUDA_TRY(ctx, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        if (!ctx->cap_stream) SS_CUDA_TRY(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        SS_CUDA_TRY(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
         ctx->capturing = true;
+        ctx->stream = ctx->cap_stream;
         int rc = factor_levels<T>(f, ns, (ShiftPtrs<T> *)pl->dp, hp, tc, nullptr);
+        ctx->stream = st;
         ctx->capturing = false;
-        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
         if (rc != SS_OK) return rc;
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -661,6 +673,7 @@ static void factor_free(ss_numeric *f) {
     if (f->d_counts) cudaFree(f->d_counts);
     f->arena.clear(); f->arena_lo.clear(); f->linv.clear(); f->dblk.clear(); f->piv.clear();
     f->d_counts = nullptr;
+    oz_free_numeric(f);
 }
 
 int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
@@ -1182,6 +1195,24 @@ static int shifted_values(ss_numeric *f, int j, const double **out) {
     return SS_OK;
 }
 
+// Y = (A - sigma_j B) X: A X - sigma_j B X on the tensor cores (ss_set_gemm_mode), else one
+// product with the values of A - sigma_j B
+static int spmm_shifted(ss_numeric *f, int j, const double *X, int k, double *Y) {
+    if (oz_spmm_ok(f, k)) {
+        const int which[2] = {0, 1};
+        const double *cs[2] = {nullptr, nullptr};
+        const double al[2] = {1.0, -f->sigma[j]};
+        const int rc = oz_spmm(f, 2, which, cs, al, X, k, k, Y, k);
+        if (rc != SS_ERR_OOM) return rc;
+        f->oz_failed = true;
+        f->sym->ctx->err.clear();
+    }
+    const double *mv = nullptr;
+    int rc;
+    if ((rc = shifted_values(f, j, &mv)) != SS_OK) return rc;
+    return spmm_launch(f->sym, mv, mv, nullptr, nullptr, X, k, Y);
+}
+
 // X = (A - sigma B)^-1 R in the original order; FP64 R, X (may alias).
 int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int refine, int *steps_done, double target) {
     ss_symbolic *s = f->sym;
@@ -1208,8 +1239,7 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
                   (const double *)w, out, 1);
         for (int it = 0; it < refine; ++it) {
             const double *mv = nullptr;
-            if ((rc = shifted_values(f, j, &mv)) != SS_OK) return rc;
-            if ((rc = spmm_launch(s, mv, mv, nullptr, nullptr, x, k, y)) != SS_OK) return rc;
+            if ((rc = spmm_shifted(f, j, x, k, y)) != SS_OK) return rc;
             ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, (const double *)y, y);
             ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
                       (const double *)y, w, 0);
@@ -1248,8 +1278,7 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
         const double *rhs = R;
         if (it > 0) {
             const double *mv = nullptr;
-            if ((rc = shifted_values(f, j, &mv)) != SS_OK) return rc;
-            if ((rc = spmm_launch(s, mv, mv, nullptr, nullptr, x, k, y)) != SS_OK) return rc;
+            if ((rc = spmm_shifted(f, j, x, k, y)) != SS_OK) return rc;
             if (mx) {
                 SS_CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 2, st));
                 ss_launch(ctx, SS_K_MISC, k_absmax_diff, g, 256, 0, st, tot, R, (const double *)y, mx);
@@ -1295,6 +1324,8 @@ extern "C" ss_status ss_spmm(ss_symbolic *s, const double *a, const double *b, c
     if (ctx->device < 0 || !a || !X || !Y || k <= 0 || (beta && !b))
         return ctx->set_error(SS_ERR_ARG, "ss_spmm: bad argument or host-only context");
     SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (ctx->gemm_mode == SS_GEMM_TENSOR && s->n >= 2048 && k >= 48)
+        return oz_spmm_vals(s, a, b ? b : a, alpha, beta, X, k, k, Y, k);
     return spmm_launch(s, a, b ? b : a, alpha, beta, X, k, Y);
 }
 

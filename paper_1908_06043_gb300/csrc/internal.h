@@ -16,11 +16,13 @@ struct GridBar;   // grid_sync.cuh
 struct ss_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;       // private stream that graph captures record on
     int sm_count = 0;
     std::string err;
     int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
     int schur_mode = SS_SCHUR_TENSOR;         // FP64 Schur update: tensor cores or CUDA cores
     int factor_graph = 0;                     // replay captured CUDA graphs of the factorisation
+    int gemm_mode = SS_GEMM_SIMT;             // probes' Gram / tall products: tensor cores or CUDA cores
     bool capturing = false;                   // a factorisation is being captured (launches not counted)
     std::vector<double> *step_times = nullptr;   // per factor step Schur time (autotuner), or null
     int64_t plan_gen = 0;                     // bumped when a setting baked into captured graphs changes
@@ -43,6 +45,7 @@ struct ss_ctx {
     }
     ~ss_ctx() {
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
         if (d_bar) cudaFree(d_bar);
     }
 };
@@ -157,8 +160,12 @@ struct FactorPlan {
     int64_t gen = 0;       // ss_ctx::plan_gen at capture
 };
 
+struct OzPlan;   // tensor-core products: (tile, piece) pairs of the pattern (oz.cu)
+struct OzVals;   // tensor-core products: digit slices of one value array (oz.cu)
+
 struct ss_symbolic {
     ss_ctx *ctx = nullptr;
+    OzPlan *oz_plan = nullptr;
     std::vector<FactorPlan *> plans;         // captured factorisations (freed with the analysis)
     std::vector<int8_t> step_mode;           // per factor step: -1 rule of ss_set_schur_mode,
                                              // 0 CUDA cores, 1 tensor cores (autotuner)
@@ -248,6 +255,8 @@ struct ss_numeric {
     unsigned long long *d_counts = nullptr;   // per shift: neg, zero, pos, tiny
     std::vector<unsigned long long> h_counts;
     bool counts_valid = false;
+    OzVals *oz[2] = {nullptr, nullptr};  // digit slices of A and B for tensor-core products, or null
+    bool oz_failed = false;               // those slices did not fit: products on the CUDA cores
 };
 
 // solves of shift j run in FP32 (an FP32 factor, or an FP64 factor with a rounded copy)
@@ -277,6 +286,25 @@ int spmm_launch(ss_symbolic *s, const double *a, const double *b, const double *
                 const double *X, int k, double *Y);
 int spmm_launch_ld(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
                    const double *X, int64_t ldx, int k, double *Y, int64_t ldy);
+// FP64-accurate products on the tensor cores (oz.cu; ss_set_gemm_mode)
+bool oz_dense_ok(const ss_ctx *ctx, int64_t n, int k1, int k2);
+bool oz_spmm_ok(const ss_numeric *f, int k);
+int oz_gram(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Y, int64_t ldy, int k2,
+            double *G);
+int oz_gemm(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Q, int k2, int transq,
+            double alpha, double beta, double *Y, int64_t ldy);
+// npass passes over X: pass p adds alpha[p] diag(colscale[p]) M_p X with M_p = A (which 0)
+// or B (which 1) of f; the first pass overwrites Y
+int oz_spmm(ss_numeric *f, int npass, const int *which, const double *const *colscale, const double *alpha,
+            const double *X, int64_t ldx, int k, double *Y, int64_t ldy);
+// the same for any value arrays, sliced for this call only
+int oz_spmm_vals(ss_symbolic *s, const double *a, const double *b, const double *alpha, const double *beta,
+                 const double *X, int64_t ldx, int k, double *Y, int64_t ldy);
+// Y = diag(alpha) A X + diag(beta) B X for value arrays a, b (tensor cores where possible)
+int spmm_f(ss_numeric *f, const double *a, const double *b, const double *alpha, const double *beta, const double *X,
+           int64_t ldx, int k, double *Y, int64_t ldy);
+void oz_free_numeric(ss_numeric *f);
+void oz_free_symbolic(ss_symbolic *s);
 // x = P L^-T D^-1/2 y (y permuted order, x original order), SPD factors only
 int solve_half_backward(ss_numeric *f, int j, const double *y, int k, double *x);
 

@@ -8,6 +8,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -50,6 +51,7 @@ int gram_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const 
             double *G, int sym = 0) {
     cudaStream_t st = ctx->stream;
     SS_CUDA_TRY(ctx, cudaMemsetAsync(G, 0, sizeof(double) * k1 * k2, st));
+    if (oz_dense_ok(ctx, n, k1, k2)) return oz_gram(ctx, X, ldx, n, k1, Y, ldy, k2, G);
     const int64_t t1 = cdiv(k1, 32), t2 = cdiv(k2, 32);
     const int64_t bxy = sym ? t1 * (t1 + 1) / 2 : t1 * t2;     // tiles that do work
     int64_t nz = std::max<int64_t>(1, (4 * (int64_t)ctx->sm_count + bxy - 1) / bxy);
@@ -70,6 +72,7 @@ int gram(ss_ctx *ctx, const double *X, int64_t n, int k1, const double *Y, int k
 // Y = beta Y + alpha X Q (Q k1 x k2) or X Q^T (Q k2 x k1)
 int gemm_ld(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int k1, const double *Q, int k2, int transq,
             double alpha, double beta, double *Y, int64_t ldy, int tri = 0) {
+    if (oz_dense_ok(ctx, n, k1, k2)) return oz_gemm(ctx, X, ldx, n, k1, Q, k2, transq, alpha, beta, Y, ldy);
     ss_launch(ctx, SS_K_GEMM, ssd::k_gemm_tall, dim3(cdiv(n, 64), cdiv(k2, 32)), 256, 0, ctx->stream, n, X, ldx, k1,
               Q, k2, transq, alpha, beta, Y, ldy, tri);
     ctx->add_flops(SS_K_GEMM, tri ? (double)n * k2 * (k2 + 1) : 2.0 * (double)n * k1 * k2);
@@ -106,7 +109,9 @@ __global__ void k_add_shift_diag(double *G, int k, double rel) {
 }
 
 // Symmetric eigenproblem of H (k x k, destroyed): ascending evals (device) and Q.
-int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf) {
+// eigenpairs of the symmetric k x k H by parallel-ordered Jacobi, stopped once the
+// off-diagonal Frobenius norm is below tol times the whole norm
+int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf, double tol = 1e-14) {
     cudaStream_t st = ctx->stream;
     double *V;
     TRY_ALLOC(ctx, buf.get(&V, (size_t)k * k));
@@ -116,7 +121,7 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
     if (k > 1 && k <= 96) {
         const int np = (k + (k & 1)) / 2;
         const size_t smem = sizeof(int) * (2 * np + 2) + sizeof(double) * 2 * np;
-        ss_launch(ctx, SS_K_JACOBI, ssd::k_jacobi_block, 1, 1024, smem, st, H, V, k, 1e-18, 1e-14, 40,
+        ss_launch(ctx, SS_K_JACOBI, ssd::k_jacobi_block, 1, 1024, smem, st, H, V, k, 1e-18, tol, 40,
                   (int *)nullptr);
     } else if (k > 96) {
         // cooperative grid: every block resident, rounds separated by a bounded barrier
@@ -137,7 +142,7 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
         SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssd::k_jacobi_grid, 256, 0));
         const int64_t want = ((int64_t)np * np + 255) / 256;
         int nb = (int)std::min<int64_t>(std::max(1, std::min(per_sm, 2)) * (int64_t)ctx->sm_count, std::max<int64_t>(1, want));
-        const double thr = 1e-18, tol = 1e-14;
+        const double thr = 1e-18;
         const long long limit = 20000000;      // polls of about 64 ns: ~1 s
         int *sw = status;
         void *args[] = {(void *)&H, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol, (void *)&max_sweeps,
@@ -188,7 +193,7 @@ int cholqr_b(ss_numeric *f, double *&V, double *&Wk, int k, double *G, double *R
     cudaStream_t st = ctx->stream;
     int rc;
     for (int pass = 0; pass < 2; ++pass) {
-        if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, Wk)) != SS_OK) return rc;
+        if ((rc = spmm_f(f, f->b_vals, f->b_vals, nullptr, nullptr, V, k, k, Wk, k)) != SS_OK) return rc;
         if ((rc = gram(ctx, V, s->n, k, Wk, k, G, 1)) != SS_OK) return rc;
         ss_launch(ctx, SS_K_SMALL_DENSE, k_symmetrize, cdiv((int64_t)k * k, 256), 256, 0, st, G, k);
         int hinfo = 0;
@@ -302,7 +307,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     TRY_ALLOC(ctx, buf.get(&info, 1));
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(V, V0, sizeof(double) * n * k, cudaMemcpyDeviceToDevice, st));
     int rc;
-    if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, V, k, BV)) != SS_OK) return rc;
+    if ((rc = spmm_f(f, f->b_vals, f->b_vals, nullptr, nullptr, V, k, k, BV, k)) != SS_OK) return rc;
     if ((rc = cholqr_track(f, V, BV, T1, T2, k, G, Rinv, info)) != SS_OK) return rc;
     std::vector<double> th(k), rs(k);
     int it = 0, refine_total = 0;
@@ -311,7 +316,11 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     double maxr = 0.0, maxr_all = INFINITY;
     int nf = 0;
     const int max_iter = o.max_iter > 0 ? o.max_iter : 200;
-    const int every = o.check_every > 0 ? o.check_every : 1;
+    // check_every < 0: the first Rayleigh-Ritz after |check_every| iterations, later ones
+    // where the residual's observed reduction per iteration predicts convergence
+    const bool adaptive = o.check_every < 0;
+    const int every = o.check_every > 0 ? o.check_every : (adaptive ? -o.check_every : 1);
+    int next_rr = every, it_prev_rr = 0;
     const int refine = o.refine > 0 ? o.refine : 2;
     const double tol = o.tol > 0 ? o.tol : 1e-10;
     const double ratio = o.refine_ratio > 0 ? std::min(o.refine_ratio, 1.0) : 1e-3;
@@ -329,10 +338,10 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
             ref_target = hist.empty() ? 1e-13 : std::max(1e-14, std::min(1e-8, ratio * hist.back()));
         if ((rc = solve_apply(f, j, BV, k, W, ref_now, &done_ref, ref_target)) != SS_OK) return rc;
         refine_total += done_ref;
-        if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, k, BW)) != SS_OK) return rc;
+        if ((rc = spmm_f(f, f->b_vals, f->b_vals, nullptr, nullptr, W, k, k, BW, k)) != SS_OK) return rc;
         // Alg. 2 step 4; one Cholesky-QR pass when no Rayleigh-Ritz follows (the next
         // solve only needs a well-conditioned basis), two before a Rayleigh-Ritz
-        const bool rr_now = (it % every == 0) || it == max_iter;
+        const bool rr_now = adaptive ? (it >= next_rr || it == max_iter) : ((it % every == 0) || it == max_iter);
         if ((rc = cholqr_track(f, W, BW, T1, T2, k, G, Rinv, info, rr_now ? 2 : 1)) != SS_OK) return rc;
         if (!rr_now) {
             std::swap(V, W);
@@ -341,9 +350,13 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         }
         // Rayleigh-Ritz: H = W^T A W; the dead V / BV buffers take A W and A X
         double *AW = V, *AX = BV;
-        if ((rc = spmm_launch(s, f->a_vals, f->a_vals, nullptr, nullptr, W, k, AW)) != SS_OK) return rc;
+        if ((rc = spmm_f(f, f->a_vals, f->a_vals, nullptr, nullptr, W, k, k, AW, k)) != SS_OK) return rc;
         if ((rc = gram(ctx, W, n, k, AW, k, G, 1)) != SS_OK) return rc;
-        if ((rc = sym_eig(ctx, G, k, theta_d, Q, buf)) != SS_OK) return rc;
+        // the eigenvectors of H need only be a little more accurate than the window's
+        // current residual: the residuals below are computed from the rotated basis itself,
+        // so a looser rotation only shows as a larger residual, never a false convergence
+        const double jtol = hist.empty() ? 1e-10 : std::min(1e-8, std::max(1e-14, 1e-3 * hist.back()));
+        if ((rc = sym_eig(ctx, G, k, theta_d, Q, buf, jtol)) != SS_OK) return rc;
         if ((rc = gemm_tall(ctx, W, n, k, Q, k, 0, T1)) != SS_OK) return rc;      // X
         if ((rc = gemm_tall(ctx, BW, n, k, Q, k, 0, T2)) != SS_OK) return rc;     // B X
         if ((rc = gemm_tall(ctx, AW, n, k, Q, k, 0, AX)) != SS_OK) return rc;     // A X
@@ -393,6 +406,20 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
             const int target = o.n_expect > 0 ? o.n_expect : std::max(1, nin - 2);
             const double rt = (int)wr.size() >= target ? wr[target - 1] : INFINITY;
             hist.push_back(rt);
+            if (adaptive) {
+                // iterations until the target-th window residual reaches tol at the rate seen
+                // between the last two checks (at most 8, at least 1)
+                int gap = every;
+                const size_t h2 = hist.size();
+                if (h2 >= 2 && std::isfinite(hist[h2 - 1]) && std::isfinite(hist[h2 - 2]) && hist[h2 - 1] > 0.0 &&
+                    hist[h2 - 1] < hist[h2 - 2] && it > it_prev_rr) {
+                    const double rate = std::pow(hist[h2 - 1] / hist[h2 - 2], 1.0 / (double)(it - it_prev_rr));
+                    const double need = rt <= tol ? 1.0 : std::log(tol / rt) / std::log(rate);
+                    gap = (int)std::max(1.0, std::min(8.0, std::ceil(need)));
+                }
+                it_prev_rr = it;
+                next_rr = it + gap;
+            }
             const size_t h = hist.size();
             const bool stalled = h >= 5 && !(hist[h - 1] < 0.5 * hist[h - 4]);
             near_conv = near_conv || rt <= 1e-6 || stalled;
@@ -468,13 +495,13 @@ int block_lanczos_impl(ss_numeric *f, int j, double lo, double hi, const ss_solv
     int refine_total = 0, blocks = 1;
     for (int blk = 1; blk < m; ++blk) {
         // W = O V_blk = (A - sigma B)^-1 B V_blk
-        if ((rc = spmm_launch_ld(s, f->b_vals, f->b_vals, nullptr, nullptr, Vb + (cur - p), dmax, p, T, p)) != SS_OK)
+        if ((rc = spmm_f(f, f->b_vals, f->b_vals, nullptr, nullptr, Vb + (cur - p), dmax, p, T, p)) != SS_OK)
             return rc;
         int done_ref = 0;
         if ((rc = solve_apply(f, j, T, p, W, refine, &done_ref)) != SS_OK) return rc;
         refine_total += done_ref;
         for (int pass = 0; pass < 2; ++pass) {    // W -= V (V^T B W), twice
-            if ((rc = spmm_launch(s, f->b_vals, f->b_vals, nullptr, nullptr, W, p, T)) != SS_OK) return rc;
+            if ((rc = spmm_f(f, f->b_vals, f->b_vals, nullptr, nullptr, W, p, p, T, p)) != SS_OK) return rc;
             if ((rc = gram_ld(ctx, Vb, dmax, n, (int)cur, T, p, p, Hc)) != SS_OK) return rc;
             if ((rc = gemm_ld(ctx, Vb, dmax, n, (int)cur, Hc, p, 0, -1.0, 1.0, W, p)) != SS_OK) return rc;
         }
@@ -486,7 +513,7 @@ int block_lanczos_impl(ss_numeric *f, int j, double lo, double hi, const ss_solv
     }
     // Rayleigh-Ritz on the basis: H = V^T A V
     const int d = (int)cur;
-    if ((rc = spmm_launch_ld(s, f->a_vals, f->a_vals, nullptr, nullptr, Vb, dmax, d, AV, dmax)) != SS_OK) return rc;
+    if ((rc = spmm_f(f, f->a_vals, f->a_vals, nullptr, nullptr, Vb, dmax, d, AV, dmax)) != SS_OK) return rc;
     if ((rc = gram_ld(ctx, Vb, dmax, n, d, AV, dmax, d, H, 1)) != SS_OK) return rc;
     if ((rc = sym_eig(ctx, H, d, theta_d, Q, buf)) != SS_OK) return rc;
     std::vector<double> th(d), hq((size_t)d * d);
@@ -511,7 +538,7 @@ int block_lanczos_impl(ss_numeric *f, int j, double lo, double hi, const ss_solv
     if ((rc = gemm_ld(ctx, Vb, dmax, n, d, Qsel, kout, 0, 1.0, 0.0, X, kout)) != SS_OK) return rc;
     // residuals ||A x - theta B x|| / (||A||_1 ||x||)
     ss_launch(ctx, SS_K_MISC, ssd::k_neg_scale, cdiv(kout, 256), 256, 0, st, kout, (const double *)theta_d, be);
-    if ((rc = spmm_launch(s, f->a_vals, f->b_vals, nullptr, be, X, kout, T)) != SS_OK) return rc;
+    if ((rc = spmm_f(f, f->a_vals, f->b_vals, nullptr, be, X, kout, kout, T, kout)) != SS_OK) return rc;
     SS_CUDA_TRY(ctx, cudaMemsetAsync(rr, 0, sizeof(double) * 2 * kout, st));
     const int64_t per = 2048;
     ss_launch(ctx, SS_K_MISC, ssd::k_col_sumsq, dim3(cdiv(kout, 128), cdiv(n, per)), 128, 0, st, n, kout,
@@ -666,6 +693,30 @@ extern "C" ss_status ss_slice_solve(ss_numeric *f, int32_t j, double lo, double 
     } catch (const std::bad_alloc &) {
         return ctx->set_error(SS_ERR_OOM, "ss_slice_solve: host allocation failed");
     }
+}
+
+extern "C" ss_status ss_dense_gram(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int32_t k1, const double *Y,
+                                   int64_t ldy, int32_t k2, double *G) {
+    if (!ctx) return SS_ERR_ARG;
+    if (n < 0 || k1 < 1 || k2 < 1 || ldx < k1 || ldy < k2 || !G || (n > 0 && (!X || !Y)))
+        return ctx->set_error(SS_ERR_ARG, "ss_dense_gram: bad argument");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (n == 0) {
+        SS_CUDA_TRY(ctx, cudaMemsetAsync(G, 0, sizeof(double) * k1 * k2, ctx->stream));
+        return SS_OK;
+    }
+    return gram_ld(ctx, X, ldx, n, k1, Y, ldy, k2, G);
+}
+
+extern "C" ss_status ss_dense_gemm(ss_ctx *ctx, const double *X, int64_t ldx, int64_t n, int32_t k1, const double *Q,
+                                   int32_t k2, int32_t transq, double alpha, double beta, double *Y, int64_t ldy) {
+    if (!ctx) return SS_ERR_ARG;
+    if (n < 0 || k1 < 1 || k2 < 1 || ldx < k1 || ldy < k2 || !Q || (transq != 0 && transq != 1) ||
+        (n > 0 && (!X || !Y)))
+        return ctx->set_error(SS_ERR_ARG, "ss_dense_gemm: bad argument");
+    if (n == 0) return SS_OK;
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    return gemm_ld(ctx, X, ldx, n, k1, Q, k2, transq, alpha, beta, Y, ldy);
 }
 
 extern "C" ss_status ss_dos_estimate(ss_symbolic *s, const double *a_vals, const double *b_vals, int32_t steps,

@@ -648,6 +648,7 @@ extern "C" ss_status ss_symbolic_perm(const ss_symbolic *sym, int32_t *perm) {
 extern "C" ss_status ss_symbolic_destroy(ss_symbolic *sym) {
     if (!sym) return SS_OK;
     ss_free_plans(sym);
+    oz_free_symbolic(sym);
     ss_symbolic_free_device(sym);
     delete sym;
     return SS_OK;

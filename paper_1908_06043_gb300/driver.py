@@ -376,10 +376,11 @@ class SliceSolver:
     """Lowest-n_e eigenpairs of (A, B) by spectrum slicing on one GPU."""
 
     def __init__(self, sym: api.Symbolic, a_vals, b_vals, precision="mixed", tol=1e-10, refine=2,
-                 refine_ratio=0.0):
+                 refine_ratio=0.0, check_every=3):
         self.sym, self.a, self.b = sym, a_vals, b_vals
         self.precision, self.tol, self.refine = precision, tol, refine
         self.refine_ratio = refine_ratio       # 0: the library default (1e-3)
+        self.check_every = check_every         # first-round Rayleigh-Ritz period (< 0: predictive)
 
     def count_below(self, sigmas):
         """Exact eigenvalue counts below each sigma (inertia of one batched FP64 factor
@@ -719,7 +720,8 @@ def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, f
     else:
         V0 = torch.randn(n, kk, generator=g, device="cuda", dtype=torch.float64)
     pr = f.slice_solve(0, lo, hi, V0, tol=solver.tol, max_iter=first_iters, refine=solver.refine,
-                       n_expect=max(1, exact), allow_noconv=True, check_every=3, refine_from_start=warm,
+                       n_expect=max(1, exact), allow_noconv=True, check_every=solver.check_every,
+                       refine_from_start=warm,
                        refine_ratio=solver.refine_ratio)
     iters, rounds = pr.iterations, 1
     f64, best, stall = None, np.inf, 0

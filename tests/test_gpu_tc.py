@@ -110,22 +110,26 @@ def _golden_inertia():
 @pytest.mark.parametrize("precision", ["fp64", "mixed_tc"])
 def test_factor_graph_replay_matches_launches(gpu_lib, precision):
     """A captured factorisation replayed for new shifts gives the factor the kernel-by-kernel
-    launches give (the same kernels in the same order: solves agree to the last bit)."""
+    launches give: the same inertia, and solves that agree to rounding.  The solve kernels
+    sum with atomics, so two solves with one factor already differ in the last bits; the
+    FP32 solves of the mixed factor are compared after FP64 refinement."""
     sig, neg = _golden_inertia()
     p = config_pencil(2)
     ctx, sym, a, b = setup(gpu_lib, p)
     R = torch.tensor(normal_block(p.n, 3, 4), device="cuda")
+    rf, tol = (0, 1e-10) if precision == "fp64" else (3, 1e-9)
     ref = []
     for s_ in sig[:3]:
         f = sym.factor(a, b, [s_], precision)
-        ref.append((f.inertia(0)[0], f.solve(0, R, refine=0)))
+        ref.append((f.inertia(0)[0], f.solve(0, R, refine=rf)))
         f.close()
     ctx.set_factor_graph(True)
     n0 = ctx.launch_count()
     for t, s_ in enumerate(sig[:3]):              # capture on the first, replay on the others
         f = sym.factor(a, b, [s_], precision)
         assert f.inertia(0)[0] == ref[t][0] == neg[t]
-        assert torch.equal(f.solve(0, R, refine=0), ref[t][1])
+        x = f.solve(0, R, refine=rf)
+        assert ((x - ref[t][1]).abs().max() / ref[t][1].abs().max()).item() <= tol
         f.close()
     assert ctx.launch_count() - n0 > 3 * 100      # the replayed kernels are counted
     ctx.set_factor_graph(False)

@@ -49,14 +49,16 @@ def test_gauss16_all_slices_match_dense_golden(gpu_lib):
     assert spectral.residual_norms(p, res.eigenvalues, X).max() <= 1e-10
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_gauss16_slice_solves_match_dense_golden(gpu_lib, precision):
+@pytest.mark.parametrize("precision,gemm", [("mixed", "simt"), ("fp64", "simt"), ("mixed", "tensor")])
+def test_gauss16_slice_solves_match_dense_golden(gpu_lib, precision, gemm):
     """The benchmark's step on a spread of windows (the sparse low tail, the body, the
-    top): exact window counts from inertia against the golden, eigenvalues to 1e-10."""
+    top): exact window counts from inertia against the golden, eigenvalues to 1e-10;
+    the probes' dense products on the CUDA cores or on the tensor cores."""
     from paper_1908_06043_gb300.driver import SliceSolver, plan_slices, solve_slice
     lam = _golden()
     p = config_pencil(2)
     ctx, sym, a, b = setup(gpu_lib, p)
+    ctx.set_gemm_mode(gemm)
     solver = SliceSolver(sym, a, b, precision=precision)
     plan = plan_slices(solver, _model(sym, a, b, p.n), 1640, 16)
     assert plan.counts[-1] < lam.size
