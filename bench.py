@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--profile-step", action="store_true",
                     help="profiling case: placement, one warm-up slice solve (window n_s/2 - 1), then one slice "
                          "solve (window n_s/2) inside the NVTX range 'slice_step'")
+    ap.add_argument("--product-only", default=None, choices=["tensor", "simt"],
+                    help="profiling case: the sparse products A X and B X and the Gram matrix X^T X of the "
+                         "workload, X N x 304, on the given path (three times: the last is the one to capture)")
     ap.add_argument("--factor-only", default=None, choices=["tensor", "simt"],
                     help="profiling case: one FP64 factorisation at sigma = -1 with the given Schur path "
                          "(twice: the second is the one to capture)")
@@ -285,6 +288,23 @@ def main():
     steps_dos, n_vec = 100, 4
     peak64 = ctx.measure_peak("fp64", 0.5)
     peak32 = ctx.measure_peak("fp32", 0.5)
+
+    if args.product_only:
+        ctx.set_gemm_mode(args.product_only)
+        X = torch.tensor(normal_block(p.n, 304, 77), device="cuda")
+        out = {}
+        for rep in range(3):
+            ctx.profile(api.L.KERNEL_CLASSES)
+            Y = sym.spmm(a, b, X, 1.0, -0.5)
+            G = ctx.dense_gram(X, Y)
+            torch.cuda.synchronize()
+            prof = {c: ctx.profile_query(c) for c in api.L.KERNEL_CLASSES}
+            ctx.profile(())
+            out = {c: [v[0], round(1e3 * v[1], 3), round(v[2] / v[1] / 1e12, 3) if v[1] > 0 else 0.0]
+                   for c, v in prof.items() if v[0]}
+        print(json.dumps({"product_only": args.product_only, "workload": wl["name"], "nnz": int(len(p.colind)),
+                          "classes": out, "check": float(G.abs().sum())}), flush=True)
+        return
 
     if args.factor_only:
         ctx.set_schur_mode(args.factor_only)

@@ -199,7 +199,7 @@ extern "C" ss_status ss_selftest_tc(ss_ctx *ctx, uint64_t seed, double *max_abs_
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(dA, ha.data(), sstc::kSliceBytes, cudaMemcpyHostToDevice, st));
     SS_CUDA_TRY(ctx, cudaMemcpyAsync(dB, hb.data(), sstc::kHalfSliceBytes, cudaMemcpyHostToDevice, st));
     SS_CUDA_TRY(ctx, cudaMemsetAsync(dD, 0, sizeof(float) * M * N, st));
-    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_selftest, 1, 128, sstc::kSliceBytes + sstc::kHalfSliceBytes, st,
+    ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_tc_selftest, 1, 128, sstc::kSelftestSmem, st,
               (const unsigned char *)dA, (const unsigned char *)dB, dD, dst);
     std::vector<float> D((size_t)M * N);
     int status = -1;
@@ -341,7 +341,7 @@ static void set_smem_attrs(int device) {
     if (std::is_same<T, double>::value) {
         cudaFuncSetAttribute(sstc::k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sstc::kSchurTcSmem);
         cudaFuncSetAttribute(sstc::k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sstc::kSliceBytes + sstc::kHalfSliceBytes));
+                             (int)sstc::kSelftestSmem);
     }
 }
 

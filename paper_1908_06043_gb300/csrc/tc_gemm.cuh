@@ -240,6 +240,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mm(const OzMM g) {
     tc_fence_after();
     const uint32_t tmem = s_tmem;
     const uint32_t idesc = idesc_f16_f32(128, 64);
+    const uint64_t da = smem_desc(smem_u32(sa)), db = smem_desc(smem_u32(sb));
     auto issue_loads = [&](int q) {
         const int kc = sparse ? g.pair_piece[q] : q;
         const unsigned char *ga = g.slA + (uint64_t)(sparse ? q : kc * g.nrtA + rt) * kOzSlices * kOzBlock;
@@ -264,19 +265,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_oz_mm(const OzMM g) {
                 s_ok = 0;
                 mbar_wait_bounded(&bar[0], parity, kOzWaitLimit);    // let copies in flight land
             } else {
-                const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
-                const bool fresh = (i & 1) == 0;    // accumulators restart every two pieces
-                for (int d = 0; d < kOzSlices; ++d) {
-                    bool first = fresh;
-                    for (int p = 0; p <= d; ++p) {
-                        const int qq = d - p;
-                        for (int kk = 0; kk < 4; ++kk) {
-                            mma_f16(tmem + (uint32_t)(d * 64), smem_desc(a0 + p * kOzBlock + kk * 256),
-                                    smem_desc(b0 + qq * kOzHalf + kk * 256), idesc, first ? 0u : 1u);
-                            first = false;
-                        }
-                    }
-                }
+                // accumulators restart every two pieces
+                issue_digit_mmas<kOzBlock, kOzHalf, 64>(tmem, da, db, idesc, (i & 1) == 0);
                 mma_commit(&bar[1]);
                 if (!mbar_wait_bounded(&bar[1], parity, kOzWaitLimit)) {
                     s_ok = 0;

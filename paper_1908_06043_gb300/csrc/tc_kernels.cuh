@@ -49,6 +49,7 @@ constexpr uint32_t kHalfSliceBytes = 64 * 64 * 2;           // its 64-row half
 constexpr int kAccum = kSlices;               // accumulators, one per p + q
 constexpr uint32_t kTmemCols = 512;           // 7 x 64 columns, rounded to a power of two
 constexpr size_t kSchurTcSmem = 1024 + (size_t)kSlices * kSliceBytes + (size_t)kSlices * kHalfSliceBytes;
+constexpr size_t kSelftestSmem = 1024 + (size_t)kSliceBytes + kHalfSliceBytes;
 constexpr int kSchurTcThreads = 256;          // 8 warps: lane quarter w % 4, column half w / 4
 constexpr long long kWaitLimit = 1ll << 24;   // mbarrier polls (about a second)
 
@@ -60,8 +61,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const unsigned char *__r
                                                          const unsigned char *__restrict__ B, float *D,
                                                          int *status) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *sa = smem_raw;
-    unsigned char *sb = smem_raw + kSliceBytes;
+    unsigned char *sa = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);   // swizzle atoms: 1024-aligned
+    unsigned char *sb = sa + kSliceBytes;
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_ok;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_selftest(const unsigned char *__r
         } else {
             const uint32_t idesc = idesc_f16_f32(kTileM, kTileN);
             for (int kk = 0; kk < 4; ++kk)
-                mma_f16(tmem, smem_desc(smem_u32(sa) + kk * 256), smem_desc(smem_u32(sb) + kk * 256), idesc,
+                mma_f16(tmem, smem_desc(smem_u32(sa) + kk * kKStepBytes), smem_desc(smem_u32(sb) + kk * kKStepBytes), idesc,
                         kk > 0);
             mma_commit(&bar[1]);
             if (!mbar_wait_bounded(&bar[1], 0, kWaitLimit)) s_ok = 0;
@@ -218,20 +219,9 @@ __global__ void __launch_bounds__(kSchurTcThreads, 1) k_schur_tc(const StepTask 
             s_ok = 0;
         } else {
             const uint32_t idesc = idesc_f16_f32(kTileM, kTileN);
-            const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
-            for (int d = 0; d < kAccum; ++d) {
-                bool first = true;
-                for (int p = 0; p <= d; ++p) {
-                    const int qq = d - p;                      // slices p, qq (0-based), p + qq = d
-                    if (p >= kSlices || qq >= kSlices) continue;
-                    for (int kk = 0; kk < 4; ++kk) {
-                        mma_f16(tmem + (uint32_t)(d * kTileN),
-                                smem_desc(a0 + p * kSliceBytes + kk * 256),
-                                smem_desc(b0 + qq * kHalfSliceBytes + kk * 256), idesc, first ? 0u : 1u);
-                        first = false;
-                    }
-                }
-            }
+            static_assert(kSlices == 7 && kAccum == 7, "the issue loop covers 7 slices and 7 accumulators");
+            issue_digit_mmas<kSliceBytes, kHalfSliceBytes, kTileN>(tmem, smem_desc(smem_u32(sa)),
+                                                                    smem_desc(smem_u32(sb)), idesc, true);
             mma_commit(&bar[1]);
             if (!mbar_wait_bounded(&bar[1], 0, kWaitLimit)) {
                 s_ok = 0;

@@ -2,12 +2,13 @@
 // copies (the TMA unit, global -> shared), tensor-memory allocation, tcgen05.mma of
 // kind::f16 with FP32 accumulation, commit, and tensor-memory loads.
 //
-// Operand layout in shared memory (no swizzle, K-major): a tile of R rows x 64 K-elements
-// of FP16 is stored as 8 x 8 "core matrices" of 128 contiguous bytes (8 rows x 16 bytes);
-// core matrix (row group g, K chunk c) sits at byte g * 1024 + c * 128.  In the matrix
-// descriptor the leading-dimension byte offset (between K-adjacent core matrices) is
-// 128 and the stride byte offset (between 8-row groups) is 1024; one MMA consumes K = 16,
-// i.e. two K chunks, so the K step advances the start address by 256 bytes.
+// Operand layout in shared memory (K-major, 128-byte swizzle): a tile of R rows x 64
+// K-elements of FP16 stores row r at byte r * 128, and the 16-byte chunk c (elements 8c ..
+// 8c + 7) of row r at chunk position c XOR (r mod 8) -- the layout the tensor cores read
+// without shared-memory bank conflicts.  Tiles start on 1024-byte boundaries (8 rows = one
+// swizzle atom).  In the matrix descriptor the stride byte offset (between 8-row groups) is
+// 1024 and the leading byte offset is unused; one MMA consumes K = 16 (32 bytes of a row),
+// so the K step advances the start address by 32 bytes inside the atom.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,14 +16,15 @@
 
 namespace sstc {
 
-constexpr uint32_t kCoreLbo = 128;      // bytes between K-adjacent core matrices
-constexpr uint32_t kCoreSbo = 1024;     // bytes between 8-row groups (8 K chunks per row group)
+constexpr uint32_t kCoreLbo = 16;       // unused by the swizzled K-major layout (encoded 1)
+constexpr uint32_t kCoreSbo = 1024;     // bytes between 8-row groups
 constexpr int kTileK = 64;              // K elements per operand tile
 constexpr uint32_t kRowGroupBytes = 1024;
+constexpr uint32_t kKStepBytes = 32;    // start-address advance per MMA K step of 16
 
-// byte offset of element (row, k) of an R x 64 FP16 tile in the core-matrix layout
+// byte offset of element (row, k) of an R x 64 FP16 tile in the swizzled layout
 __host__ __device__ __forceinline__ uint32_t core_offset(int row, int k) {
-    return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+    return (uint32_t)(row * 128 + ((((k >> 3) ^ row) & 7) << 4) + (k & 7) * 2);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -79,13 +81,14 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// ---- matrix descriptor of a K-major, unswizzled operand tile at shared address saddr
+// ---- matrix descriptor of a K-major, 128-byte-swizzled operand tile at shared address saddr
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
     d |= (uint64_t)((kCoreLbo >> 4) & 0x3FFFu) << 16;
     d |= (uint64_t)((kCoreSbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;     // descriptor version of the sm_100 family; layout type 0 = no swizzle
+    d |= (uint64_t)1 << 46;     // descriptor version of the sm_100 family
+    d |= (uint64_t)2 << 61;     // layout type: 128-byte swizzle
     return d;
 }
 
@@ -111,6 +114,32 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
+}
+
+// The 112 MMAs of one 64-wide piece of a digit-sliced product (7 slices per operand):
+// accumulator d (tensor-memory columns d * kNCols ..) gets sum_{p + q = d} A_p B_q^T.  da, db
+// are the descriptors of slice 0 of A and B, the slices kAStride / kBStride bytes apart.  The
+// descriptors advance by additions to the start-address field (16-byte units), a few
+// instructions per MMA, so one thread keeps the tensor pipe fed; the (d, p) loops stay
+// rolled so the 224 descriptors are not all held in registers.  fresh: the first MMA into
+// each accumulator overwrites it.
+template <uint32_t kAStride, uint32_t kBStride, uint32_t kNCols>
+__device__ __forceinline__ void issue_digit_mmas(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                                 bool fresh) {
+    const uint32_t keep_first = fresh ? 0u : 1u;
+#pragma unroll 1
+    for (int d = 0; d < 7; ++d) {
+        const uint32_t t = tmem + (uint32_t)d * kNCols;
+#pragma unroll 1
+        for (int p = 0; p <= d; ++p) {
+            const uint64_t a = da + (uint64_t)(p * (kAStride >> 4));
+            const uint64_t b = db + (uint64_t)((d - p) * (kBStride >> 4));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                mma_f16(t, a + (uint64_t)(kk * (kKStepBytes >> 4)), b + (uint64_t)(kk * (kKStepBytes >> 4)), idesc,
+                        (kk == 0 && p == 0) ? keep_first : 1u);
+        }
+    }
 }
 
 // 32 lanes x 32 bits, 16 consecutive columns per thread (warp w reads lanes 32 w .. 32 w + 31).
