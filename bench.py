@@ -54,8 +54,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "fp64"])
-    ap.add_argument("--gemm", default="simt", choices=["tensor", "simt"],
-                    help="where the probes' dense FP64 products (Gram, tall) run")
+    ap.add_argument("--gemm", default="tensor", choices=["tensor", "simt"],
+                    help="where the probes' FP64 products (sparse A X, B X; Gram; tall) run")
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end pass (default: --steps)")

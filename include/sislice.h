@@ -158,7 +158,7 @@ ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops);
 /* Where the probes' FP64 products run (the sparse products A X, B X and (A - sigma B) X of
  * Alg. 2 steps 3-5, and the Gram matrices and tall products of Cholesky-QR and
  * Rayleigh-Ritz, steps 4-5; an implementation choice with no paper counterpart).
- * SS_GEMM_TENSOR: products with at least 2,048 rows and small dimensions >= 48 run on the
+ * SS_GEMM_TENSOR (default): products with at least 2,048 rows and small dimensions >= 48 run on the
  * FP16 tensor cores: every operand row (a row of A or B, a column of X) is split exactly
  * into 7 digit slices of 8 bits under one power-of-two scale, the 28 leading digit
  * products are summed exactly (FP32 accumulators in tensor memory, read out as integers
@@ -166,7 +166,7 @@ ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops);
  * units of 2^-53 of K max|a_row| max|b_row| (K the reduction length).  A factor keeps the
  * slices of its A and B (7 x 16 KB per 128-row tile and 64-column piece holding entries)
  * from its first product until ss_factor_destroy; where they do not fit the factor falls
- * back to the CUDA cores.  SS_GEMM_SIMT (default): CUDA-core FP64.  Errors: SS_ERR_ARG. */
+ * back to the CUDA cores.  SS_GEMM_SIMT: CUDA-core FP64.  Errors: SS_ERR_ARG. */
 enum { SS_GEMM_TENSOR = 0, SS_GEMM_SIMT = 1 };
 ss_status ss_set_gemm_mode(ss_ctx *ctx, int32_t mode);
 

@@ -22,7 +22,7 @@ struct ss_ctx {
     int solve_mode = SS_SOLVE_SWEEP_KERNEL;   // how the triangular sweeps are launched
     int schur_mode = SS_SCHUR_TENSOR;         // FP64 Schur update: tensor cores or CUDA cores
     int factor_graph = 0;                     // replay captured CUDA graphs of the factorisation
-    int gemm_mode = SS_GEMM_SIMT;             // probes' Gram / tall products: tensor cores or CUDA cores
+    int gemm_mode = SS_GEMM_TENSOR;           // probes' FP64 products: tensor cores or CUDA cores
     bool capturing = false;                   // a factorisation is being captured (launches not counted)
     std::vector<double> *step_times = nullptr;   // per factor step Schur time (autotuner), or null
     int64_t plan_gen = 0;                     // bumped when a setting baked into captured graphs changes
