@@ -42,6 +42,17 @@ WORKLOADS = {
 }
 DEFAULT_WORKLOAD = "gauss16"
 METRIC = "slice solves/s at N=110,592 (mixed vs FP64, resid<=1e-10); factor TFLOP/s"
+def measured_peaks():
+    """The machine's measured HBM / BF16 peaks (MEASURED_PEAKS.json beside this file), or None."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return None
+
+
+TENSOR_CLASSES = {"schur_tc", "gemm_tc", "spmm_tc"}
 FLOP_CLASSES = {"schur", "panel", "fwd_update", "bwd_gather", "spmm", "gram", "gemm", "solve",
                 "schur_f32", "panel_f32", "fwd_update_f32", "bwd_gather_f32", "solve_f32", "schur_tc", "gemm_tc", "spmm_tc"}
 
@@ -429,6 +440,7 @@ def main():
     torch.cuda.synchronize()
     launches = ctx.launch_count() - n0
     dom_n, dom_t, dom_flops = ctx.profile_query(dom)
+    dom_tensor = ctx.profile_query_tensor(dom)
     ctx.profile(())
     clk = clocks.stop()
     barrier(ws)
@@ -492,7 +504,22 @@ def main():
     # timed region (counted by the library from the schedule) over their event time,
     # against the FMA peak measured on this GPU at the start of the run
     per_launch = dom_t / max(dom_n, 1)
-    if dom in FLOP_CLASSES and dom_t > 0:
+    fp64_equiv = None
+    if dom in TENSOR_CLASSES and dom_t > 0 and dom_tensor > 0:
+        # FP64 emulated on the FP16 tensor cores: the roofline is the tensor pipe's, with the
+        # MMA work the kernels issued (the digit-product algorithm); the FP64-equivalent rate
+        # of the same launches is reported beside it
+        achieved = dom_tensor / dom_t / 1e12
+        peaks = measured_peaks()
+        peak = peaks.get("bf16_tflops_sustained") if peaks else None
+        bound, unit = "tensor", "TFLOP/s"
+        peak_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS BF16 GEMM under the power cap; dense FP16 "
+                    "runs at the BF16 rate)") if peak else "fallback"
+        if peak is None:
+            peak = 1700.0
+        fp64_equiv = {"achieved": dom_flops / dom_t / 1e12, "unit": "TFLOP/s",
+                      "vs_fp64_fma_peak": dom_flops / dom_t / 1e12 / peak64 if peak64 else None}
+    elif dom in FLOP_CLASSES and dom_t > 0:
         achieved = dom_flops / dom_t / 1e12
         f32 = dom.endswith("_f32")
         peak = peak32 if f32 else peak64
@@ -506,6 +533,8 @@ def main():
                 "launches": dom_n, "avg_launch_ms": 1e3 * per_launch,
                 "share_of_profiled_time": prof[dom][1] / tot_prof if tot_prof else None,
                 "peak_source": peak_src}
+    if fp64_equiv:
+        roofline["fp64_equivalent"] = fp64_equiv
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:

@@ -445,6 +445,11 @@ ss_status ss_profile(ss_ctx *ctx, uint32_t mask);
  * lower triangle only for the Schur update); 0 for the others.  Classes ending in _F32 are the
  * FP32 instantiations of the mixed-precision factor and solves. */
 ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launches, double *seconds, double *flops);
+/* For the tensor-core classes (SS_K_SCHUR_TC, SS_K_GEMM_TC, SS_K_SPMM_TC): the FP16 MMA
+ * work (2 M N K per MMA, zero padding of sparse tiles included) their launches issued since
+ * the last ss_profile call; 0 for the other classes.  Call after ss_profile_query (which
+ * synchronises).  Errors: SS_ERR_ARG. */
+ss_status ss_profile_query_tensor(ss_ctx *ctx, int32_t cls, double *tensor_flops);
 
 #ifdef __cplusplus
 }

@@ -146,6 +146,13 @@ class Context:
             mask |= 1 << L.KERNEL_CLASSES.index(c)
         self.check(self.lib.ss_profile(self.h, mask), "ss_profile")
 
+    def profile_query_tensor(self, cls: str) -> float:
+        """FP16 MMA flops a tensor-core kernel class issued since profile()."""
+        out = C.c_double()
+        self.check(self.lib.ss_profile_query_tensor(self.h, L.KERNEL_CLASSES.index(cls), C.byref(out)),
+                   "ss_profile_query_tensor")
+        return out.value
+
     def profile_query(self, cls: str):
         """(launches, seconds, algorithmic flops) of a kernel class since profile()
         (synchronises)."""

@@ -60,6 +60,7 @@ extern "C" ss_status ss_profile(ss_ctx *ctx, uint32_t mask) {
         ctx->prof_launches[c] = 0;
         ctx->prof_seconds[c] = 0.0;
         ctx->prof_flops[c] = 0.0;
+        ctx->prof_tensor_flops[c] = 0.0;
     }
     ctx->prof_mask = mask;
     return SS_OK;
@@ -73,6 +74,12 @@ extern "C" ss_status ss_profile_query(ss_ctx *ctx, int32_t cls, int64_t *launche
     if (launches) *launches = ctx->prof_launches[cls];
     if (seconds) *seconds = ctx->prof_seconds[cls];
     if (flops) *flops = ctx->prof_flops[cls];
+    return SS_OK;
+}
+
+extern "C" ss_status ss_profile_query_tensor(ss_ctx *ctx, int32_t cls, double *tensor_flops) {
+    if (!ctx || cls < 0 || cls >= SS_K_COUNT || !tensor_flops) return SS_ERR_ARG;
+    *tensor_flops = ctx->prof_tensor_flops[cls];
     return SS_OK;
 }
 
@@ -424,6 +431,8 @@ static int factor_levels(ss_numeric *f, int ns, ShiftPtrs<T> *dp, const std::vec
                 ss_launch(ctx, SS_K_SCHUR_TC, sstc::k_schur_tc, dim3(sd.tc_tiles, ns), sstc::kSchurTcThreads,
                           sstc::kSchurTcSmem, st, tk, sd.count, (const ShiftPtrs<double> *)(void *)dp);
                 ctx->add_flops(SS_K_SCHUR_TC, sd.flops3 * ns);
+                // 112 MMAs of 128 x 64 x 16 per tile
+                ctx->add_tensor_flops(SS_K_SCHUR_TC, 112.0 * 2.0 * 128 * 64 * 16 * sd.tc_tiles * ns);
             } else if (sd.tiles3 > 0) {
                 const int cls = std::is_same<T, float>::value ? SS_K_SCHUR_F32 : SS_K_SCHUR;
                 ss_launch(ctx, cls, k_schur<T>, dim3(sd.tiles3, ns), 256, schur_smem<T>(), st, tk, sd.count,

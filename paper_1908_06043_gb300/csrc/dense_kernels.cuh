@@ -341,24 +341,31 @@ __global__ void __launch_bounds__(1024) k_jacobi_block(double *H, double *V, int
 using ::GridBar;
 using ::grid_barrier;
 
-// The same parallel-ordered Jacobi as k_jacobi_block, spread over a cooperative grid:
-// per round the rotations go to global scratch (pairs / cs), a grid barrier, the 2 x 2
-// block and row-pair updates over all threads, a grid barrier.  acc: 2 * max_sweeps
-// doubles (zeroed) for the per-sweep off-diagonal / total norms.
-__global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *V, int k, double thr, double tol,
-                                                     int max_sweeps, int2 *pairs, double2 *cs, double *acc,
-                                                     GridBar *bar, long long limit, int *sweeps_done) {
+// The same parallel-ordered Jacobi as k_jacobi_block, spread over a cooperative grid with
+// one grid barrier per round: H is double-buffered (round r reads Ha and writes every
+// entry of Hb, then the two swap), so each block can compute all of the round's rotations
+// itself from Ha into shared memory (np x 24 bytes of dynamic shared memory) while other
+// blocks already write Hb.  acc: 2 * max_sweeps doubles (zeroed) for the per-sweep
+// off-diagonal / total norms.  On return the matrix is in H (copied back from the scratch
+// buffer H2 when the last round left it there).
+__global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *H2, double *V, int k, double thr, double tol,
+                                                     int max_sweeps, double *acc, GridBar *bar, long long limit,
+                                                     int *sweeps_done) {
+    extern __shared__ __align__(16) unsigned char jac_smem[];
     const int kp = k + (k & 1);
     const int np = kp / 2;
+    double2 *s_cs = reinterpret_cast<double2 *>(jac_smem);
+    int2 *s_pq = reinterpret_cast<int2 *>(jac_smem + sizeof(double2) * np);
     const unsigned int nb = gridDim.x;
     const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)nb * blockDim.x;
     __shared__ double red_off[8], red_all[8];
+    double *Ha = H, *Hb = H2;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         double off = 0.0, all = 0.0;
         for (int64_t q = gtid; q < (int64_t)k * k; q += gthreads) {
-            double v = H[q] * H[q];
+            double v = Ha[q] * Ha[q];
             all += v;
             if (q / k != q % k) off += v;
         }
@@ -378,14 +385,15 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *V, int k
         const double o2 = *(volatile double *)&acc[2 * sweep], a2 = *(volatile double *)&acc[2 * sweep + 1];
         if (o2 <= tol * tol * a2) break;
         for (int r = 0; r < kp - 1; ++r) {
-            for (int64_t t = gtid; t < np; t += gthreads) {
+            // the round's rotations, from Ha, by every block
+            for (int t = threadIdx.x; t < np; t += blockDim.x) {
                 int i = (t == 0) ? kp - 1 : (int)((r + t) % (kp - 1));
                 int y = jac_partner(i, r, kp);
                 int p = min(i, y), q = max(i, y);
                 double c = 1.0, sn = 0.0;
                 if (q < k) {
-                    const double hpq = H[(int64_t)p * k + q];
-                    const double hpp = H[(int64_t)p * k + p], hqq = H[(int64_t)q * k + q];
+                    const double hpq = Ha[(int64_t)p * k + q];
+                    const double hpp = Ha[(int64_t)p * k + p], hqq = Ha[(int64_t)q * k + q];
                     if (hpq != 0.0 && fabs(hpq) > thr * sqrt(fabs(hpp * hqq))) {
                         const double th = (hqq - hpp) / (2.0 * hpq);
                         const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
@@ -393,45 +401,56 @@ __global__ void __launch_bounds__(256) k_jacobi_grid(double *H, double *V, int k
                         sn = tt * c;
                     }
                 }
-                pairs[t] = make_int2(p, q);
-                cs[t] = make_double2(c, sn);
+                s_pq[t] = make_int2(p, q);
+                s_cs[t] = make_double2(c, sn);
             }
-            if (!grid_barrier(bar, nb, limit)) return;
+            __syncthreads();
+            // Hb = J^T Ha J, every 2 x 2 block written (copied where both rotations are trivial)
             for (int64_t e = gtid; e < (int64_t)np * np; e += gthreads) {
                 const int ta = (int)(e / np), tb = (int)(e % np);
-                const double2 r1 = cs[ta], r2 = cs[tb];
+                const double2 r1 = s_cs[ta], r2 = s_cs[tb];
                 const double c1 = r1.x, s1 = r1.y, c2 = r2.x, s2 = r2.y;
-                if (s1 == 0.0 && s2 == 0.0) continue;
-                const int2 a1 = pairs[ta], a2p = pairs[tb];
+                const int2 a1 = s_pq[ta], a2p = s_pq[tb];
                 const int p1 = a1.x, q1 = a1.y, p2 = a2p.x, q2 = a2p.y;
                 const bool rq = q1 < k, cq = q2 < k;
-                double h11 = H[(int64_t)p1 * k + p2];
-                double h12 = cq ? H[(int64_t)p1 * k + q2] : 0.0;
-                double h21 = rq ? H[(int64_t)q1 * k + p2] : 0.0;
-                double h22 = (rq && cq) ? H[(int64_t)q1 * k + q2] : 0.0;
-                double x11 = c2 * h11 - s2 * h12, x12 = s2 * h11 + c2 * h12;
-                double x21 = c2 * h21 - s2 * h22, x22 = s2 * h21 + c2 * h22;
-                double b11 = c1 * x11 - s1 * x21, b21 = s1 * x11 + c1 * x21;
-                double b12 = c1 * x12 - s1 * x22, b22 = s1 * x12 + c1 * x22;
-                if (ta == tb && s1 != 0.0) { b12 = 0.0; b21 = 0.0; }
-                H[(int64_t)p1 * k + p2] = b11;
-                if (cq) H[(int64_t)p1 * k + q2] = b12;
-                if (rq) H[(int64_t)q1 * k + p2] = b21;
-                if (rq && cq) H[(int64_t)q1 * k + q2] = b22;
+                const double h11 = Ha[(int64_t)p1 * k + p2];
+                const double h12 = cq ? Ha[(int64_t)p1 * k + q2] : 0.0;
+                const double h21 = rq ? Ha[(int64_t)q1 * k + p2] : 0.0;
+                const double h22 = (rq && cq) ? Ha[(int64_t)q1 * k + q2] : 0.0;
+                double b11 = h11, b12 = h12, b21 = h21, b22 = h22;
+                if (s1 != 0.0 || s2 != 0.0) {
+                    const double x11 = c2 * h11 - s2 * h12, x12 = s2 * h11 + c2 * h12;
+                    const double x21 = c2 * h21 - s2 * h22, x22 = s2 * h21 + c2 * h22;
+                    b11 = c1 * x11 - s1 * x21;
+                    b21 = s1 * x11 + c1 * x21;
+                    b12 = c1 * x12 - s1 * x22;
+                    b22 = s1 * x12 + c1 * x22;
+                    if (ta == tb && s1 != 0.0) { b12 = 0.0; b21 = 0.0; }
+                }
+                Hb[(int64_t)p1 * k + p2] = b11;
+                if (cq) Hb[(int64_t)p1 * k + q2] = b12;
+                if (rq) Hb[(int64_t)q1 * k + p2] = b21;
+                if (rq && cq) Hb[(int64_t)q1 * k + q2] = b22;
             }
+            // V = V J (each entry updated by exactly one thread per round)
             for (int64_t e = gtid; e < (int64_t)k * np; e += gthreads) {
                 const int row = (int)(e / np), tb = (int)(e % np);
-                const double2 r2 = cs[tb];
+                const double2 r2 = s_cs[tb];
                 if (r2.y == 0.0) continue;
-                const int2 a2p = pairs[tb];
+                const int2 a2p = s_pq[tb];
                 double *vr = V + (int64_t)row * k;
                 const double vp = vr[a2p.x], vq = vr[a2p.y];
                 vr[a2p.x] = r2.x * vp - r2.y * vq;
                 vr[a2p.y] = r2.y * vp + r2.x * vq;
             }
             if (!grid_barrier(bar, nb, limit)) return;
+            double *t = Ha;
+            Ha = Hb;
+            Hb = t;
         }
     }
+    if (Ha != H)
+        for (int64_t q = gtid; q < (int64_t)k * k; q += gthreads) H[q] = Ha[q];
     if (gtid == 0 && sweeps_done) *sweeps_done = sweep;
 }
 

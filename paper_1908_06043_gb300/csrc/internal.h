@@ -36,6 +36,10 @@ struct ss_ctx {
     int64_t prof_launches[SS_K_COUNT] = {};
     double prof_seconds[SS_K_COUNT] = {};
     double prof_flops[SS_K_COUNT] = {};
+    double prof_tensor_flops[SS_K_COUNT] = {};   // FP16 MMA work the tensor-core classes issued
+    void add_tensor_flops(int cls, double f) {
+        if (prof_mask & (1u << cls)) prof_tensor_flops[cls] += f;
+    }
     void add_flops(int cls, double f) {
         if (prof_mask & (1u << cls)) prof_flops[cls] += f;
     }

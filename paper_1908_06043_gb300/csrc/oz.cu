@@ -27,6 +27,9 @@ using sstc::OzOperand;
 
 inline unsigned cdivu(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
+// FP16 MMA work of one (output tile, piece): 36 digit products x 2 K steps of 128 x 64 x 16
+constexpr double kPieceTensorFlops = 36.0 * 2.0 * 2.0 * 128 * 64 * 16;
+
 // per-call device scratch from the stream-ordered pool
 struct Scratch {
     std::vector<void *> ptrs;
@@ -67,8 +70,8 @@ void oz_attrs(int device) {
 
 // exponents and digit slices of a dense operand (blocks kc * nrt + rt)
 int slice_dense(ss_ctx *ctx, const OzOperand &op, Scratch &buf, unsigned char **sl, int **em) {
-    const unsigned nrt = cdivu(op.rows, 128), nkc = cdivu(op.kdim, 64);
-    OZ_ALLOC(ctx, buf.get(sl, (size_t)nrt * nkc * sstc::kOzSlices * sstc::kOzBlock));
+    const unsigned nrt = cdivu(op.rows, 128), nkc = cdivu(op.kdim, sstc::kOzK);
+    OZ_ALLOC(ctx, buf.get(sl, (size_t)nrt * nkc * sstc::kOzStageA));
     OZ_ALLOC(ctx, buf.get(em, (size_t)op.rows));
     SS_CUDA_TRY(ctx, cudaMemsetAsync(*em, 0, sizeof(int) * op.rows, ctx->stream));
     const int64_t per_k = std::max<int64_t>(64, (int64_t)cdivu(op.kdim, std::max<unsigned>(1, 4 * ctx->sm_count / nrt)));
@@ -101,15 +104,14 @@ int dense_mm(ss_ctx *ctx, const OzOperand &A, const OzOperand &B, int mode, doub
     int rc;
     if ((rc = slice_dense(ctx, A, buf, &sa, &ea)) != SS_OK) return rc;
     if ((rc = slice_dense(ctx, B, buf, &sb, &eb)) != SS_OK) return rc;
-    const int nrtA = (int)cdivu(A.rows, 128), nrtB = (int)cdivu(B.rows, 128), nkc = (int)cdivu(A.kdim, 64);
+    const int nrtA = (int)cdivu(A.rows, 128), nrtB = (int)cdivu(B.rows, 128), nkc = (int)cdivu(A.kdim, sstc::kOzK);
     const int nct = (int)cdivu(B.rows, 64);
     const int64_t tiles = (int64_t)nrtA * nct;
     int per = nkc;
     if (mode == 0) {
-        // split the reduction until about two CTAs per SM; an even share per CTA
+        // split the reduction until about two CTAs per SM
         const int64_t want = std::max<int64_t>(1, std::min<int64_t>(nkc, cdivu(2ll * ctx->sm_count, tiles)));
         per = (int)cdivu(nkc, want);
-        per += per & 1;
     }
     const int nsplit = (int)cdivu(nkc, per);
     sstc::OzMM g{};
@@ -118,23 +120,24 @@ int dense_mm(ss_ctx *ctx, const OzOperand &A, const OzOperand &B, int mode, doub
     g.nkc = nkc; g.per = per; g.mode = mode; g.alpha = alpha; g.beta = beta;
     g.out = out; g.ldo = ldo;
     ctx->add_flops(SS_K_GEMM_TC, flops);
+    ctx->add_tensor_flops(SS_K_GEMM_TC, kPieceTensorFlops * nrtA * nct * nkc);
     return run_mm(ctx, g, dim3(nct, nrtA, nsplit), SS_K_GEMM_TC);
 }
 
-// (tile, piece) pairs of the pattern: for each 128-row tile the 64-column pieces that hold
+// (tile, piece) pairs of the pattern: for each 128-row tile the 32-column pieces that hold
 // entries, and per pair and row the CSR position of the row's first entry in the piece
 int plan_build(ss_symbolic *s) {
     ss_ctx *ctx = s->ctx;
     const int64_t n = s->n;
     const int32_t nrt = (int32_t)cdivu(n, 128);
-    const int64_t npieces = (n + 63) / 64;
+    const int64_t npieces = (n + sstc::kOzK - 1) / sstc::kOzK;
     std::vector<int32_t> tile_ptr(nrt + 1, 0), pair_tile, pair_piece, mark(npieces, -1), list;
     std::vector<int64_t> seg;
     for (int32_t rt = 0; rt < nrt; ++rt) {
         list.clear();
         const int64_t r0 = (int64_t)rt * 128, r1 = std::min<int64_t>(n, r0 + 128);
         for (int64_t p = s->rowptr[r0]; p < s->rowptr[r1]; ++p) {
-            const int32_t pc = s->colind[p] >> 6;
+            const int32_t pc = s->colind[p] / sstc::kOzK;
             if (mark[pc] != rt) {
                 mark[pc] = rt;
                 list.push_back(pc);
@@ -152,7 +155,7 @@ int plan_build(ss_symbolic *s) {
             int64_t ptr = row < n ? s->rowptr[row] : 0;
             const int64_t end = row < n ? s->rowptr[row + 1] : 0;
             for (size_t u = 0; u < list.size(); ++u) {
-                while (ptr < end && s->colind[ptr] < (int64_t)list[u] * 64) ++ptr;
+                while (ptr < end && s->colind[ptr] < (int64_t)list[u] * sstc::kOzK) ++ptr;
                 seg[(base + u) * 128 + r] = ptr;
             }
         }
@@ -189,7 +192,7 @@ int vals_make(ss_symbolic *s, const double *vals, OzVals *v, Scratch *buf) {
     int rc;
     if (!s->oz_plan && (rc = plan_build(s)) != SS_OK) return rc;
     const OzPlan *pl = s->oz_plan;
-    const size_t bytes = (size_t)std::max<int64_t>(1, pl->npairs) * sstc::kOzSlices * sstc::kOzBlock;
+    const size_t bytes = (size_t)std::max<int64_t>(1, pl->npairs) * sstc::kOzStageA;
     v->vals = vals;
     if (buf) {
         OZ_ALLOC(ctx, buf->get(&v->sl, bytes));
@@ -245,6 +248,7 @@ int spmm_core(ss_symbolic *s, int npass, OzVals *const *v, const double *const *
         g.mode = 1; g.alpha = alpha[p]; g.beta = p == 0 ? 0.0 : 1.0; g.colscale = colscale[p];
         g.out = Y; g.ldo = ldy;
         ctx->add_flops(SS_K_SPMM_TC, 2.0 * (double)s->nnz * k);
+        ctx->add_tensor_flops(SS_K_SPMM_TC, kPieceTensorFlops * (double)pl->npairs * cdivu(k, 64));
         if ((rc = run_mm(ctx, g, dim3(cdivu(k, 64), pl->nrt, 1), SS_K_SPMM_TC)) != SS_OK) return rc;
     }
     return SS_OK;

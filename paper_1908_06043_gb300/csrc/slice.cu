@@ -126,32 +126,32 @@ int sym_eig(ss_ctx *ctx, double *H, int k, double *evals, double *Q, DevBuf &buf
     } else if (k > 96) {
         // cooperative grid: every block resident, rounds separated by a bounded barrier
         const int np = (k + (k & 1)) / 2, max_sweeps = 40;
-        int2 *pairs;
-        double2 *cs;
-        double *acc;
+        const size_t smem = (sizeof(double2) + sizeof(int2)) * (size_t)np;
+        double *acc, *H2;
         ssd::GridBar *bar;
         int *status;
-        TRY_ALLOC(ctx, buf.get(&pairs, (size_t)np));
-        TRY_ALLOC(ctx, buf.get(&cs, (size_t)np));
+        TRY_ALLOC(ctx, buf.get(&H2, (size_t)k * k));
         TRY_ALLOC(ctx, buf.get(&acc, (size_t)2 * max_sweeps));
         TRY_ALLOC(ctx, buf.get(&bar, 1));
         TRY_ALLOC(ctx, buf.get(&status, 1));
         SS_CUDA_TRY(ctx, cudaMemsetAsync(acc, 0, sizeof(double) * 2 * max_sweeps, st));
         SS_CUDA_TRY(ctx, cudaMemsetAsync(bar, 0, sizeof(ssd::GridBar), st));
+        SS_CUDA_TRY(ctx, cudaFuncSetAttribute(ssd::k_jacobi_grid, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)std::max<size_t>(smem, 1)));
         int per_sm = 0;
-        SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssd::k_jacobi_grid, 256, 0));
+        SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ssd::k_jacobi_grid, 256, smem));
         const int64_t want = ((int64_t)np * np + 255) / 256;
         int nb = (int)std::min<int64_t>(std::max(1, std::min(per_sm, 2)) * (int64_t)ctx->sm_count, std::max<int64_t>(1, want));
         const double thr = 1e-18;
-        const long long limit = 20000000;      // polls of about 64 ns: ~1 s
+        const long long limit = 20000000;      // units of 64 ns: ~1.3 s
         int *sw = status;
-        void *args[] = {(void *)&H, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol, (void *)&max_sweeps,
-                        (void *)&pairs, (void *)&cs, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
+        void *args[] = {(void *)&H, (void *)&H2, (void *)&V, (void *)&k, (void *)&thr, (void *)&tol,
+                        (void *)&max_sweeps, (void *)&acc, (void *)&bar, (void *)&limit, (void *)&sw};
         g_ss_launches.fetch_add(1, std::memory_order_relaxed);
         size_t slot = 0;
         const bool prof = ctx->prof_mask & (1u << SS_K_JACOBI);
         if (prof) slot = ss_prof_begin(ctx, SS_K_JACOBI);
-        SS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)ssd::k_jacobi_grid, dim3(nb), dim3(256), args, 0, st));
+        SS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)ssd::k_jacobi_grid, dim3(nb), dim3(256), args, smem, st));
         if (prof) ss_prof_end(ctx, SS_K_JACOBI, slot);
         int herr = 0;
         SS_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, st));
