@@ -84,23 +84,55 @@ __device__ __forceinline__ void fwd_diag_item(unsigned char *smem_raw, int slot,
     const PanelDesc pd = panels[p];
     const int w = pd.w, c0 = chunk * KD, kc = min(KD, k - c0);
     const int tid = threadIdx.x;
-    __syncthreads();
-    for (int q = tid; q < w * KD; q += 256) {
-        int i = q / KD, c = q % KD;
-        int src = piv[(int64_t)p * NB + i];
-        Y[i][c] = c < kc ? b[(int64_t)(pd.g0 + src) * k + c0 + c] : (T)0;
+    // all loads before the first store to shared memory (one memory latency per item)
+    constexpr int MU = NB * NB / 256, YU = NB * KD / 256;
+    double mv[MU];
+    T yv[YU];
+    int sv[YU];
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int i = (tid + 256 * u) / KD;
+        sv[u] = i < w ? piv[(int64_t)p * NB + i] : 0;
     }
-    for (int q = tid; q < w * w; q += 256) {
-        int i = q / w, j = q % w;
-        Lm[i][j] = (T)linv[(int64_t)p * NB * NB + i * NB + j];
+#pragma unroll
+    for (int u = 0; u < MU; ++u) mv[u] = linv[(int64_t)p * NB * NB + tid + 256 * u];
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u, i = q / KD, c = q % KD;
+        yv[u] = (i < w && c < kc) ? b[(int64_t)(pd.g0 + sv[u]) * k + c0 + c] : (T)0;
     }
     __syncthreads();
-    for (int q = tid; q < w * KD; q += 256) {
-        int i = q / KD, c = q % KD;
-        if (c >= kc) continue;
-        T acc = 0;
-        for (int t = 0; t <= i; ++t) acc += Lm[i][t] * Y[t][c];
-        b[(int64_t)(pd.g0 + i) * k + c0 + c] = acc;
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u;
+        Y[q / KD][q % KD] = yv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < MU; ++u) {
+        const int q = tid + 256 * u;
+        Lm[q / NB][q % NB] = (T)mv[u];
+    }
+    __syncthreads();
+    // rows i and i + 32 of column c accumulate side by side
+    {
+        constexpr int RU = NB * KD / 256;
+        const int c = tid % KD, i0 = tid / KD;
+        T acc[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) acc[u] = 0;
+        for (int t = 0; t < w; ++t) {
+            const T yt = Y[t][c];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int i = i0 + (256 / KD) * u;
+                acc[u] += (t <= i) ? Lm[i][t] * yt : (T)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int i = i0 + (256 / KD) * u;
+            if (i < w && c < kc) b[(int64_t)(pd.g0 + i) * k + c0 + c] = acc[u];
+        }
     }
 }
 
@@ -123,14 +155,29 @@ __device__ __forceinline__ void fwd_update_item(unsigned char *smem_raw, int til
     const T *F = arena + pd.front_off;
     const int64_t rowbase = pd.k0 + w + r0;
     const int tid = threadIdx.x;
-    __syncthreads();
-    for (int q = tid; q < w * TR; q += 256) {
-        int t = q / TR, i = q % TR;
-        Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
+    // all loads before the first store to shared memory (one memory latency per item)
+    constexpr int LU = NB * TR / 256, YU = NB * KC / 256;
+    T lv[LU], yv[YU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u, t = q / TR, i = q % TR;
+        lv[u] = (t < w && i < nr) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
     }
-    for (int q = tid; q < w * KC; q += 256) {
-        int t = q / KC, c = q % KC;
-        Y[t][c] = c < kc ? b[(int64_t)(pd.g0 + t) * k + c0 + c] : (T)0;
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u, t = q / KC, c = q % KC;
+        yv[u] = (t < w && c < kc) ? b[(int64_t)(pd.g0 + t) * k + c0 + c] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u;
+        Ls[q / TR][q % TR] = lv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u;
+        Y[q / KC][q % KC] = yv[u];
     }
     __syncthreads();
     const int *gi = idx + pd.idx_off + rowbase;
@@ -168,14 +215,30 @@ __device__ __forceinline__ void fwd_update_f32_item(unsigned char *smem_raw, int
     const float *F = arena + pd.front_off;
     const int64_t rowbase = pd.k0 + w + r0;
     const int tid = threadIdx.x;
-    __syncthreads();
-    for (int q = tid; q < w * TR; q += 256) {
-        int t = q / TR, i = q % TR;
-        Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
+    // every load of the tile is issued before the first store to shared memory, so the
+    // item waits for one memory latency instead of one per loop trip
+    constexpr int LU = NB * TR / 256, YU = NB * KC / 256;
+    float lv[LU], yv[YU];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u, t = q / TR, i = q % TR;
+        lv[u] = (t < w && i < nr) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
     }
-    for (int q = tid; q < w * KC; q += 256) {
-        int t = q / KC, c = q % KC;
-        Y[t][c] = c < kc ? b[(int64_t)(pd.g0 + t) * k + c0 + c] : 0.f;
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u, t = q / KC, c = q % KC;
+        yv[u] = (t < w && c < kc) ? b[(int64_t)(pd.g0 + t) * k + c0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u;
+        Ls[q / TR][q % TR] = lv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u;
+        Y[q / KC][q % KC] = yv[u];
     }
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;          // columns 2tx, 2tx+1; rows 4ty .. 4ty+3
@@ -218,14 +281,36 @@ __device__ __forceinline__ void bwd_gather_item(unsigned char *smem_raw, int til
     const int64_t rowbase = pd.k0 + w + r0;
     const int *gi = idx + pd.idx_off + rowbase;
     const int tid = threadIdx.x;
-    __syncthreads();
-    for (int q = tid; q < w * TR; q += 256) {
-        int t = q / TR, i = q % TR;
-        Ls[t][i] = i < nr ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
+    // all loads before the first store to shared memory (one memory latency per item, plus
+    // one for the row indices)
+    constexpr int LU = NB * TR / 256, XU = TR * KC / 256;
+    T lv[LU], xv[XU];
+    int gv[XU];
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+        const int i = (tid + 256 * u) / KC;
+        gv[u] = i < nr ? gi[i] : 0;
     }
-    for (int q = tid; q < TR * KC; q += 256) {
-        int i = q / KC, c = q % KC;
-        Xs[i][c] = (i < nr && c < kc) ? x[(int64_t)gi[i] * k + c0 + c] : (T)0;
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u, t = q / TR, i = q % TR;
+        lv[u] = (t < w && i < nr) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+        const int q = tid + 256 * u, i = q / KC, c = q % KC;
+        xv[u] = (i < nr && c < kc) ? x[(int64_t)gv[u] * k + c0 + c] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u;
+        Ls[q / TR][q % TR] = lv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+        const int q = tid + 256 * u;
+        Xs[q / KC][q % KC] = xv[u];
     }
     __syncthreads();
     T *z = zbuf + (int64_t)lo * NB * k;
@@ -258,14 +343,36 @@ __device__ __forceinline__ void bwd_gather_f32_item(unsigned char *smem_raw, int
     const int64_t rowbase = pd.k0 + w + r0;
     const int *gi = idx + pd.idx_off + rowbase;
     const int tid = threadIdx.x;
-    __syncthreads();
-    for (int q = tid; q < NB * TR; q += 256) {
-        int t = q / TR, i = q % TR;
-        Lt[i][t] = (i < nr && t < w) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
+    // all loads first (see the FP32 update); the row indices of this thread's right-hand
+    // side entries are loaded one step ahead of the entries themselves
+    constexpr int LU = NB * TR / 256, XU = TR * KC / 256;
+    float lv[LU], xv[XU];
+    int gv[XU];
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+        const int i = (tid + 256 * u) / KC;
+        gv[u] = i < nr ? gi[i] : 0;
     }
-    for (int q = tid; q < TR * KC; q += 256) {
-        int i = q / KC, c = q % KC;
-        Xs[i][c] = (i < nr && c < kc) ? x[(int64_t)gi[i] * k + c0 + c] : 0.f;
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u, t = q / TR, i = q % TR;
+        lv[u] = (i < nr && t < w) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+        const int q = tid + 256 * u, i = q / KC, c = q % KC;
+        xv[u] = (i < nr && c < kc) ? x[(int64_t)gv[u] * k + c0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u;
+        Lt[q % TR][q / TR] = lv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < XU; ++u) {
+        const int q = tid + 256 * u;
+        Xs[q / KC][q % KC] = xv[u];
     }
     __syncthreads();
     const int tx = tid & 15, ty = tid >> 4;          // columns 2tx, 2tx+1; panel columns 4ty .. 4ty+3
@@ -304,18 +411,35 @@ __device__ __forceinline__ void bwd_diag_item(unsigned char *smem_raw, int slot,
     const PanelDesc pd = panels[p];
     const int w = pd.w, c0 = chunk * KD, kc = min(KD, k - c0);
     const int tid = threadIdx.x;
+    // all loads before the first store to shared memory (one memory latency per item)
+    constexpr int MU = NB * NB / 256, UU = NB * KD / 256;
+    double mv[MU], dv = 0.0, ev = 0.0;
+    T uv[UU];
+    if (tid < NB) {
+        dv = dblk[(int64_t)p * 2 * NB + tid];
+        ev = dblk[(int64_t)p * 2 * NB + NB + tid];
+    }
+#pragma unroll
+    for (int u = 0; u < MU; ++u) mv[u] = linv[(int64_t)p * NB * NB + tid + 256 * u];
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+        const int q = tid + 256 * u, i = q / KD, c = q % KD;
+        uv[u] = (i < w && c < kc) ? x[(int64_t)(pd.g0 + i) * k + c0 + c] : (T)0;
+    }
     __syncthreads();
     if (tid < NB) {
-        sd[tid] = dblk[(int64_t)p * 2 * NB + tid];
-        se[tid] = dblk[(int64_t)p * 2 * NB + NB + tid];
+        sd[tid] = dv;
+        se[tid] = ev;
     }
-    for (int q = tid; q < w * w; q += 256) {
-        int i = q / w, j = q % w;
-        Lm[i][j] = (T)linv[(int64_t)p * NB * NB + i * NB + j];
+#pragma unroll
+    for (int u = 0; u < MU; ++u) {
+        const int q = tid + 256 * u;
+        Lm[q / NB][q % NB] = (T)mv[u];
     }
-    for (int q = tid; q < w * KD; q += 256) {
-        int i = q / KD, c = q % KD;
-        U[i][c] = c < kc ? x[(int64_t)(pd.g0 + i) * k + c0 + c] : (T)0;
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+        const int q = tid + 256 * u;
+        U[q / KD][q % KD] = uv[u];
     }
     __syncthreads();
     T val[NB * KD / 256];
@@ -347,13 +471,27 @@ __device__ __forceinline__ void bwd_diag_item(unsigned char *smem_raw, int slot,
         if (i < w) U[i][c] = val[a];
     }
     __syncthreads();
-    // x'[i] = sum_{t >= i} Linv[t][i] u[t];  x[g0 + piv[i]] = x'[i]
-    for (int q = tid; q < w * KD; q += 256) {
-        int i = q / KD, cc = q % KD;
-        if (cc >= kc) continue;
-        T acc = 0;
-        for (int t = i; t < w; ++t) acc += Lm[t][i] * U[t][cc];
-        x[(int64_t)(pd.g0 + piv[(int64_t)p * NB + i]) * k + c0 + cc] = acc;
+    // x'[i] = sum_{t >= i} Linv[t][i] u[t];  x[g0 + piv[i]] = x'[i]  (rows i and i + 32
+    // of column cc accumulate side by side)
+    {
+        constexpr int RU = NB * KD / 256;
+        const int cc = tid % KD, i0 = tid / KD;
+        T acc[RU];
+#pragma unroll
+        for (int u = 0; u < RU; ++u) acc[u] = 0;
+        for (int t = 0; t < w; ++t) {
+            const T ut = U[t][cc];
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int i = i0 + (256 / KD) * u;
+                acc[u] += (t >= i) ? Lm[t][i] * ut : (T)0;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RU; ++u) {
+            const int i = i0 + (256 / KD) * u;
+            if (i < w && cc < kc) x[(int64_t)(pd.g0 + piv[(int64_t)p * NB + i]) * k + c0 + cc] = acc[u];
+        }
     }
 }
 
@@ -431,6 +569,9 @@ struct SweepArgs {
     GridBar *bar;
     long long limit;
     int32_t *sm_slots;     // nsm_slots zeroed counters (blocks seen per SM id), or null
+    int32_t *arrive;       // fused FP32 sweep: (number of panels) x (k / KC chunks) zeroed
+                           // counters of finished gather items, or null
+    int32_t fuse_max;      // FP32 levels with at most this many fused items take them
 };
 
 // Position of this block in the order (rank on its SM, SM id), so that the first items
@@ -459,13 +600,320 @@ __device__ __forceinline__ int spread_block_id(const SweepArgs &a, bool *ok) {
     return s_vb;
 }
 
+// ---------------------------------------------------------------- fused FP32 sweep items
+// With FP32 arithmetic a solve is bound by the chain of levels, not by its flops, so the
+// FP32 sweep takes one grid barrier per level and sweep instead of two:
+//  * forward: every update item (row tile, KC columns) of a panel computes the panel's
+//    y = L11^-1 P b1 for its own columns itself (the diagonal block's 64 x 64 x KC
+//    multiply-adds, half of the update's) and pushes L21 y; the panel's first item (or its
+//    only item, when no rows lie below the panel) writes y to the separate array yout, so
+//    no item overwrites a b1 that another item of the level still reads;
+//  * backward: the gather items of a panel count their arrivals on the panel's counter
+//    (after a memory fence); the last one to arrive runs the panel's diagonal step for its
+//    KC columns, reading the gathered z from L2 -- no block waits for another.
+constexpr size_t fused_fwd_smem() { return sizeof(float) * (NB * (NB + 1) + 2 * NB * KC + NB * TR); }
+constexpr size_t fused_bwd_smem() { return sizeof(float) * (NB * (NB + 1) + NB * KC); }
+constexpr size_t fused_smem() {
+    return fused_fwd_smem() > tile_solve_smem_f32() ? fused_fwd_smem() : tile_solve_smem_f32();
+}
+
+// dynamic shared memory of a k_solve_sweeps<T> launch (the FP32 kernel also runs the fused sweep)
+template <typename T> constexpr size_t sweep_launch_smem() {
+    return std::is_same<T, float>::value ? (sweep_smem<T>() > fused_smem() ? sweep_smem<T>() : fused_smem())
+                                         : sweep_smem<T>();
+}
+
+// rows below panel slot `slot` of a level, in row tiles
+__device__ __forceinline__ int slot_tiles(const int32_t *__restrict__ tile_pre, int32_t count, int32_t row_tiles,
+                                          int slot) {
+    return (slot + 1 < count ? tile_pre[slot + 1] : row_tiles) - tile_pre[slot];
+}
+
+// forward item: panel slot `slot`, its row tile `rt` (rt < 0: the panel has no rows below),
+// right-hand-side chunk `chunk` (KC columns)
+__device__ __forceinline__ void fwd_fused_f32_item(unsigned char *smem_raw, int slot, int rt, int chunk,
+                                                   const int32_t *__restrict__ lvl_panels,
+                                                   const PanelDesc *__restrict__ panels,
+                                                   const int32_t *__restrict__ idx,
+                                                   const double *__restrict__ linv,
+                                                   const int32_t *__restrict__ piv,
+                                                   const float *__restrict__ arena, float *b, float *yout, int k) {
+    float (*Lm)[NB + 1] = reinterpret_cast<float (*)[NB + 1]>(smem_raw);
+    float (*Y0)[KC] = reinterpret_cast<float (*)[KC]>(smem_raw + sizeof(float) * NB * (NB + 1));
+    float (*Y)[KC] = reinterpret_cast<float (*)[KC]>(smem_raw + sizeof(float) * (NB * (NB + 1) + NB * KC));
+    float (*Ls)[TR] = reinterpret_cast<float (*)[TR]>(smem_raw + sizeof(float) * (NB * (NB + 1) + 2 * NB * KC));
+    const int p = lvl_panels[slot];
+    const PanelDesc pd = panels[p];
+    const int w = pd.w, m = pd.m;
+    const int c0 = chunk * KC, kc = min(KC, k - c0);
+    const int tid = threadIdx.x;
+    const int r0 = rt < 0 ? 0 : rt * TR;
+    const int nr = rt < 0 ? 0 : min(TR, m - pd.k0 - w - r0);
+    const int64_t rowbase = pd.k0 + w + r0;
+    const float *F = arena + pd.front_off;
+    // every load first: L11^-1, the pivoted b1 chunk, the L21 tile
+    constexpr int MU = NB * NB / 256, YU = NB * KC / 256, LU = NB * TR / 256;
+    double mv[MU];
+    float yv[YU], lv[LU];
+    int sv[YU];
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int i = (tid + 256 * u) / KC;
+        sv[u] = i < w ? piv[(int64_t)p * NB + i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < MU; ++u) mv[u] = linv[(int64_t)p * NB * NB + tid + 256 * u];
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u, t = q / TR, i = q % TR;
+        lv[u] = (t < w && i < nr) ? F[(int64_t)(pd.k0 + t) * m + rowbase + i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u, i = q / KC, c = q % KC;
+        yv[u] = (i < w && c < kc) ? b[(int64_t)(pd.g0 + sv[u]) * k + c0 + c] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < MU; ++u) {
+        const int q = tid + 256 * u;
+        Lm[q / NB][q % NB] = (float)mv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < YU; ++u) {
+        const int q = tid + 256 * u;
+        Y0[q / KC][q % KC] = yv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < LU; ++u) {
+        const int q = tid + 256 * u;
+        Ls[q / TR][q % TR] = lv[u];
+    }
+    __syncthreads();
+    // y = L11^-1 (P b1): thread column c, rows rr + 8 a (a warp shares its rows); the
+    // eight rows accumulate side by side so their multiply-adds do not wait on each other
+    {
+        const int c = tid & 31, rr = tid >> 5;
+        const bool write = rt <= 0 && c < kc;
+        float acc[NB / 8];
+#pragma unroll
+        for (int a = 0; a < NB / 8; ++a) acc[a] = 0.f;
+        for (int t = 0; t < w; ++t) {
+            const float yt = Y0[t][c];
+#pragma unroll
+            for (int a = 0; a < NB / 8; ++a) {
+                const int i = rr + 8 * a;
+                acc[a] += (t <= i) ? Lm[i][t] * yt : 0.f;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NB / 8; ++a) {
+            const int i = rr + 8 * a;
+            const float v = i < w ? acc[a] : 0.f;
+            Y[i][c] = v;
+            if (write && i < w) yout[(int64_t)(pd.g0 + i) * k + c0 + c] = v;
+        }
+    }
+    if (rt < 0) return;
+    __syncthreads();
+    // b2 -= L21 y (the FP32 update's 4 x 2 register tile)
+    const int tx = tid & 15, ty = tid >> 4;
+    float acc[4][2] = {};
+    for (int t = 0; t < w; ++t) {
+        const float4 l = *reinterpret_cast<const float4 *>(&Ls[t][4 * ty]);
+        const float2 y = *reinterpret_cast<const float2 *>(&Y[t][2 * tx]);
+        acc[0][0] += l.x * y.x; acc[0][1] += l.x * y.y;
+        acc[1][0] += l.y * y.x; acc[1][1] += l.y * y.y;
+        acc[2][0] += l.z * y.x; acc[2][1] += l.z * y.y;
+        acc[3][0] += l.w * y.x; acc[3][1] += l.w * y.y;
+    }
+    const int c = 2 * tx;
+    if (c >= kc) return;
+    const bool both = c + 1 < kc, paired = both && (k % 2 == 0);
+    const int *gi = idx + pd.idx_off + rowbase;
+    for (int r = 0; r < 4; ++r) {
+        const int i = 4 * ty + r;
+        if (i < nr) atomic_add_pair(&b[(int64_t)gi[i] * k + c0 + c], -acc[r][0], -acc[r][1], both, paired);
+    }
+}
+
+// backward diagonal step of panel slot `slot` for KC columns: x1 = P^T L11^-T (D^-1 y - z),
+// y read from yin (the forward sweep's output), z (when use_z) from L2
+__device__ __forceinline__ void bwd_diag_kc_f32_item(unsigned char *smem_raw, int slot, int chunk,
+                                                     const int32_t *__restrict__ lvl_panels,
+                                                     const PanelDesc *__restrict__ panels,
+                                                     const double *__restrict__ linv,
+                                                     const double *__restrict__ dblk,
+                                                     const int32_t *__restrict__ piv, const float *zslot,
+                                                     int use_z, const float *__restrict__ yin, float *x, int k) {
+    float (*Lm)[NB + 1] = reinterpret_cast<float (*)[NB + 1]>(smem_raw);
+    float (*U)[KC] = reinterpret_cast<float (*)[KC]>(smem_raw + sizeof(float) * NB * (NB + 1));
+    __shared__ double sd[NB], se[NB];
+    const int p = lvl_panels[slot];
+    const PanelDesc pd = panels[p];
+    const int w = pd.w, c0 = chunk * KC, kc = min(KC, k - c0);
+    const int tid = threadIdx.x;
+    constexpr int MU = NB * NB / 256, UU = NB * KC / 256;
+    double mv[MU], dv = 0.0, ev = 0.0;
+    float uv[UU], zv[UU];
+    if (tid < NB) {
+        dv = dblk[(int64_t)p * 2 * NB + tid];
+        ev = dblk[(int64_t)p * 2 * NB + NB + tid];
+    }
+#pragma unroll
+    for (int u = 0; u < MU; ++u) mv[u] = linv[(int64_t)p * NB * NB + tid + 256 * u];
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+        const int q = tid + 256 * u, i = q / KC, c = q % KC;
+        const bool in = i < w && c < kc;
+        uv[u] = in ? yin[(int64_t)(pd.g0 + i) * k + c0 + c] : 0.f;
+        zv[u] = (in && use_z) ? __ldcg(zslot + (int64_t)i * k + c0 + c) : 0.f;
+    }
+    __syncthreads();
+    if (tid < NB) {
+        sd[tid] = dv;
+        se[tid] = ev;
+    }
+#pragma unroll
+    for (int u = 0; u < MU; ++u) {
+        const int q = tid + 256 * u;
+        Lm[q / NB][q % NB] = (float)mv[u];
+    }
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+        const int q = tid + 256 * u;
+        U[q / KC][q % KC] = uv[u];
+    }
+    __syncthreads();
+    // u = D^-1 y - z (1x1 and 2x2 blocks of D, in FP64)
+    float val[UU];
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+        const int q = tid + 256 * u, i = q / KC, c = q % KC;
+        double v = 0.0;
+        if (i < w && c < kc) {
+            if (se[i] != 0.0) {                     // first row of a 2x2 block
+                const double A = sd[i], B = se[i], C = sd[i + 1], det = A * C - B * B;
+                v = (C * (double)U[i][c] - B * (double)U[i + 1][c]) / det;
+            } else if (i > 0 && se[i - 1] != 0.0) { // second row of a 2x2 block
+                const double A = sd[i - 1], B = se[i - 1], C = sd[i], det = A * C - B * B;
+                v = (-B * (double)U[i - 1][c] + A * (double)U[i][c]) / det;
+            } else {
+                v = sd[i] != 0.0 ? (double)U[i][c] / sd[i] : 0.0;
+            }
+            v -= (double)zv[u];
+        }
+        val[u] = (float)v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < UU; ++u) {
+        const int q = tid + 256 * u;
+        U[q / KC][q % KC] = val[u];
+    }
+    __syncthreads();
+    // x'[i] = sum_{t >= i} Linv[t][i] u[t];  x[g0 + piv[i]] = x'[i]
+    // (the eight rows of a thread accumulate side by side, as in the forward item)
+    const int c = tid & 31, rr = tid >> 5;
+    float acc[NB / 8];
+#pragma unroll
+    for (int a = 0; a < NB / 8; ++a) acc[a] = 0.f;
+    for (int t = 0; t < w; ++t) {
+        const float ut = U[t][c];
+#pragma unroll
+        for (int a = 0; a < NB / 8; ++a) {
+            const int i = rr + 8 * a;
+            acc[a] += (t >= i) ? Lm[t][i] * ut : 0.f;
+        }
+    }
+    if (c >= kc) return;
+#pragma unroll
+    for (int a = 0; a < NB / 8; ++a) {
+        const int i = rr + 8 * a;
+        if (i < w) x[(int64_t)(pd.g0 + piv[(int64_t)p * NB + i]) * k + c0 + c] = acc[a];
+    }
+}
+
+// One level of the FP32 forward sweep with the fused items (see above); no barrier.
+__device__ __forceinline__ void fwd_level_fused_f32(const SweepArgs &a, unsigned char *smem_raw, int vb,
+                                                    const SweepLevel &lv, const float *__restrict__ arena, float *b,
+                                                    float *ybuf) {
+    const int k = a.k, nchunk = (k + KC - 1) / KC;
+    const unsigned nb = gridDim.x;
+    const int32_t *lp = a.solve_panels + lv.panel_off;
+    const int32_t *tp = a.tile_pre + lv.panel_off;
+    const int nup = lv.row_tiles * nchunk;
+    for (int q = vb; q < nup + lv.count * nchunk; q += nb) {
+        if (q < nup) {
+            const int tile = q % lv.row_tiles, chunk = q / lv.row_tiles;
+            const int slot = tile_slot(tp, lv.count, tile);
+            __syncthreads();
+            fwd_fused_f32_item(smem_raw, slot, tile - tp[slot], chunk, lp, a.panels, a.idx, a.linv, a.piv, arena, b,
+                               ybuf, k);
+        } else {
+            const int slot = (q - nup) % lv.count, chunk = (q - nup) / lv.count;
+            if (slot_tiles(tp, lv.count, lv.row_tiles, slot) > 0) continue;   // done by its tile items
+            __syncthreads();
+            fwd_fused_f32_item(smem_raw, slot, -1, chunk, lp, a.panels, a.idx, a.linv, a.piv, arena, b, ybuf, k);
+        }
+    }
+}
+
+// One level of the FP32 backward sweep with the fused items: gathers, and the diagonal
+// step of each (panel, chunk) run by its last gather item; no barrier.
+__device__ __forceinline__ void bwd_level_fused_f32(const SweepArgs &a, unsigned char *smem_raw, int vb,
+                                                    const SweepLevel &lv, const float *__restrict__ arena, float *b,
+                                                    float *zall, const float *ybuf) {
+    const int k = a.k, nchunk = (k + KC - 1) / KC;
+    const unsigned nb = gridDim.x;
+    __shared__ int s_last;
+    const int32_t *lp = a.solve_panels + lv.panel_off;
+    const int32_t *tp = a.tile_pre + lv.panel_off;
+    float *z = zall + (int64_t)lv.panel_off * NB * k;
+    const int ngt = lv.row_tiles * nchunk;
+    for (int q = vb; q < ngt + lv.count * nchunk; q += nb) {
+        if (q < ngt) {
+            const int tile = q % lv.row_tiles, chunk = q / lv.row_tiles;
+            bwd_gather_f32_item(smem_raw, tile, chunk, lp, tp, lv.count, a.panels, a.idx, arena, b, k, z);
+            // the panel's last gather item for this chunk runs its diagonal step
+            const int slot = tile_slot(tp, lv.count, tile);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int need = slot_tiles(tp, lv.count, lv.row_tiles, slot);
+                const int old = atomicAdd(&a.arrive[(int64_t)(lv.panel_off + slot) * nchunk + chunk], 1);
+                s_last = old == need - 1;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                bwd_diag_kc_f32_item(smem_raw, slot, chunk, lp, a.panels, a.linv, a.dblk, a.piv,
+                                     z + (int64_t)slot * NB * k, 1, ybuf, b, k);
+            }
+        } else {
+            const int slot = (q - ngt) % lv.count, chunk = (q - ngt) / lv.count;
+            if (slot_tiles(tp, lv.count, lv.row_tiles, slot) > 0) continue;   // done by its last gather
+            __syncthreads();
+            bwd_diag_kc_f32_item(smem_raw, slot, chunk, lp, a.panels, a.linv, a.dblk, a.piv, nullptr, 0, ybuf, b, k);
+        }
+    }
+}
+
+// whether level lv of an FP32 solve takes the fused items: only levels whose items all
+// fit in one pass of the resident blocks (a level with more items is bound by the items'
+// throughput, where the fused items' extra work costs more than the barrier it saves)
+__device__ __forceinline__ bool level_fused(const SweepArgs &a, const SweepLevel &lv, int nchunk) {
+    return a.arrive != nullptr && (int64_t)(lv.row_tiles + lv.count) * nchunk <= a.fuse_max;
+}
+
 // Forward and/or backward sweep over every level in one cooperative launch.  The work
 // items of a step are spread over the resident blocks; a grid barrier separates
 // consecutive steps.  zall: (number of panels) x NB x k, zero on entry (each level
 // gathers into its own slots).  On a barrier timeout bar->err is set and every block
 // returns.
 template <typename T>
-__global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__restrict__ arena, T *b, T *zall) {
+__global__ void __launch_bounds__(256, 4) k_solve_sweeps(SweepArgs a, const T *__restrict__ arena, T *b, T *zall,
+                                                         T *ybuf) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int k = a.k;
     const int nchunk = (k + KC - 1) / KC, ndchunk = (k + KD - 1) / KD;
@@ -477,6 +925,13 @@ __global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__re
         for (int L = 0; L < a.nlev; ++L) {
             const SweepLevel lv = a.lev[L];
             const int32_t *lp = a.solve_panels + lv.panel_off;
+            if constexpr (std::is_same<T, float>::value) {
+                if (level_fused(a, lv, nchunk)) {       // y of this level goes to ybuf
+                    fwd_level_fused_f32(a, smem_raw, vb, lv, arena, b, ybuf);
+                    if (!grid_barrier(a.bar, nb, a.limit)) return;
+                    continue;
+                }
+            }
             for (int q = vb; q < lv.count * ndchunk; q += nb)
                 fwd_diag_item<T>(smem_raw, q % lv.count, q / lv.count, lp, a.panels, a.linv, a.piv, b, k);
             if (!grid_barrier(a.bar, nb, a.limit)) return;
@@ -498,6 +953,13 @@ __global__ void __launch_bounds__(256) k_solve_sweeps(SweepArgs a, const T *__re
         const SweepLevel lv = a.lev[L];
         const int32_t *lp = a.solve_panels + lv.panel_off;
         T *z = zall + (int64_t)lv.panel_off * NB * k;
+        if constexpr (std::is_same<T, float>::value) {
+            if (level_fused(a, lv, nchunk)) {
+                bwd_level_fused_f32(a, smem_raw, vb, lv, arena, b, zall, ybuf);
+                if (L > 0 && !grid_barrier(a.bar, nb, a.limit)) return;
+                continue;
+            }
+        }
         if (lv.row_tiles > 0) {
             const int32_t *tp = a.tile_pre + lv.panel_off;
             for (int q = vb; q < lv.row_tiles * nchunk; q += nb) {

@@ -153,11 +153,12 @@ def test_gauss16_inertia_golden(gpu_lib):
         del f
 
 
-@pytest.mark.parametrize("k", [5, 34])
+@pytest.mark.parametrize("k", [5, 34, 64])
 def test_gauss16_rounded_fp32_solves(gpu_lib, k):
     # interior shifts of the N = 16,384 pencil whose FP32 factor fails the quality gate
     # are refactored in FP64 and solved in FP32 from the rounded factor inside FP64
-    # refinement; the refined solve must match the FP64 solve
+    # refinement; the refined solve must match the FP64 solve (k = 64: the refinement's
+    # residuals A X - sigma B X on the tensor cores)
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "gauss16_eigs.txt")
     lam = np.array([float(l) for l in open(path) if not l.startswith("#")])
@@ -202,3 +203,8 @@ def test_sweep_kernel_matches_per_step_launches(gpu_lib, precision, k):
         assert ((x1 - x2).norm() / x1.norm()).item() <= 1e-9
         ref = np.linalg.solve(M[j], R.cpu().numpy())
         assert np.abs(x2.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+        # the FP32 sweep's fused levels (one grid barrier per level) solve the same system
+        ctx.set_sweep_fusion(1 << 30)
+        x3 = f.solve(j, R, refine=2)
+        ctx.set_sweep_fusion(0)
+        assert ((x3 - x2).norm() / x2.norm()).item() <= 1e-9

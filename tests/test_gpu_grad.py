@@ -52,7 +52,7 @@ def test_config1_autograd_gradient_matches_dense_oracle(gpu_lib):
 def test_gauss16_gradient_central_finite_differences(gpu_lib):
     """64 seeded stored entries (p < q, each tying (p, q) and (q, p)), 32 of A and 32 of B:
     the sum of their gradients against one central difference of E along all of them
-    together, and two entries of each matrix individually."""
+    together, and one entry of each matrix on its own."""
     from paper_1908_06043_gb300.driver import SliceSolver, solve_plan
     p = config_pencil(2)
     ctx, sym, a, b = setup(gpu_lib, p)
@@ -102,10 +102,8 @@ def test_gauss16_gradient_central_finite_differences(gpu_lib):
     signs = rng.choice([-1.0, 1.0], 64)
     check(pick[:32], signs[:32], True)
     check(pick[32:], signs[32:], False)
-    for e in pick[:2]:
-        check([e], [1.0], True)
-    for e in pick[32:34]:
-        check([e], [1.0], False)
+    check([pick[0]], [1.0], True)
+    check([pick[32]], [1.0], False)
 
 
 def test_band_energy_not_differentiable_at_a_degenerate_boundary(gpu_lib):
