@@ -75,6 +75,10 @@ def parse():
     ap.add_argument("--sequence", type=int, default=0,
                     help="instead of the benchmark: solve this many pencils A_i = A_0 + 0.1 2^-i R of the "
                          "workload with probe migration and print one JSON line per pencil")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of the benchmark: the first BATCH pencils of the seeded uneven batch (lattice "
+                         "dims 8-18, 2 or 4 functions per atom, lowest 10%% via 8 shifts each); window-bound "
+                         "counts of all pencils from one stacked factorisation per bound, then every slice solve")
     ap.add_argument("--only-probe", action="store_true",
                     help="profiling case: factor one shift of the workload and run its probe for 6 iterations")
     ap.add_argument("--profile-step", action="store_true",
@@ -270,6 +274,78 @@ def run_reference(args, wl):
 
 
 # ----------------------------------------------------------------- GPU leg
+def run_batch(args, ctx):
+    """The uneven batch of independent pencils (first args.batch of the 256 seeded ones):
+    each pencil's shifts placed from its own DOS estimate; the exact counts at every
+    window bound of every pencil from the stacked pencils, one inertia-only factorisation
+    of the stack per bound index (all pencils in the same launches), checked against the
+    pencils counted one at a time; then every slice solve of every pencil."""
+    import numpy as np
+    import torch
+
+    from paper_1908_06043_gb300.driver import (DosModel, SliceSolver, count_below_stacked, plan_slices,
+                                               plan_with_counts, solve_slice)
+    from workloads.pencils import batch_pencils, normal_block, stack_pencils, uneven_batch_specs
+
+    n_s = 8
+    t0 = time.perf_counter()
+    specs = uneven_batch_specs(256)[:args.batch]
+    ps = batch_pencils(specs)
+    st, seg, _ = stack_pencils(ps)
+    gen_s = time.perf_counter() - t0
+    sym_st = ctx.analyze(st.rowptr, st.colind)
+    a_st = torch.tensor(st.a, device="cuda")
+    b_st = torch.tensor(st.b, device="cuda")
+    solvers, plans0 = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i, q in enumerate(ps):
+        sym = ctx.analyze(q.rowptr, q.colind)
+        a = torch.tensor(q.a, device="cuda")
+        b = torch.tensor(q.b, device="cuda")
+        sv = SliceSolver(sym, a, b, precision=args.precision)
+        model = DosModel(q.n, sym.dos_estimate(a, b, 100, torch.tensor(normal_block(q.n, 4, 1000 + i),
+                                                                         device="cuda")))
+        solvers.append(sv)
+        plans0.append(plan_slices(sv, model, int(0.1 * q.n), n_s, windows=[]))
+    torch.cuda.synchronize()
+    place_s = time.perf_counter() - t0
+    # exact counts at the 9 bounds of every pencil: stacked, then one pencil at a time
+    t0 = time.perf_counter()
+    got = count_below_stacked(sym_st, a_st, b_st, seg, [pl.bounds for pl in plans0])
+    torch.cuda.synchronize()
+    stacked_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref = [sv.count_below(pl.bounds) for sv, pl in zip(solvers, plans0)]
+    torch.cuda.synchronize()
+    single_s = time.perf_counter() - t0
+    plans = [plan_with_counts(pl, c, q.n) for pl, c, q in zip(plans0, got, ps)]
+    # every slice solve of every pencil
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    n_ok, n_solves, eig_ok = 0, 0, 0
+    for i, (sv, pl) in enumerate(zip(solvers, plans)):
+        found = 0
+        for j in range(n_s):
+            o = solve_slice(sv, pl, j, seed=7 * i + j)
+            n_solves += 1
+            n_ok += int(o.ok)
+            found += o.theta.size
+        eig_ok += int(found == pl.counts[-1] - pl.counts[0])
+    ev1.record()
+    torch.cuda.synchronize()
+    solve_s = ev0.elapsed_time(ev1) / 1e3
+    sizes = [q.n for q in ps]
+    print(json.dumps({"batch": args.batch, "of": 256, "precision": args.precision,
+                      "pencil_n": {"min": min(sizes), "max": max(sizes), "sum": int(sum(sizes))},
+                      "shifts_per_pencil": n_s, "generation_s": gen_s, "placement_s": place_s,
+                      "bound_counts": {"stacked_s": stacked_s, "one_at_a_time_s": single_s,
+                                       "speedup": single_s / stacked_s if stacked_s > 0 else None,
+                                       "factorisations": len(ps) * (n_s + 1), "stacked_equal": got == ref},
+                      "slice_solves": n_solves, "validated": n_ok, "pencils_complete": eig_ok,
+                      "solve_s": solve_s, "slice_solves_per_s": n_solves / solve_s}), flush=True)
+
+
 def main():
     args = parse()
     wl = WORKLOADS[args.workload]
@@ -331,6 +407,9 @@ def main():
         print(json.dumps({"factor_only": args.factor_only, "workload": wl["name"], "classes": out}), flush=True)
         return
 
+    if args.batch:
+        return run_batch(args, ctx)
+
     if args.sequence:
         # SCF-like pencil sequence: DOS placement for the first pencil, k-means probe
         # migration with warm starts afterwards; per-pencil wall time and iterations
@@ -340,12 +419,8 @@ def main():
         a_list = [torch.tensor(scf_pencil(p, r, i).a, device="cuda") for i in range(args.sequence)]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        res = solve_sequence(sym, a_list, b, n_e, n_s, precision=args.precision,
-                             start=torch.tensor(normal_block(p.n, n_vec, 1000), device="cuda"),
-                             uniforms=np.random.default_rng(7).random(n_s))
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        for i, rs in enumerate(res):
+
+        def report(i, rs):
             mig = rs.timings["migration"]
             ok = bool(rs.timings["converged"]) and len(rs.residuals) > 0 and float(rs.residuals.max()) <= 1e-10
             print(json.dumps({"sequence_step": i, "workload": wl["name"], "precision": args.precision,
@@ -355,7 +430,14 @@ def main():
                               "max_resid": float(rs.residuals.max()),
                               "shifts": [float(x) for x in rs.shifts], "n_probes": len(rs.shifts),
                               "migration_init": mig["init"] if mig else "DOS placement",
+                              "ball_fallback": mig["ball_fallback"] if mig else None,
                               "cluster_sizes": mig["sizes"] if mig else None}), flush=True)
+
+        res = solve_sequence(sym, a_list, b, n_e, n_s, precision=args.precision,
+                             start=torch.tensor(normal_block(p.n, n_vec, 1000), device="cuda"),
+                             uniforms=np.random.default_rng(7).random(n_s), on_step=report)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
         print(json.dumps({"sequence_total_s": t1 - t0, "pencils": len(res)}), flush=True)
         return
 

@@ -143,6 +143,17 @@ const char *ss_last_error(const ss_ctx *ctx);
 enum { SS_SOLVE_SWEEP_KERNEL = 0, SS_SOLVE_PER_STEP = 1 };
 ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode);
 
+/* FP32 sweep solves (implementation choice, no paper counterpart): a level whose fused
+ * items -- (rows-below tiles + panels) x ceil(k / 32) -- number at most max_items runs them
+ * with one grid barrier instead of two: every update item solves its panel's diagonal
+ * block for its own 32 columns, and the last gather item of a panel runs its backward
+ * diagonal step.  0 (default): never; -1: levels whose fused items fit in one pass of the
+ * resident blocks.  Measured on GB300 (N = 16,384, k = 304): 6.5 ms per FP32 solve unfused,
+ * 7.7 ms with -1 and 13.1 ms with every level fused -- the extra work of the fused items
+ * costs more than the barriers they save, so the default leaves it off.
+ * Errors: SS_ERR_ARG (max_items < -1). */
+ss_status ss_set_sweep_fusion(ss_ctx *ctx, int32_t max_items);
+
 /* Where the FP64 Schur-complement updates of ss_factor run (Alg. 2 step 2; an
  * implementation choice with no paper counterpart).  SS_SCHUR_TENSOR (default): a factor
  * step whose Schur update has at least min_flops algorithmic flops [2e7] runs on the FP16
@@ -280,6 +291,34 @@ ss_status ss_factor_destroy(ss_numeric *f);
  * Errors: SS_ERR_ARG, SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_TIMEOUT. */
 ss_status ss_autotune_schur(ss_symbolic *sym, const double *a_vals, const double *b_vals, double sigma,
                             int32_t *n_tc_steps);
+
+/* ---- ss_factor_segments (Alg. 2 step 2 for many pencils; Section 2.2) -------------
+ * Batched factorisation of many independent pencils of uneven size in the same launches:
+ * the caller stacks the pencils into one block-diagonal pattern (each pencil's rows and
+ * columns contiguous or not; no stored entry may couple rows of two pencils) and analyses
+ * it once; ss_analyze's dissection keeps every pencil in its own subtrees, so each level
+ * of the factorisation is one launch over the fronts of all pencils.  Shift j of the call
+ * factors A_p - sigma[j * n_seg + p] B_p for every pencil p at once (HOST sigma, n_shift x
+ * n_seg row-major; HOST row_segment, N entries, the pencil in [0, n_seg) of each
+ * original row; DEVICE a_vals, b_vals as for ss_factor).  The factor is FP64 and
+ * inertia-only (no L kept: solves return SS_ERR_ARG); ss_inertia gives the counts of the
+ * whole stack, ss_inertia_segments those of each pencil.  It is what the validation of
+ * every pencil's windows needs (exact counts at the window bounds, Section 2.2).
+ * Errors: SS_ERR_ARG (bad pencil index, an entry coupling two pencils, non-finite shift),
+ * SS_ERR_OOM, SS_ERR_CUDA, SS_ERR_SINGULAR (a pivot of some pencil fell below
+ * 64 u (||A||_1 + max_p |sigma_jp| ||B||_1); the factor is still returned and
+ * ss_inertia_segments reports which pencils). */
+ss_status ss_factor_segments(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                             const int32_t *row_segment, int32_t n_seg, const double *sigma,
+                             int32_t n_shift, ss_numeric **out);
+
+/* Inertia of A_p - sigma_jp B_p for every pencil p of an ss_factor_segments factor: the
+ * 1x1 and 2x2 pivots of D classified as by ss_inertia and counted per pencil.  HOST int64
+ * outputs of n_seg entries each; n_tiny (may be NULL): pivots of the pencil below the
+ * singularity threshold.  Errors: SS_ERR_ARG (also for a factor made by ss_factor),
+ * SS_ERR_OOM, SS_ERR_CUDA. */
+ss_status ss_inertia_segments(const ss_numeric *f, int32_t shift_idx, int64_t *n_neg, int64_t *n_zero,
+                              int64_t *n_pos, int64_t *n_tiny);
 
 /* ---- ss_inertia (Section 2.2: Sylvester's law of inertia) ------------------------
  * Inertia of A - sigma_j B from the block-diagonal D: n_neg = #negative 1x1 pivots

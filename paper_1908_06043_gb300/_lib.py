@@ -51,8 +51,8 @@ class ss_solve_opts(C.Structure):
 
 
 EXPORTS = ["ss_create", "ss_destroy", "ss_last_error", "ss_analyze", "ss_symbolic_info_get",
-           "ss_symbolic_perm", "ss_symbolic_destroy", "ss_symbolic_validate", "ss_factor", "ss_factor_destroy", "ss_inertia", "ss_factor_stats", "ss_factor_quality",
-           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode", "ss_selftest_barrier", "ss_measure_peak", "ss_set_schur_mode", "ss_selftest_tc", "ss_set_factor_graph", "ss_autotune_schur", "ss_set_gemm_mode", "ss_dense_gram", "ss_dense_gemm", "ss_profile_query_tensor"]
+           "ss_symbolic_perm", "ss_symbolic_destroy", "ss_symbolic_validate", "ss_factor", "ss_factor_segments", "ss_factor_destroy", "ss_inertia", "ss_inertia_segments", "ss_factor_stats", "ss_factor_quality",
+           "ss_solve", "ss_solve_noalloc", "ss_slice_solve", "ss_dos_estimate", "ss_dos_lanczos", "ss_band_energy_grad", "ss_spmm", "ss_sync", "ss_launch_count", "ss_profile", "ss_profile_query", "ss_set_solve_mode", "ss_set_sweep_fusion", "ss_selftest_barrier", "ss_measure_peak", "ss_set_schur_mode", "ss_selftest_tc", "ss_set_factor_graph", "ss_autotune_schur", "ss_set_gemm_mode", "ss_dense_gram", "ss_dense_gemm", "ss_profile_query_tensor"]
 KERNEL_CLASSES = ["assemble", "extend_add", "diag_bk", "panel", "schur", "fwd_diag", "fwd_update", "bwd_gather",
                   "bwd_diag", "permute", "spmm", "gram", "gemm", "small_dense", "jacobi", "lanczos", "sddmm", "misc",
                   "panel_f32", "schur_f32", "fwd_update_f32", "bwd_gather_f32", "solve", "solve_f32",
@@ -94,6 +94,9 @@ def load():
         "ss_factor": ([P, P, P, P, i32, i32, PP], i32),
         "ss_factor_destroy": ([P], i32),
         "ss_inertia": ([P, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(i32)], i32),
+        "ss_factor_segments": ([P, P, P, P, i32, P, i32, PP], i32),
+        "ss_set_sweep_fusion": ([P, i32], i32),
+        "ss_inertia_segments": ([P, i32, P, P, P, P], i32),
         "ss_factor_stats": ([P, i32, C.POINTER(dbl), C.POINTER(dbl), C.POINTER(i64)], i32),
         "ss_factor_quality": ([P, i32, C.POINTER(i32), C.POINTER(dbl)], i32),
         "ss_solve": ([P, i32, P, i32, P, i32], i32),

@@ -71,6 +71,12 @@ class Context:
     def analyze(self, rowptr: np.ndarray, colind: np.ndarray, nd_leaf: int = 0, dense: bool = False) -> "Symbolic":
         return analyze(self, rowptr, colind, nd_leaf, dense)
 
+    def set_sweep_fusion(self, max_items: int = 0):
+        """FP32 sweep solves: levels with at most max_items fused items take one grid barrier
+        instead of two (0, the default: never; -1: those that fit in one pass of the
+        resident blocks)."""
+        self.check(self.lib.ss_set_sweep_fusion(self.h, int(max_items)), "ss_set_sweep_fusion")
+
     def set_solve_mode(self, mode: str):
         """"sweep": one cooperative launch per solve (default); "per_step": one launch per
         solve level and step."""
@@ -211,6 +217,9 @@ class Symbolic:
     def spmm(self, a_vals, b_vals, X, alpha=None, beta=None) -> torch.Tensor:
         return spmm(self, a_vals, b_vals, X, alpha, beta)
 
+    def factor_segments(self, a_vals, b_vals, row_segment, sigma) -> "Factor":
+        return factor_segments(self, a_vals, b_vals, row_segment, sigma)
+
     def autotune_schur(self, a_vals, b_vals, sigma: float) -> int:
         """Time every factor step's Schur update on the tensor cores and on the CUDA cores
         (one inertia-only factorisation at sigma each) and keep the faster path per step.
@@ -263,6 +272,31 @@ def factor(sym: Symbolic, a_vals, b_vals, sigma, precision: str = "fp64",
     return Factor(sym, h, a_vals, b_vals, sig, precision, rc == L.SS_ERR_SINGULAR)
 
 
+def factor_segments(sym: Symbolic, a_vals, b_vals, row_segment, sigma) -> "Factor":
+    """Inertia-only FP64 factorisation of many pencils stacked into one block-diagonal
+    pattern, every pencil with its own shifts, all pencils in the same launches.
+    row_segment: the pencil of each row (N ints); sigma: n_shift x n_seg shifts (row j: the
+    shifts of call slot j, one per pencil).  Per-pencil counts: Factor.inertia_segments.
+    A pivot below the singularity threshold in some pencil does not raise: the factor's
+    `singular` is set and inertia_segments reports the pencil's tiny pivots."""
+    ctx = sym.ctx
+    _dev(a_vals, "a_vals")
+    _dev(b_vals, "b_vals")
+    if a_vals.numel() != sym.nnz or b_vals.numel() != sym.nnz:
+        raise ValueError("value arrays must match the analysed pattern")
+    seg = np.ascontiguousarray(np.asarray(row_segment, dtype=np.int32))
+    sig = np.ascontiguousarray(np.atleast_2d(np.asarray(sigma, dtype=np.float64)))
+    if seg.size != sym.n:
+        raise ValueError("row_segment needs one entry per row")
+    h = C.c_void_p()
+    rc = ctx.lib.ss_factor_segments(sym.h, _ptr(a_vals), _ptr(b_vals), seg.ctypes.data, sig.shape[1],
+                                    sig.ctypes.data, sig.shape[0], C.byref(h))
+    ctx.check(rc, "ss_factor_segments", allow=(L.SS_ERR_SINGULAR,))
+    f = Factor(sym, h, a_vals, b_vals, sig.max(axis=1), "inertia", rc == L.SS_ERR_SINGULAR)
+    f.n_seg = sig.shape[1]
+    return f
+
+
 @dataclass
 class ProbeResult:
     """One spectral probe SP(sigma) = (sigma, Lambda, X, R) plus solver statistics."""
@@ -306,6 +340,16 @@ class Factor:
 
     def solve(self, j: int, R: torch.Tensor, refine: int = 2) -> torch.Tensor:
         return solve(self, j, R, refine)
+
+    def inertia_segments(self, j: int = 0):
+        """Per-pencil (n_neg, n_zero, n_pos, n_tiny) arrays of slot j of a factor_segments factor."""
+        n = getattr(self, "n_seg", 0)
+        if n <= 0:
+            raise ValueError("not a factor_segments factor")
+        out = [np.zeros(n, dtype=np.int64) for _ in range(4)]
+        self.ctx.check(self.ctx.lib.ss_inertia_segments(self.h, j, *[o.ctypes.data for o in out]),
+                       "ss_inertia_segments")
+        return tuple(out)
 
     def slice_solve(self, j: int, lo: float, hi: float, V0: torch.Tensor, **kw) -> ProbeResult:
         return slice_solve(self, j, lo, hi, V0, **kw)

@@ -150,6 +150,13 @@ extern "C" ss_status ss_set_solve_mode(ss_ctx *ctx, int32_t mode) {
 template <typename T>
 static void set_smem_attrs(int device);
 
+extern "C" ss_status ss_set_sweep_fusion(ss_ctx *ctx, int32_t max_items) {
+    if (!ctx) return SS_ERR_ARG;
+    if (max_items < -1) return ctx->set_error(SS_ERR_ARG, "ss_set_sweep_fusion: max_items must be >= -1");
+    ctx->sweep_fuse_max = max_items;
+    return SS_OK;
+}
+
 extern "C" ss_status ss_set_schur_mode(ss_ctx *ctx, int32_t mode, double min_flops) {
     if (!ctx) return SS_ERR_ARG;
     if ((mode != SS_SCHUR_TENSOR && mode != SS_SCHUR_SIMT) || !(min_flops >= 0.0))
@@ -344,7 +351,7 @@ static void set_smem_attrs(int device) {
     cudaFuncSetAttribute(k_bwd_diag<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)diag_solve_smem<T>());
     cudaFuncSetAttribute(k_fwd_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_kernel_smem<T>());
     cudaFuncSetAttribute(k_bwd_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_kernel_smem<T>());
-    cudaFuncSetAttribute(k_solve_sweeps<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem<T>());
+    cudaFuncSetAttribute(k_solve_sweeps<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_launch_smem<T>());
     if (std::is_same<T, double>::value) {
         cudaFuncSetAttribute(sstc::k_schur_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sstc::kSchurTcSmem);
         cudaFuncSetAttribute(sstc::k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -459,6 +466,8 @@ static void fill_shift(ss_numeric *f, int j, ShiftPtrs<T> &p) {
     p.dblk = f->dblk[j];
     p.piv = f->piv[j];
     p.counts = f->d_counts + SS_NCOUNT * j;
+    p.seg_sigma = f->d_seg_sigma ? f->d_seg_sigma + (int64_t)f->n_seg * j : nullptr;
+    p.eseg = f->d_seg_sigma ? f->d_eseg : nullptr;
     p.sigma = f->sigma[j];
     p.norm = f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1;
     p.tiny_thr = 64.0 * 1.1102230246251565e-16 * p.norm;
@@ -680,13 +689,18 @@ static void factor_free(ss_numeric *f) {
     for (double *p : f->mvals) if (p) cudaFree(p);
     f->mvals.clear();
     if (f->d_counts) cudaFree(f->d_counts);
+    if (f->d_eseg) cudaFree(f->d_eseg);
+    if (f->d_rowseg) cudaFree(f->d_rowseg);
+    if (f->d_seg_sigma) cudaFree(f->d_seg_sigma);
+    f->d_eseg = f->d_rowseg = nullptr;
+    f->d_seg_sigma = nullptr;
     f->arena.clear(); f->arena_lo.clear(); f->linv.clear(); f->dblk.clear(); f->piv.clear();
     f->d_counts = nullptr;
     oz_free_numeric(f);
 }
 
 int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
-                     int32_t n_shift, int32_t precision, ss_numeric **out) {
+                     int32_t n_shift, int32_t precision, ss_numeric **out, const SegShifts *seg) {
     ss_ctx *ctx = sym->ctx;
     *out = nullptr;
     ss_numeric *f = new (std::nothrow) ss_numeric();
@@ -712,6 +726,23 @@ int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_val
     f->dblk.assign(n_shift, nullptr);
     f->piv.assign(n_shift, nullptr);
     cudaError_t e = cudaMalloc((void **)&f->d_counts, sizeof(unsigned long long) * SS_NCOUNT * n_shift);
+    if (seg && e == cudaSuccess) {
+        // the pencil of every stored entry (from its row) and the shift table, on the device
+        f->n_seg = seg->n_seg;
+        std::vector<int32_t> eseg(std::max<int64_t>(1, sym->nnz));
+        for (int64_t r = 0; r < sym->n; ++r)
+            for (int64_t q = sym->rowptr[r]; q < sym->rowptr[r + 1]; ++q) eseg[q] = seg->row_seg[r];
+        e = cudaMalloc((void **)&f->d_eseg, sizeof(int32_t) * eseg.size());
+        if (e == cudaSuccess) e = cudaMalloc((void **)&f->d_rowseg, sizeof(int32_t) * std::max<int64_t>(1, sym->n));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&f->d_seg_sigma, sizeof(double) * n_shift * seg->n_seg);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(f->d_eseg, eseg.data(), sizeof(int32_t) * eseg.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(f->d_rowseg, seg->row_seg, sizeof(int32_t) * sym->n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(f->d_seg_sigma, seg->sigma, sizeof(double) * n_shift * seg->n_seg,
+                           cudaMemcpyHostToDevice);
+    }
     for (int j = 0; j < n_shift && e == cudaSuccess; ++j) {
         if (!f->inertia_only) e = cudaMalloc(&f->arena[j], esz * std::max<int64_t>(1, sym->l_total));
         if (e == cudaSuccess) e = cudaMalloc((void **)&f->linv[j], sizeof(double) * NB * NB * npan);
@@ -850,6 +881,71 @@ extern "C" ss_status ss_factor(ss_symbolic *sym, const double *a_vals, const dou
     }
 }
 
+extern "C" ss_status ss_factor_segments(ss_symbolic *sym, const double *a_vals, const double *b_vals,
+                                        const int32_t *row_segment, int32_t n_seg, const double *sigma,
+                                        int32_t n_shift, ss_numeric **out) {
+    if (!sym) return SS_ERR_ARG;
+    ss_ctx *ctx = sym->ctx;
+    if (ctx->device < 0) return ctx->set_error(SS_ERR_ARG, "ss_factor_segments: host-only context");
+    if (!out || !a_vals || !b_vals || !row_segment || !sigma || n_seg <= 0 || n_shift <= 0 || n_shift > 65535)
+        return ctx->set_error(SS_ERR_ARG, "ss_factor_segments: bad argument");
+    for (int64_t r = 0; r < sym->n; ++r)
+        if (row_segment[r] < 0 || row_segment[r] >= n_seg)
+            return ctx->set_error(SS_ERR_ARG, "ss_factor_segments: row " + std::to_string(r) +
+                                                  " has a pencil index outside [0, n_seg)");
+    // the pattern must not couple rows of different pencils
+    for (int64_t r = 0; r < sym->n; ++r)
+        for (int64_t q = sym->rowptr[r]; q < sym->rowptr[r + 1]; ++q)
+            if (row_segment[sym->colind[q]] != row_segment[r])
+                return ctx->set_error(SS_ERR_ARG, "ss_factor_segments: entry (" + std::to_string(r) + ", " +
+                                                      std::to_string(sym->colind[q]) +
+                                                      ") couples two pencils");
+    std::vector<double> smax(n_shift, 0.0);
+    for (int j = 0; j < n_shift; ++j)
+        for (int g = 0; g < n_seg; ++g) {
+            const double v = sigma[(int64_t)j * n_seg + g];
+            if (!std::isfinite(v)) return ctx->set_error(SS_ERR_ARG, "ss_factor_segments: non-finite shift");
+            smax[j] = std::max(smax[j], std::fabs(v));
+        }
+    try {
+        const SegShifts seg{n_seg, row_segment, sigma};
+        return ss_factor_create(sym, a_vals, b_vals, smax.data(), n_shift, SS_FP64 | SS_INERTIA_ONLY, out, &seg);
+    } catch (const std::bad_alloc &) {
+        return ctx->set_error(SS_ERR_OOM, "ss_factor_segments: host allocation failed");
+    }
+}
+
+extern "C" ss_status ss_inertia_segments(const ss_numeric *f, int32_t j, int64_t *n_neg, int64_t *n_zero,
+                                         int64_t *n_pos, int64_t *n_tiny) {
+    if (!f) return SS_ERR_ARG;
+    ss_ctx *ctx = f->sym->ctx;
+    if (f->n_seg <= 0 || j < 0 || j >= f->n_shift || !n_neg || !n_zero || !n_pos)
+        return ctx->set_error(SS_ERR_ARG, "ss_inertia_segments: bad argument (or not an ss_factor_segments factor)");
+    SS_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    const ss_symbolic *s = f->sym;
+    const int32_t npan = (int32_t)s->panels.size();
+    cudaStream_t st = ctx->stream;
+    unsigned long long *d = nullptr;
+    SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&d, sizeof(unsigned long long) * 4 * f->n_seg, st));
+    SS_CUDA_TRY(ctx, cudaMemsetAsync(d, 0, sizeof(unsigned long long) * 4 * f->n_seg, st));
+    const double tiny = 64.0 * 1.1102230246251565e-16 * (f->norm_a1 + std::fabs(f->sigma[j]) * f->norm_b1);
+    if (npan > 0)
+        ss_launch(ctx, SS_K_MISC, k_segment_inertia, (unsigned)npan, NB, 0, st, npan, (const PanelDesc *)s->d_panels,
+                  (const double *)f->dblk[j], (const int32_t *)s->d_perm, (const int32_t *)f->d_rowseg, tiny, d);
+    std::vector<unsigned long long> h(4 * (size_t)f->n_seg);
+    cudaError_t e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d, st);
+    SS_CUDA_TRY(ctx, e);
+    for (int g = 0; g < f->n_seg; ++g) {
+        n_neg[g] = (int64_t)h[4 * g];
+        n_zero[g] = (int64_t)h[4 * g + 1];
+        n_pos[g] = (int64_t)h[4 * g + 2];
+        if (n_tiny) n_tiny[g] = (int64_t)h[4 * g + 3];
+    }
+    return SS_OK;
+}
+
 extern "C" ss_status ss_autotune_schur(ss_symbolic *sym, const double *a_vals, const double *b_vals, double sigma,
                                        int32_t *n_tc_steps) {
     if (!sym) return SS_ERR_ARG;
@@ -962,22 +1058,36 @@ static int solve_sweeps(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     int &per_sm = ctx->sweep_blocks_per_sm[std::is_same<T, float>::value ? 1 : 0];
     if (per_sm == 0) {
         SS_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_sweeps<T>, 256,
-                                                                       sweep_smem<T>()));
+                                                                       sweep_launch_smem<T>()));
         if (per_sm <= 0) return ctx->set_error(SS_ERR_CUDA, "solve: sweep kernel cannot be resident");
     }
     const int nchunk = (k + KC - 1) / KC, ndchunk = (k + KD - 1) / KD;
+    // FP32 solves with both sweeps may take the fused items on their small levels (one grid
+    // barrier per level and sweep there)
+    const bool fused = std::is_same<T, float>::value && forward && backward && dinv && ctx->sweep_fuse_max != 0;
     int64_t items = 1;
     double flops = 0.0;
     for (const SolveLevel &sl : s->solve_levels) {
         items = std::max<int64_t>(items, std::max<int64_t>((int64_t)sl.count * ndchunk, (int64_t)sl.row_tiles * nchunk));
+        if (fused) items = std::max<int64_t>(items, (int64_t)(sl.row_tiles + sl.count) * nchunk);
         flops += ((forward ? 2.0 : 0.0) + (backward ? 2.0 : 0.0)) * sl.offdiag * k;
     }
     const int nb = (int)std::min<int64_t>((int64_t)per_sm * ctx->sm_count, items);
-    const int64_t zn = std::max<int64_t>(1, (int64_t)s->panels.size()) * NB * k;
-    T *zall = nullptr;
+    const int64_t npan = std::max<int64_t>(1, (int64_t)s->panels.size());
+    const int64_t zn = npan * NB * k;
+    // fused: the arrival counters (npan x nchunk int32) and the forward output y (N x k)
+    // follow z in the same allocation
+    const int64_t an = fused ? (npan * nchunk * (int64_t)sizeof(int32_t) + sizeof(T) - 1) / sizeof(T) : 0;
+    const int64_t yn = fused ? s->n * (int64_t)k : 0;
+    T *zall = nullptr, *ybuf = nullptr;
+    int32_t *arrive = nullptr;
     if (backward) {
-        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&zall, sizeof(T) * zn, st));
-        SS_CUDA_TRY(ctx, cudaMemsetAsync(zall, 0, sizeof(T) * zn, st));
+        SS_CUDA_TRY(ctx, cudaMallocAsync((void **)&zall, sizeof(T) * (zn + an + yn), st));
+        SS_CUDA_TRY(ctx, cudaMemsetAsync(zall, 0, sizeof(T) * (zn + an), st));
+        if (fused) {
+            arrive = reinterpret_cast<int32_t *>(zall + zn);
+            ybuf = zall + zn + an;
+        }
     }
     SS_CUDA_TRY(ctx, cudaMemsetAsync(ctx->d_bar, 0, sizeof(GridBar) + sizeof(int32_t) * kSmSlots, st));
     SweepArgs a{};
@@ -998,13 +1108,15 @@ static int solve_sweeps(ss_numeric *f, int j, T *b, int k, bool forward, bool ba
     a.limit = 20000000;        // polls of about 64 ns: ~1 s per barrier
     a.sm_slots = sm_slots;
     a.nsm_slots = kSmSlots;
-    void *args[] = {(void *)&a, (void *)&arena, (void *)&b, (void *)&zall};
+    a.arrive = arrive;
+    a.fuse_max = ctx->sweep_fuse_max < 0 ? nb : ctx->sweep_fuse_max;
+    void *args[] = {(void *)&a, (void *)&arena, (void *)&b, (void *)&zall, (void *)&ybuf};
     g_ss_launches.fetch_add(1, std::memory_order_relaxed);
     size_t slot = 0;
     const bool prof = ctx->prof_mask & (1u << cls);
     if (prof) slot = ss_prof_begin(ctx, cls);
     SS_CUDA_TRY(ctx, cudaLaunchCooperativeKernel((void *)k_solve_sweeps<T>, dim3(nb), dim3(256), args,
-                                                 sweep_smem<T>(), st));
+                                                 sweep_launch_smem<T>(), st));
     if (prof) ss_prof_end(ctx, cls, slot);
     ctx->add_flops(cls, flops);
     int herr = 0;
@@ -1205,7 +1317,9 @@ static int shifted_values(ss_numeric *f, int j, const double **out) {
 }
 
 // Y = (A - sigma_j B) X: A X - sigma_j B X on the tensor cores (ss_set_gemm_mode), else one
-// product with the values of A - sigma_j B
+// product with the values of A - sigma_j B.  (One pass over slices of A - sigma_j B was
+// measured: its residuals carry the rounding of each shifted entry, and the FP32 solves
+// then needed about 1.6x as many refinement steps, costing more than the pass it saves.)
 static int spmm_shifted(ss_numeric *f, int j, const double *X, int k, double *Y) {
     if (oz_spmm_ok(f, k)) {
         const int which[2] = {0, 1};

@@ -43,6 +43,9 @@ struct ShiftPtrs {
     unsigned char *sl;              // operand slices of the tensor-core Schur update
     int32_t *ex;                    // their row exponents
     unsigned long long *counts;     // [neg, zero, pos, tiny, min_pivot_bits, n2x2, max_abs_l_bits, timeouts]
+    const double *seg_sigma;        // several pencils in one block-diagonal pattern: the shift
+    const int32_t *eseg;            // of each pencil (seg_sigma) and the pencil of each stored
+                                    // entry (eseg); null for one pencil (sigma)
     double sigma;
     double tiny_thr;                // pivots below this are flagged
     double norm;                    // ||A - sigma B||_1 bound (for min-pivot ratio)
@@ -56,7 +59,39 @@ __global__ void k_assemble(int64_t count, const int32_t *__restrict__ asm_e,
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count;
          q += (int64_t)gridDim.x * blockDim.x) {
         int32_t e = asm_e[q];
-        s.ws[asm_dest[q]] = (T)(s.a[e] - s.sigma * s.b[e]);
+        const double sg = s.eseg ? s.seg_sigma[s.eseg[e]] : s.sigma;
+        s.ws[asm_dest[q]] = (T)(s.a[e] - sg * s.b[e]);
+    }
+}
+
+// Inertia of D per pencil of a block-diagonal pattern: every panel's 1x1 and 2x2 pivots
+// (the classification of k_diag_bk) counted for the pencil its rows belong to.  seg:
+// pencil of each original row; perm: permuted -> original row; out: n_seg x 4
+// (neg, zero, pos, tiny).
+__global__ void k_segment_inertia(int32_t npan, const PanelDesc *__restrict__ panels,
+                                  const double *__restrict__ dblk, const int32_t *__restrict__ perm,
+                                  const int32_t *__restrict__ seg, double tiny_thr,
+                                  unsigned long long *__restrict__ out) {
+    const int p = blockIdx.x;
+    if (p >= npan) return;
+    const PanelDesc pd = panels[p];
+    const int i = threadIdx.x;
+    if (i >= pd.w) return;
+    const double *dd = dblk + (int64_t)p * 2 * NB, *de = dd + NB;
+    unsigned long long *o = out + 4ll * seg[perm[pd.g0]];
+    if (i > 0 && de[i - 1] != 0.0) return;                 // second row of a 2x2 block
+    if (de[i] != 0.0) {                                     // 2x2 block (i, i+1)
+        const double a = dd[i], b = de[i], c = dd[i + 1], det = a * c - b * b, tr = a + c;
+        if (det < 0) { atomicAdd(&o[0], 1ull); atomicAdd(&o[2], 1ull); }
+        else if (det > 0) atomicAdd(&o[tr > 0 ? 2 : 0], 2ull);
+        else { atomicAdd(&o[1], 1ull); atomicAdd(&o[tr > 0 ? 2 : (tr < 0 ? 0 : 1)], 1ull); }
+        const double emax = fabs(0.5 * tr) + sqrt(0.25 * (a - c) * (a - c) + b * b);
+        const double emin = emax > 0 ? fabs(det) / emax : 0.0;
+        if (emin < tiny_thr) atomicAdd(&o[3], 1ull);
+    } else {
+        const double d = dd[i];
+        atomicAdd(&o[d < 0 ? 0 : (d > 0 ? 2 : 1)], 1ull);
+        if (fabs(d) < tiny_thr) atomicAdd(&o[3], 1ull);
     }
 }
 

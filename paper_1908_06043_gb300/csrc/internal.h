@@ -29,6 +29,8 @@ struct ss_ctx {
     double tc_min_flops = 2.0e7;              // a factor step's Schur flops below which it stays on CUDA cores
     GridBar *d_bar = nullptr;                 // grid barrier state of the sweep kernel
     int sweep_blocks_per_sm[2] = {0, 0};      // resident sweep-kernel blocks per SM (FP64, FP32)
+    int sweep_fuse_max = 0;                   // FP32 sweep: fuse levels with at most this many items
+                                              // (-1: the resident blocks; 0: never)
     // per-class launch timing (ss_profile): event pairs recorded around launches
     uint32_t prof_mask = 0;
     std::vector<cudaEvent_t> ev_pool;
@@ -261,6 +263,11 @@ struct ss_numeric {
     bool counts_valid = false;
     OzVals *oz[2] = {nullptr, nullptr};  // digit slices of A and B for tensor-core products, or null
     bool oz_failed = false;               // those slices did not fit: products on the CUDA cores
+    // several pencils in one block-diagonal pattern (ss_factor_segments): a shift per pencil
+    int32_t n_seg = 0;
+    int32_t *d_eseg = nullptr;            // pencil of each stored entry (nnz)
+    int32_t *d_rowseg = nullptr;          // pencil of each original row (n)
+    double *d_seg_sigma = nullptr;        // n_shift x n_seg shifts
 };
 
 // solves of shift j run in FP32 (an FP32 factor, or an FP64 factor with a rounded copy)
@@ -273,8 +280,14 @@ int ss_symbolic_upload(ss_symbolic *s);
 void ss_symbolic_free_device(ss_symbolic *s);
 void ss_free_plans(ss_symbolic *s);
 int ss_factor_fetch_counts(ss_numeric *f);
+// seg (optional): several pencils of one block-diagonal pattern, each with its own shifts
+struct SegShifts {
+    int32_t n_seg;
+    const int32_t *row_seg;   // host, n: pencil of each row
+    const double *sigma;      // host, n_shift x n_seg
+};
 int ss_factor_create(ss_symbolic *sym, const double *a_vals, const double *b_vals, const double *sigma,
-                     int32_t n_shift, int32_t precision, ss_numeric **out);
+                     int32_t n_shift, int32_t precision, ss_numeric **out, const SegShifts *seg = nullptr);
 constexpr int SS_NCOUNT = 8;   // per-shift device counters: neg, zero, pos, tiny, min pivot, 2x2, max |L|,
                                // device waits that ran out
 int ss_norm1(ss_symbolic *s, const double *vals, double *out);

@@ -323,13 +323,14 @@ int spmm_f(ss_numeric *f, const double *a, const double *b, const double *alpha,
 }
 
 void oz_free_numeric(ss_numeric *f) {
-    for (OzVals *&v : f->oz) {
-        if (!v) continue;
+    auto drop = [](OzVals *&v) {
+        if (!v) return;
         if (v->sl) cudaFree(v->sl);
         if (v->em) cudaFree(v->em);
         delete v;
         v = nullptr;
-    }
+    };
+    for (OzVals *&v : f->oz) drop(v);
 }
 
 void oz_free_symbolic(ss_symbolic *s) {

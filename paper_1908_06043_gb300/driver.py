@@ -455,6 +455,12 @@ class SliceSolver:
             lo = lam_min if j == 0 else tau[j]
             hi = lam_max if j == ns - 1 else tau[j + 1]
             windows.append((lo, hi))
+        # exact counts of the windows themselves: inertia at the split points between
+        # neighbouring probes (one inertia-only factor), so each probe's first round stops
+        # once its window's eigenvalues have converged
+        inner = [windows[j][1] for j in range(ns - 1)]
+        below = [nneg_min] + (self.count_below(inner) if inner else []) + [nneg_max]
+        wcount = [below[j + 1] - below[j] for j in range(ns)]
         # basis sizes from the exact counts at the shifts (the window holds about half of
         # each neighbouring slice) or the DOS
         kout, m1, cnt = [], [], []
@@ -496,14 +502,15 @@ class SliceSolver:
                                        driver="lanczos", k_out=ko, allow_noconv=True)
                 else:
                     kk = k or (ks[j] if ks is not None else min(n, -(-(2 * cnt[j] + 16) // 16) * 16))
-                    kk = min(n, 4096, max(kk, -(-(cnt[j] + 16) // 16) * 16))
+                    kk = min(n, 4096, max(kk, -(-(cnt[j] + 16) // 16) * 16, -(-(wcount[j] + 16) // 16) * 16))
                     if Xs[j] is None:
                         v0 = V0[j] if V0 is not None and V0[j] is not None else torch.randn(n, kk, generator=g, device="cuda",
                                                                      dtype=torch.float64)
-                        # stop the first round at 80% of the window's estimated count;
-                        # validation then tops up with short rounds
-                        est = (float(model.Phi(hi)[0] - model.Phi(lo)[0]) if model is not None else cnt[j])
-                        mi, ne = first_iters, max(1, int(0.8 * est))
+                        # the first round stops once as many window Ritz pairs as the
+                        # window's exact count have converged (a window without
+                        # eigenvalues gets three iterations); validation then tops up
+                        # with short rounds
+                        mi, ne = (first_iters, wcount[j]) if wcount[j] > 0 else (3, 1)
                     else:
                         v0, mi, ne = Xs[j], iters_per_round, v0_never(Xs[j])
                     fj, jj = (f64[j], 0) if j in f64 else (f, j)
@@ -675,7 +682,7 @@ def plan_slices(solver: "SliceSolver", model: "DosModel", n_e: int, n_s: int, mo
              for j in range(1, n_s)]
     bounds = [lam_min] + inner + [lam_max]
     need = sorted(set(range(n_s + 1)) if windows is None else {b for j in windows for b in (j, j + 1)})
-    got = solver.count_below([bounds[b] for b in need])
+    got = solver.count_below([bounds[b] for b in need]) if need else []
     counts = [None] * (n_s + 1)
     for b, c in zip(need, got):
         counts[b] = c
@@ -687,6 +694,43 @@ def plan_slices(solver: "SliceSolver", model: "DosModel", n_e: int, n_s: int, mo
         c = counts[j + 1] - counts[j] if counts[j] is not None and counts[j + 1] is not None else 0
         out.append(min(n, 4096, max(k or 0, _ceil16(2 * c + 16), _ceil16(c + 16))))
     return SlicePlan(list(shifts), bounds, counts, out, lam_min, lam_max)
+
+
+def count_below_stacked(sym_stack, a_stack, b_stack, row_segment, sigmas):
+    """Exact eigenvalue counts of many independent pencils at once: the pencils stacked
+    into one block-diagonal pattern (workloads.pencils.stack_pencils), sigmas[p] the list
+    of shifts of pencil p (lists of any lengths).  One inertia-only FP64 factorisation of
+    the stack per call slot, every pencil at its own shift in the same launches
+    (ss_factor_segments); a pencil with fewer shifts repeats its last one.  Returns one
+    list of counts per pencil.  Raises if a shift is within the singularity threshold of
+    an eigenvalue of its pencil."""
+    n_seg = len(sigmas)
+    width = max(len(x) for x in sigmas)
+    tab = np.array([[float(sigmas[p][min(j, len(sigmas[p]) - 1)]) for p in range(n_seg)] for j in range(width)])
+    f = sym_stack.factor_segments(a_stack, b_stack, row_segment, tab)
+    out = [[] for _ in range(n_seg)]
+    try:
+        for j in range(width):
+            neg, _, _, tiny = f.inertia_segments(j)
+            for p in range(n_seg):
+                if j < len(sigmas[p]):
+                    if tiny[p]:
+                        raise api.SisliceError(api.L.SS_ERR_SINGULAR, f"pencil {p}: shift {tab[j, p]} is within the "
+                                                                  f"singularity threshold of an eigenvalue")
+                    out[p].append(int(neg[p]))
+    finally:
+        f.close()
+    return out
+
+
+def plan_with_counts(plan: SlicePlan, counts, n: int) -> SlicePlan:
+    """The plan of an N = n pencil with its window-bound counts (and the basis widths that
+    follow from them, as plan_slices sets them) taken from `counts` (one per bound)."""
+    ks = []
+    for j, k in enumerate(plan.ks):
+        c = counts[j + 1] - counts[j]
+        ks.append(min(n, 4096, max(k or 0, _ceil16(2 * c + 16), _ceil16(c + 16))))
+    return SlicePlan(list(plan.shifts), list(plan.bounds), list(counts), ks, plan.lam_min, plan.lam_max)
 
 
 def solve_slice(solver: "SliceSolver", plan: SlicePlan, j: int, seed: int = 0, first_iters: int = 80,
@@ -934,7 +978,8 @@ def ball_windows_from_spectrum(values, lam_min: float, lam_max: float, n_s: int)
 
 def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precision: str = "mixed",
                    tol: float = 1e-10, lanczos_steps: int = 100, n_vec: int = 4, seed: int = 0,
-                   start=None, uniforms=None, eta_tol: float = np.inf, balance: float = 2.0):
+                   start=None, uniforms=None, eta_tol: float = np.inf, balance: float = 2.0,
+                   on_step=None):
     """Lowest n_e eigenpairs of a sequence of pencils (A_i, B) on one pattern, as the SCF
     loop of Alg. 1 produces them (Section 3.2).  Step 0 places the shifts from a Lanczos
     DOS estimate.  Every later step migrates the probes: k-means of the previous step's
@@ -954,7 +999,8 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
     that ball placement instead, each probe warm-started from the previous eigenvectors
     in its window.  Returns one SliceResult per
     pencil; timings["migration"] records the shifts and cluster sizes chosen and
-    timings["eta"] the monitor's (old, new, changed)."""
+    timings["eta"] the monitor's (old, new, changed).  on_step(i, result), if given, is
+    called as soon as pencil i is solved."""
     n = sym.n
     rng = np.random.default_rng(seed)
     etas = []
@@ -1017,6 +1063,8 @@ def solve_sequence(sym: api.Symbolic, a_list, b_vals, n_e: int, n_s: int, precis
                                             ball_fallback=bool(fallback))
         res.timings["eta"] = etas[-1] if i > 0 else None
         results.append(res)
+        if on_step is not None:
+            on_step(i, res)
     return results
 
 

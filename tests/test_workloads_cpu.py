@@ -31,3 +31,36 @@ def test_drop_compensation_eight_exponents():
     assert sla.eigvalsh(big.dense("b"))[0] < 0.0
     big_c = gaussian_pencil((8, 8, 8), exponents_8(), seed=3, compensate_drop=True)
     assert sla.eigvalsh(big_c.dense("b"))[0] > 1e-5
+
+
+def test_uneven_batch_specs_ranges_and_seeding():
+    from workloads.pencils import EXPONENTS_2, EXPONENTS_4, uneven_batch_specs
+    specs = uneven_batch_specs(256)
+    assert specs == uneven_batch_specs(256)                 # seeded
+    dims = np.array([d for d, _, _ in specs])
+    assert dims.min() == 8 and dims.max() == 18
+    kinds = {e for _, e, _ in specs}
+    assert kinds == {EXPONENTS_2, EXPONENTS_4}
+    n = np.array([np.prod(d) * len(e) for d, e, _ in specs])
+    assert 1000 <= n.min() and n.max() <= 4 * 18 ** 3
+
+
+def test_stack_pencils_is_block_diagonal_and_analyses_per_pencil():
+    from paper_1908_06043_gb300 import api
+    from workloads.pencils import EXPONENTS_2, gaussian_pencil, laplacian_1d, stack_pencils
+    ps = [gaussian_pencil((3, 4, 5), EXPONENTS_2, seed=5), laplacian_1d(50, mass=True), gaussian_pencil((4, 4, 4), seed=6)]
+    st, seg, offs = stack_pencils(ps)
+    assert st.n == sum(q.n for q in ps) and st.nnz == sum(q.nnz for q in ps)
+    rows = st.rows()
+    assert np.array_equal(seg[rows], seg[st.colind])        # no entry couples two pencils
+    for i, q in enumerate(ps):
+        blk = slice(offs[i], offs[i + 1])
+        assert np.array_equal(st.dense("a")[blk, blk], q.dense("a"))
+        assert np.array_equal(st.dense("b")[blk, blk], q.dense("b"))
+    # the dissection keeps each pencil in its own subtrees: the stack's factor flops are
+    # the sum of the pencils' own
+    ctx = api.Context(-1)
+    whole = ctx.analyze(st.rowptr, st.colind)
+    whole.validate()
+    parts = sum(ctx.analyze(q.rowptr, q.colind).info["factor_flops"] for q in ps)
+    assert abs(whole.info["factor_flops"] - parts) <= 1e-9 * parts

@@ -279,6 +279,38 @@ def config_pencil(config: int) -> Pencil:
     raise ValueError(f"unknown config {config}")
 
 
+def uneven_batch_specs(count: int = 256, seed: int = 44):
+    """The uneven batch of independent pencils: for each, lattice dims drawn uniformly from
+    8..18 per axis and 2 or 4 functions per atom (EXPONENTS_2 / EXPONENTS_4, equally
+    likely), with its own potential seed.  Returns a list of (dims, exps, seed)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        dims = tuple(int(d) for d in rng.integers(8, 19, size=3))
+        exps = EXPONENTS_4 if rng.random() < 0.5 else EXPONENTS_2
+        out.append((dims, exps, 1000 + i))
+    return out
+
+
+def batch_pencils(specs):
+    return [gaussian_pencil(d, e, seed=s_) for d, e, s_ in specs]
+
+
+def stack_pencils(pencils):
+    """Block-diagonal stack of independent pencils on one pattern: pencil p's rows and
+    columns follow those of pencils 0..p-1.  Returns (stacked Pencil, pencil of each row,
+    row offset of each pencil)."""
+    offs = np.cumsum([0] + [q.n for q in pencils]).astype(np.int64)
+    nnz_off = np.cumsum([0] + [q.nnz for q in pencils]).astype(np.int64)
+    rowptr = np.concatenate([[0]] + [q.rowptr[1:] + nnz_off[i] for i, q in enumerate(pencils)]).astype(np.int64)
+    colind = np.concatenate([q.colind.astype(np.int64) + offs[i] for i, q in enumerate(pencils)]).astype(np.int32)
+    a = np.concatenate([q.a for q in pencils])
+    b = np.concatenate([q.b for q in pencils])
+    seg = np.concatenate([np.full(q.n, i, dtype=np.int32) for i, q in enumerate(pencils)])
+    st = Pencil(int(offs[-1]), rowptr, colind, a, b, dict(kind="stack", count=len(pencils)))
+    return st, seg, offs
+
+
 def normal_block(n: int, k: int, seed: int) -> np.ndarray:
     """Seeded N(0,1) start block, N x k row-major (used as V0 / Lanczos start vectors)."""
     return np.random.default_rng(seed).standard_normal((n, k))
