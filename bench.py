@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_tc", "fp64"])
     ap.add_argument("--gemm", default="tensor", choices=["tensor", "simt"],
                     help="where the probes' FP64 products (sparse A X, B X; Gram; tall) run")
+    ap.add_argument("--refine-ratio", type=float, default=0.0,
+                    help="FP32 solves refine to this fraction of the window's residual (0: library default)")
+    ap.add_argument("--check-every", type=int, default=3, help="first-round Rayleigh-Ritz period of a probe")
     ap.add_argument("--no-fp64-side", action="store_true", help="skip the FP64 side-by-side steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end pass (default: --steps)")
@@ -446,7 +449,8 @@ def main():
     t_place = time.perf_counter()
     start = torch.tensor(normal_block(p.n, n_vec, 1000), device="cuda")
     model = DosModel(p.n, sym.dos_estimate(a, b, steps_dos, start))
-    solver = SliceSolver(sym, a, b, precision=args.precision)
+    solver = SliceSolver(sym, a, b, precision=args.precision, refine_ratio=args.refine_ratio,
+                         check_every=args.check_every)
     # exact counts only at the bounds of the windows this run solves (warm-up, timed,
     # end-to-end and FP64 steps all take windows 0, 1, ... cyclically)
     n_used = min(n_s, max(args.warmup, args.steps, args.e2e_steps, n_s // 2 + 1 if args.profile_step else 0))
@@ -562,7 +566,7 @@ def main():
     if not args.no_fp64_side and args.precision != "fp64" and rank == 0:
         m = min(args.steps, n_s, 8)
         js = sorted({int(round(i * (min(args.steps, n_s) - 1) / max(1, m - 1))) for i in range(m)})
-        solver64 = SliceSolver(sym, a, b, precision="fp64")
+        solver64 = SliceSolver(sym, a, b, precision="fp64", check_every=args.check_every)
         t64, ok64, f64s, res64 = [], 0, [], []
         for jx in js:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -626,6 +630,7 @@ def main():
            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
            "data": "synthetic",
            "config": {"workload": wl["name"], "precision": args.precision, "dense_products": args.gemm,
+                      "refine_ratio": args.refine_ratio or 1e-1, "check_every": args.check_every,
                       "step": "one slice solve: LDL^T of A - sigma_j B, inertia, shift-invert subspace "
                               "iteration of window j to resid <= 1e-10, validation by inertia counts",
                       "windows": f"step s solves window s mod {n_s}",

@@ -120,7 +120,7 @@ typedef struct ss_solve_opts {
     int32_t reserved;
     double refine_ratio;        /* FP32 solves refine until their residual is this
                                    fraction of the window's current residual (clamped
-                                   to 1e-14 .. 1e-8) [1e-3]                          */
+                                   to 1e-14 .. 1e-8) [1e-1]                          */
 } ss_solve_opts;
 
 /* ---- context ---------------------------------------------------------------------
@@ -381,7 +381,7 @@ ss_status ss_solve_noalloc(ss_numeric *f, int32_t shift_idx, const double *R, in
  * Builds the spectral probe of shift sigma_j.  V0 is the DEVICE N x k start block
  * (seeded N(0,1) or a previous probe's X; required; k <= min(N, 4096)).  Solves of a
  * shift solved in FP32 are refined once the window is near convergence, until their
- * residual is 1e-3 of the window's current residual (1e-13 .. 1e-8).  SS_SUBSPACE iterates on k
+ * residual is 1e-1 of the window's current residual (1e-13 .. 1e-8).  SS_SUBSPACE iterates on k
  * vectors and returns k Ritz pairs.  SS_BLOCK_LANCZOS builds max_iter blocks of width k
  * (O = (A - sigma B)^-1 B, full B-re-orthogonalisation), does one Rayleigh-Ritz on the
  * whole basis and returns the k_out Ritz pairs nearest sigma.

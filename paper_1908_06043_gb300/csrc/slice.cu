@@ -323,7 +323,7 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
     int next_rr = every, it_prev_rr = 0;
     const int refine = o.refine > 0 ? o.refine : 2;
     const double tol = o.tol > 0 ? o.tol : 1e-10;
-    const double ratio = o.refine_ratio > 0 ? std::min(o.refine_ratio, 1.0) : 1e-3;
+    const double ratio = o.refine_ratio > 0 ? std::min(o.refine_ratio, 1.0) : 1e-1;
     const int64_t per = 2048;
     while (it < max_iter) {
         ++it;
@@ -331,8 +331,9 @@ int slice_solve_impl(ss_numeric *f, int j, double lo, double hi, const ss_solve_
         // while the window's residuals are above 1e-6 and FP64 refinement afterwards
         int done_ref = 0;
         const int ref_now = near_conv ? (ss_solves_f32(f, j) ? refine : 1) : 0;
-        // FP32 solves refine until their residual is 1e-3 of the window's current residual
-        // (1e-13 before the first Rayleigh-Ritz of this call, at most 1e-8)
+        // FP32 solves refine until their residual is 1e-1 of the window's current residual
+        // (1e-13 before the first Rayleigh-Ritz of this call, at most 1e-8): inexact inverse
+        // iteration keeps converging while the solve error falls in step with the residual
         double ref_target = 0.0;
         if (near_conv && ss_solves_f32(f, j))
             ref_target = hist.empty() ? 1e-13 : std::max(1e-14, std::min(1e-8, ratio * hist.back()));

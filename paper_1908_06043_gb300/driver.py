@@ -379,7 +379,7 @@ class SliceSolver:
                  refine_ratio=0.0, check_every=3):
         self.sym, self.a, self.b = sym, a_vals, b_vals
         self.precision, self.tol, self.refine = precision, tol, refine
-        self.refine_ratio = refine_ratio       # 0: the library default (1e-3)
+        self.refine_ratio = refine_ratio       # 0: the library default (1e-1)
         self.check_every = check_every         # first-round Rayleigh-Ritz period (< 0: predictive)
 
     def count_below(self, sigmas):

@@ -200,3 +200,15 @@ def test_ball_windows_from_previous_spectrum():
     counts = [int(np.sum((t > b[j]) & (t <= b[j + 1]))) for j in range(16)]
     assert sum(counts) == t.size
     assert max(ks) <= 4096 and min(counts[2:]) > 0
+
+
+def test_plan_with_counts_sets_exact_windows_and_widths():
+    # the window-bound counts of a batched factorisation go into a plan: exact counts per
+    # window, and basis widths of at least 2c + 16 (multiple of 16), capped at N
+    from paper_1908_06043_gb300.driver import SlicePlan, plan_with_counts
+    plan = SlicePlan([0.0, 1.0, 2.0], [-1.0, 0.5, 1.5, 2.5], [None] * 4, [None, 64, None], -1.0, 2.5)
+    out = plan_with_counts(plan, [0, 10, 70, 75], n=120)
+    assert out.counts == [0, 10, 70, 75]
+    assert [out.exact(j) for j in range(3)] == [10, 60, 5]
+    assert out.ks == [48, 120, 32]                  # 2*10+16=36 -> 48; 2*60+16=136 -> capped at N; 2*5+16 -> 32
+    assert out.shifts == plan.shifts and out.bounds == plan.bounds
