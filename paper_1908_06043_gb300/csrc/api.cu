@@ -1361,7 +1361,6 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
         ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
                   (const double *)w, out, 1);
         for (int it = 0; it < refine; ++it) {
-            const double *mv = nullptr;
             if ((rc = spmm_shifted(f, j, x, k, y)) != SS_OK) return rc;
             ss_launch(ctx, SS_K_MISC, k_axpy_sub, g, 256, 0, st, tot, R, (const double *)y, y);
             ss_launch(ctx, SS_K_PERMUTE, k_permute_rows<double, double>, g, 256, 0, st, s->n, k, s->d_perm,
@@ -1400,7 +1399,6 @@ int solve_apply(ss_numeric *f, int j, const double *R, int k, double *X, int ref
     for (int it = 0; it <= refine; ++it) {
         const double *rhs = R;
         if (it > 0) {
-            const double *mv = nullptr;
             if ((rc = spmm_shifted(f, j, x, k, y)) != SS_OK) return rc;
             if (mx) {
                 SS_CUDA_TRY(ctx, cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * 2, st));
