@@ -64,3 +64,15 @@ def test_stack_pencils_is_block_diagonal_and_analyses_per_pencil():
     whole.validate()
     parts = sum(ctx.analyze(q.rowptr, q.colind).info["factor_flops"] for q in ps)
     assert abs(whole.info["factor_flops"] - parts) <= 1e-9 * parts
+
+
+def test_stacked_spectrum_is_the_union_of_the_pencils_spectra():
+    # the oracle's eigenvalues of the stack are the pencils' eigenvalues merged, so each
+    # pencil's count below its own shift is the stack's count restricted to its rows
+    from oracle import dense
+    from workloads.pencils import EXPONENTS_2, gaussian_pencil, laplacian_1d, stack_pencils
+    ps = [gaussian_pencil((3, 3, 4), EXPONENTS_2, seed=8), laplacian_1d(40, mass=True)]
+    st, _, _ = stack_pencils(ps)
+    lam_st = dense.gen_eig(st.dense("a"), st.dense("b"), vectors=False)[0]
+    parts = np.sort(np.concatenate([dense.gen_eig(q.dense("a"), q.dense("b"), vectors=False)[0] for q in ps]))
+    assert np.allclose(lam_st, parts, rtol=1e-12, atol=1e-12 * np.abs(parts).max())
