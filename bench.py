@@ -364,6 +364,10 @@ def main():
     build()
     ws, rank, local = dist_setup(args)
     dev = torch.cuda.current_device()
+    if args.batch:
+        ctx = api.Context(dev)
+        ctx.set_gemm_mode(args.gemm)
+        return run_batch(args, ctx)
     t_setup = time.perf_counter()
     p = config_pencil(wl["config"])
     ctx = api.Context(dev)
@@ -409,9 +413,6 @@ def main():
                    for c, v in prof.items() if v[0]}
         print(json.dumps({"factor_only": args.factor_only, "workload": wl["name"], "classes": out}), flush=True)
         return
-
-    if args.batch:
-        return run_batch(args, ctx)
 
     if args.sequence:
         # SCF-like pencil sequence: DOS placement for the first pencil, k-means probe
