@@ -306,7 +306,8 @@ def run_batch(args, ctx):
         sym = ctx.analyze(q.rowptr, q.colind)
         a = torch.tensor(q.a, device="cuda")
         b = torch.tensor(q.b, device="cuda")
-        sv = SliceSolver(sym, a, b, precision=args.precision)
+        sv = SliceSolver(sym, a, b, precision=args.precision, refine_ratio=args.refine_ratio,
+                         check_every=args.check_every)
         model = DosModel(q.n, sym.dos_estimate(a, b, 100, torch.tensor(normal_block(q.n, 4, 1000 + i),
                                                                          device="cuda")))
         solvers.append(sv)
