@@ -40,7 +40,7 @@ __device__ __forceinline__ unsigned long long gb_clock_ns() {
 }
 
 __device__ __forceinline__ bool grid_barrier(GridBar *bar, unsigned int nblocks, long long limit) {
-    __shared__ int s_ok;     // one verdict per block, read by all of its threads
+    __shared__ int s_ok;     // one outcome per block, read by all of its threads
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int g = gb_ld_acquire(&bar->gen);
